@@ -1,0 +1,164 @@
+"""Direct and Krylov solvers of the Stokes system (oracle).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+* ``solve_direct``  sparse-direct solve of eq. discretestokes
+  [A B; B^T 0][u; p] = [f; g], bordered by the constraint int p = 0 when
+  there is no Neumann face (eq. pressure).
+* ``pcg``           preconditioned CG on A with the relative stopping test
+  ||A y - x|| / ||x|| < eps of Sec. 6 (inner viscous solve).
+* ``fgmres``        right-preconditioned flexible GMRES (Saad's FGMRES) on the
+  saddle system with the upper block-triangular preconditioner of
+  eq. discretestokespc, S replaced by the diagonal S* (Sec. 5), and
+  A^{-1} replaced by an inner PCG solve (Sec. 6).  Stopping test: residual
+  2-norm reduced by ``rtol`` from the initial one (Sec. 7 settings).
+  Orthogonalisation: classical Gram-Schmidt applied twice.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import sip
+
+
+def stokes_matrix(A, B):
+    return sp.bmat([[A, B], [B.T, None]], format="csr")
+
+
+def solve_direct(prob, A, B, f, g=None):
+    """Sparse-direct (SuperLU) solve of the saddle system.  Without a
+    Neumann face the pressure is fixed by int_Omega p = 0."""
+    n_u, n_p = B.shape
+    g = np.zeros(n_p) if g is None else g
+    K = stokes_matrix(A, B)
+    rhs = np.concatenate([f, g])
+    if not prob.has_neumann:
+        w = sip.pressure_mass(prob) * sip.pressure_constant(prob)   # int psi_i
+        col = sp.csr_matrix(np.concatenate([np.zeros(n_u), w])[:, None])
+        K = sp.bmat([[K, col], [col.T, None]], format="csc")
+        rhs = np.concatenate([rhs, [0.0]])
+    sol = spla.spsolve(K.tocsc(), rhs)
+    return sol[:n_u], sol[n_u:n_u + n_p]
+
+
+def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
+    """Preconditioned CG for A y = x; stops when ||A y - x|| < rtol ||x||.
+
+    Returns (y, iterations)."""
+    y = np.zeros_like(x) if y0 is None else y0.copy()
+    r = x - apply_A(y) if y0 is not None else x.copy()
+    nx = np.linalg.norm(x)
+    if nx == 0.0:
+        return y, 0
+    z = precond(r)
+    d = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        q = apply_A(d)
+        alpha = rz / (d @ q)
+        y += alpha * d
+        r -= alpha * q
+        if np.linalg.norm(r) < rtol * nx:
+            return y, it
+        z = precond(r)
+        rz_new = r @ z
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+    return y, maxit
+
+
+class BlockPreconditioner:
+    """Action of the upper block-triangular preconditioner inverse
+    (eq. discretestokespc) with S -> S* and A^{-1} -> inner PCG:
+        y_p = S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
+
+    def __init__(self, A, B, s_diag, inner_precond, inner_rtol=1e-3,
+                 inner_maxit=200, null_p=None):
+        self.A, self.B, self.s = A, B, s_diag
+        self.inner_precond = inner_precond
+        self.inner_rtol, self.inner_maxit = inner_rtol, inner_maxit
+        self.null_p = null_p
+        self.inner_its = []
+
+    def __call__(self, x):
+        n_u = self.A.shape[0]
+        xu, xp = x[:n_u], x[n_u:]
+        yp = xp / self.s
+        if self.null_p is not None:
+            yp = project_out(yp, self.null_p)
+        t = xu - self.B @ yp
+        yu, its = pcg(lambda v: self.A @ v, self.inner_precond, t,
+                      self.inner_rtol, self.inner_maxit)
+        self.inner_its.append(its)
+        return np.concatenate([yu, yp])
+
+
+def project_out(v, z):
+    return v - (z @ v) / (z @ z) * z
+
+
+def fgmres(apply_K, precond, b, rtol, restart=100, maxit=200, null_p=None, n_u=None):
+    """Right-preconditioned flexible GMRES (Saad, Alg. 9.6) with CGS2.
+
+    Solves K x = b from x0 = 0; stops when ||b - K x||_2 <= rtol ||b||_2.
+    ``null_p`` (with ``n_u``) projects the constant pressure out of every
+    basis vector (Sec. 5, consistent right-hand side for a singular system).
+    Returns (x, iterations, residual history)."""
+    n = b.size
+    x = np.zeros(n)
+    beta0 = np.linalg.norm(b)
+    hist = [beta0]
+    if beta0 == 0.0:
+        return x, 0, hist
+    total = 0
+
+    def proj(v):
+        if null_p is None:
+            return v
+        v = v.copy()
+        v[n_u:] = project_out(v[n_u:], null_p)
+        return v
+
+    r = proj(b.copy())
+    while total < maxit:
+        beta = np.linalg.norm(r)
+        V = np.zeros((restart + 1, n))
+        Z = np.zeros((restart, n))
+        H = np.zeros((restart + 1, restart))
+        V[0] = r / beta
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        j_done = 0
+        for j in range(restart):
+            Z[j] = proj(precond(V[j]))
+            w = proj(apply_K(Z[j]))
+            for _ in range(2):                      # classical Gram-Schmidt, twice
+                h = V[:j + 1] @ w
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):                     # apply previous rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            total += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= rtol * beta0 or total >= maxit:
+                break
+        yk = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        x = x + Z[:j_done].T @ yk
+        r = proj(b - apply_K(x))
+        if np.linalg.norm(r) <= rtol * beta0:
+            break
+    return x, total, hist

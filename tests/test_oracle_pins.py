@@ -1,0 +1,396 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix.
+
+None of these re-derive the oracle's own formula: they use closed forms,
+invariants, brute force, textbook values and convergence theory.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import basis, exact, krylov, materials, multigrid, rng, sip
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BCS = [("navier",) * 4, ("dirichlet",) * 4, ("navier", "navier", "navier", "neumann"),
+       ("neumann", "dirichlet", "navier", "navier")]
+
+
+def _prob(nx, ny, k, bc, seed=0, contrast=3.0, lx=1.0, ly=1.0):
+    eta = 10.0 ** np.random.default_rng(seed).uniform(0, contrast, nx * ny)
+    return sip.Problem(nx, ny, k, eta, bc=bc, lx=lx, ly=ly)
+
+
+# ---------------------------------------------------------------- basis
+def test_legendre_textbook_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "legendre_orthonormal.txt"))
+    for i, x, p in rows:
+        val, _ = basis.legendre_values(int(i), np.array([x]))
+        assert val[int(i), 0] == pytest.approx(np.sqrt((2 * i + 1) / 2) * p, rel=1e-14)
+
+
+def test_legendre_orthonormal_by_dense_trapezoid():
+    # brute-force integration on a fine grid (no Gauss rule involved)
+    x = np.linspace(-1, 1, 200001)
+    val, der = basis.legendre_values(6, x)
+    M = np.trapezoid(val[:, None, :] * val[None, :, :], x, axis=2)
+    assert np.abs(M - np.eye(7)).max() < 1e-8
+    # derivative against central differences
+    h = 1e-6
+    vp, _ = basis.legendre_values(6, x[1000:1010] + h)
+    vm, _ = basis.legendre_values(6, x[1000:1010] - h)
+    assert np.abs((vp - vm) / (2 * h) - der[:, 1000:1010]).max() < 1e-6
+
+
+# ---------------------------------------------------------------- rng
+def test_splitmix64_published_vector():
+    vals = [int(v) for v in np.loadtxt(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"),
+                                       dtype=np.uint64)]
+    got = [int(v) for v in rng.splitmix64(1234567, 3)]
+    assert got == vals
+
+
+def test_uniform_range():
+    u = rng.uniform_pm1(42, 100000)
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.01
+
+
+# ---------------------------------------------------------------- A
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_A_symmetric_positive_definite(bc, k):
+    """P1: A = A^T and A is SPD (SIP coercivity, Lemma 4.4)."""
+    pr = _prob(3, 4, k, bc, seed=k)
+    A = sip.assemble_A(pr).toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)
+    nb = pr.num.nb
+    for e in range(pr.num.ne):     # element blocks SPD (M_K of Sec. 6)
+        np.linalg.cholesky(A[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb])
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_A_closed_form_energies(k):
+    """P2: on the unit square with Navier sides and constant eta,
+    sigma_b = 8 eta (k+1)^2 / h: a((c,0),(c,0)) = 2 sigma_b c^2,
+    a((x,0),(x,0)) = sigma_b - 2 eta, a((y,0),(y,0)) = eta + 2 sigma_b / 3."""
+    nx, eta = 4, 1.7
+    pr = sip.Problem(nx, nx, k, np.full(nx * nx, eta))
+    A = sip.assemble_A(pr)
+    sb = 8 * eta * (k + 1) ** 2 * nx
+    cases = [(lambda x, y: (0.7 + 0 * x, 0 * x), 2 * sb * 0.49),
+             (lambda x, y: (x, 0 * x), sb - 2 * eta),
+             (lambda x, y: (y, 0 * x), eta + 2 * sb / 3),
+             (lambda x, y: (0 * x, x), eta + 2 * sb / 3)]
+    for f, expect in cases:
+        u = sip.project_velocity(pr, f)
+        assert u @ (A @ u) == pytest.approx(expect, rel=1e-12)
+
+
+def test_A_rigid_rotation_energy_neumann():
+    """A rigid rotation u = (-y, x) has eps(u) = 0 and no jumps, so with
+    Neumann on every side its energy is exactly 0."""
+    pr = sip.Problem(3, 3, 2, np.linspace(1, 5, 9), bc=("neumann",) * 4)
+    A = sip.assemble_A(pr)
+    u = sip.project_velocity(pr, lambda x, y: (-y, x))
+    assert abs(u @ (A @ u)) < 1e-11 * np.abs(A).max()
+
+
+def test_penalty_lower_bound_values():
+    """Lemma 4.4 at its bound with tau = 0 and Lemma 4.1 on squares."""
+    pr = sip.Problem(4, 4, 3, np.ones(16))
+    assert sip.penalty(pr, 2.0, 5.0, 0.25) == pytest.approx(4 * 5.0 * 16 / 0.25)
+    assert sip.penalty(pr, 2.0, None, 0.25) == pytest.approx(8 * 2.0 * 16 / 0.25)
+
+
+def test_element_rows_match_assembly():
+    pr = _prob(4, 3, 2, ("navier", "dirichlet", "neumann", "navier"))
+    A = sip.assemble_A(pr).toarray()
+    B = sip.assemble_B(pr).toarray()
+    nb, mp = pr.num.nb, pr.num.mp
+    for ex, ey in [(0, 0), (1, 1), (3, 2), (2, 0)]:
+        e = pr.num.elem(ex, ey)
+        row = np.zeros((nb, A.shape[1]))
+        for f, blk in sip.element_rows_A(pr, ex, ey).items():
+            row[:, f * nb:(f + 1) * nb] = blk
+        assert np.abs(row - A[e * nb:(e + 1) * nb]).max() < 1e-12 * np.abs(A).max()
+        rowb = np.zeros((nb, B.shape[1]))
+        for f, blk in sip.element_rows_B(pr, ex, ey).items():
+            rowb[:, f * mp:(f + 1) * mp] = blk
+        assert np.abs(rowb - B[e * nb:(e + 1) * nb]).max() < 1e-13
+        colb = np.zeros((mp, B.shape[0]))
+        for f, blk in sip.element_cols_B(pr, ex, ey).items():
+            colb[:, f * nb:(f + 1) * nb] = blk
+        assert np.abs(colb - B.T[e * mp:(e + 1) * mp]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- B, S*
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_B_constant_pressure_null_space(k):
+    """P3: without Neumann faces, b(u, 1) = 0 for every u, i.e. B 1 = 0;
+    with a Neumann face the constant is not in the kernel."""
+    pr = _prob(3, 3, k, ("navier", "dirichlet", "navier", "navier"))
+    B = sip.assemble_B(pr)
+    one = sip.pressure_constant(pr)
+    assert np.abs(B @ one).max() < 1e-13
+    pr2 = _prob(3, 3, k, ("navier", "navier", "navier", "neumann"))
+    assert np.abs(sip.assemble_B(pr2) @ sip.pressure_constant(pr2)).max() > 1e-3
+
+
+def test_B_divergence_of_linear_field():
+    """b(u, q) for u = (x, 0) (div u = 1) on a Neumann box equals
+    -int q (volume) + boundary-free jumps (u continuous) = -int q."""
+    pr = sip.Problem(3, 2, 2, np.ones(6), bc=("neumann",) * 4)
+    B = sip.assemble_B(pr)
+    u = sip.project_velocity(pr, lambda x, y: (x, 0 * x))
+    q = sip.project_pressure(pr, lambda x, y: 1 + x * y)
+    # int_Omega (1 + x y) = 1 + 1/4
+    assert u @ (B @ q) == pytest.approx(-(1 + 0.25), rel=1e-12)
+
+
+def test_schur_mass_diagonal():
+    """S* is diagonal for the orthonormal basis (Sec. 5): the full element
+    pressure mass block equals (h_x h_y / 4) I."""
+    pr = sip.Problem(2, 3, 4, np.ones(6), lx=1.0, ly=1.5)
+    Mb = sip.pressure_mass_block(pr, 1, 2)
+    assert np.abs(Mb - np.eye(16) * (0.5 * 0.5 / 4)).max() < 1e-15
+
+
+# ---------------------------------------------------------------- exact solutions
+@pytest.mark.parametrize("sol", [exact.SmoothNavier(2.0), exact.SmoothDirichlet(1.5),
+                                 exact.PolynomialPatch()])
+def test_exact_solutions_satisfy_pde(sol):
+    """-div(2 eta eps(u)) + grad p = f and div u = 0 by finite differences."""
+    eta = getattr(sol, "eta", 1.0)
+    rng_ = np.random.default_rng(0)
+    x, y = rng_.uniform(0.1, 0.9, 20), rng_.uniform(0.1, 0.9, 20)
+    h = 1e-4
+
+    def u(x_, y_):
+        return np.array(sol.u(x_, y_))
+
+    lap = (u(x + h, y) + u(x - h, y) + u(x, y + h) + u(x, y - h) - 4 * u(x, y)) / h ** 2
+    gp = np.array([(sol.p(x + h, y) - sol.p(x - h, y)) / (2 * h),
+                   (sol.p(x, y + h) - sol.p(x, y - h)) / (2 * h)])
+    div = ((u(x + h, y) - u(x - h, y))[0] + (u(x, y + h) - u(x, y - h))[1]) / (2 * h)
+    f = np.array(sol.f(x, y))
+    assert np.abs(-eta * lap + gp - f).max() < 1e-4 * max(1, np.abs(f).max())
+    assert np.abs(div).max() < 1e-6
+
+
+# ---------------------------------------------------------------- discretisation
+def _solve(sol, n, k, bc, eta=None):
+    eta = np.full(n * n, getattr(sol, "eta", 1.0)) if eta is None else eta
+    pr = sip.Problem(n, n, k, eta, bc=bc)
+    A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+    u, p = krylov.solve_direct(pr, A, B, sip.rhs_force(pr, sol.f))
+    return pr, u, p
+
+
+def test_patch_test_polynomial_solution_exact():
+    """P4: u in Q_4^2, p in Q_3 with Dirichlet sides: SIP consistency makes
+    the k = 4 discrete solution equal to the exact one."""
+    sol = exact.PolynomialPatch()
+    pr, u, p = _solve(sol, 3, 4, ("dirichlet",) * 4)
+    eu, ep = sip.l2_errors(pr, u, p, sol.u, sol.p)
+    assert eu < 1e-12 and ep < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_convergence_rates_smooth_navier(k):
+    """P5: ||e_u|| ~ h^(k+1), ||e_p|| ~ h^k (a-priori estimates, Sec. 4.2;
+    the paper's table shows 3.00 / 2.02 for k = 2)."""
+    sol = exact.SmoothNavier(1.0)
+    e = []
+    for n in (4, 8):
+        pr, u, p = _solve(sol, n, k, ("navier",) * 4)
+        e.append(sip.l2_errors(pr, u, p, sol.u, sol.p))
+    ru = np.log2(e[0][0] / e[1][0])
+    rp = np.log2(e[0][1] / e[1][1])
+    assert ru > k + 1 - 0.15
+    assert rp > k - 0.15
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_convergence_rates_viscosity_jump(k):
+    """P5 with a mesh-aligned viscosity jump of 1e3 (pressure discontinuous)."""
+    sol = exact.JumpNavier(1e3, 1.0, 0.25)
+    e = []
+    for n in (8, 16):
+        pr = sip.Problem(n, n, k, sol.eta_elements(n, n))
+        A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+        u, p = krylov.solve_direct(pr, A, B, sip.rhs_force(pr, sol.f))
+        e.append(sip.l2_errors(pr, u, p, sol.u, sol.p))
+    assert np.log2(e[0][0] / e[1][0]) > k + 1 - 0.15
+    assert np.log2(e[0][1] / e[1][1]) > k - 0.15
+
+
+def test_dirichlet_rates():
+    sol = exact.SmoothDirichlet(1.0)
+    e = []
+    for n in (4, 8):
+        pr, u, p = _solve(sol, n, 2, ("dirichlet",) * 4)
+        e.append(sip.l2_errors(pr, u, p, sol.u, sol.p))
+    assert np.log2(e[0][0] / e[1][0]) > 2.85
+
+
+def test_body_force_load_vector():
+    """f(v) for f = (0, -g rho): only the (0,0) mode of v_y sees it, with
+    int phi_00 = |K| / 2 on the orthonormal basis."""
+    pr = sip.Problem(2, 2, 2, np.ones(4))
+    rho = np.array([1.0, 2.0, 3.0, 4.0])
+    f = sip.rhs_body_force(pr, rho, g=10.0)
+    F = f.reshape(4, 2, 3, 3)
+    assert np.allclose(F[:, 1, 0, 0], -10 * rho * 0.25 / 2, rtol=1e-14)
+    F[:, 1, 0, 0] = 0
+    assert np.abs(F).max() < 1e-14
+
+
+# ---------------------------------------------------------------- materials
+def test_rasterise_brute_force():
+    """eta = max over the open cell, rho = min over the cell, by dense
+    point sampling of the cell (brute force)."""
+    shapes = np.array([[0, 0.3, 0.4, 0.17, 0, 50.0, 1.5],
+                       [0, 0.7, 0.7, 0.12, 0, 7.0, 1.2],
+                       [1, 0.5, 0.77, 0.05, 0.31, 3.0, 1.1]])
+    nx, ny = 12, 10
+    eta, rho = materials.rasterise_inclusions(nx, ny, shapes)
+    s = np.linspace(0, 1, 41)[1:-1]
+    for e in range(nx * ny):
+        ex, ey = e % nx, e // nx
+        X, Y = np.meshgrid((ex + s) / nx, (ey + s) / ny)
+        X, Y = X.ravel(), Y.ravel()
+        et = np.ones_like(X)
+        rh_in = []
+        for kind, a, b, c, d, ei, ri in shapes:
+            if kind == 0:
+                ins = (X - a) ** 2 + (Y - b) ** 2 <= c ** 2
+            else:
+                ins = (X >= a) & (X <= b) & (Y >= c) & (Y <= d)
+            et = np.where(ins, np.maximum(et, ei), et)
+            rh_in.append(ri if ins.all() else 1.0)
+        assert eta[e] == et.max(), e
+        assert rho[e] == max(rh_in), e
+
+
+def test_rasterise_mesh_aligned_box():
+    eta, rho = materials.rasterise_inclusions(8, 8, [[1, 0.25, 0.75, 0.25, 0.75, 1e4, 1.2]])
+    E = eta.reshape(8, 8)
+    assert (E[2:6, 2:6] == 1e4).all() and E.sum() == 16 * 1e4 + 48
+
+
+# ---------------------------------------------------------------- multigrid
+def test_chebyshev_closed_form():
+    """P8: on diag(lam) with M = I the Chebyshev error after m steps from
+    x0 = 0 is T_m((theta - lam)/delta) / T_m(theta/delta) times the initial
+    error (Chebyshev polynomial closed form)."""
+    lam = np.linspace(0.2, 2.0, 30)
+    b = np.ones(30)
+    lo, hi = 0.1, 2.2
+    th, de = (hi + lo) / 2, (hi - lo) / 2
+    for m in (1, 2, 3, 5):
+        x = multigrid.chebyshev(lambda v: lam * v, lambda v: v, b, None, m, lo, hi)
+        err = x - b / lam
+        T = np.polynomial.chebyshev.Chebyshev.basis(m)
+        expect = T((th - lam) / de) / T(th / de) * (-b / lam)
+        assert np.abs(err - expect).max() < 1e-13
+
+
+def test_lambda_estimate_close_to_dense():
+    """P10: 10 Arnoldi steps estimate lambda_max(M^{-1}A) within 5 %."""
+    pr = _prob(6, 6, 2, ("navier", "navier", "navier", "neumann"), seed=3, contrast=2.0)
+    A = sip.assemble_A(pr)
+    blocks = multigrid.block_jacobi_blocks(A, pr.num.nb)
+    inv = multigrid.invert_blocks(blocks)
+    est = multigrid.estimate_lambda_max(lambda v: A @ v, lambda v: multigrid.block_apply(inv, v),
+                                        A.shape[0], seed=11)
+    Ad = A.toarray()
+    Minv = np.zeros_like(Ad)
+    nb = pr.num.nb
+    for e in range(pr.num.ne):
+        Minv[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb] = inv[e]
+    true = np.max(np.linalg.eigvals(Minv @ Ad).real)
+    assert abs(est - true) / true < 0.05
+    assert est <= true * (1 + 1e-10)
+
+
+def test_galerkin_A1_is_order1_sip_with_fine_penalty():
+    """P6: A_1 = P^T A P equals the order-1 SIP matrix assembled with the
+    fine-degree trace constant (hierarchical basis, Sec. 6)."""
+    pr = _prob(3, 3, 3, ("navier", "neumann", "dirichlet", "navier"), seed=5)
+    A = sip.assemble_A(pr)
+    P = multigrid.p_prolongation(3, pr.num.ne, 1)
+    A1 = (P.T @ A @ P).toarray()
+    pr1 = sip.Problem(3, 3, 1, pr.eta, bc=pr.bc, k_penalty=3)
+    A1d = sip.assemble_A(pr1).toarray()
+    assert np.abs(A1 - A1d).max() < 1e-12 * np.abs(A1).max()
+
+
+def test_pcd_reproduces_bilinears():
+    """P7: P_cd maps vertex values of a global bilinear to its exact modal
+    Q_1 coefficients; P_h interpolates bilinears exactly."""
+    nx, ny = 4, 3
+    f = lambda x, y: (1 + 2 * x - y + 3 * x * y, -1 + x * y)
+    vx, vy = np.meshgrid(np.arange(nx + 1) / nx, np.arange(ny + 1) / ny)
+    fx, fy = f(vx.ravel(), vy.ravel())
+    vert = np.stack([fx, fy], 1).ravel()
+    Pcd = multigrid.continuous_to_dg(nx, ny)
+    pr1 = sip.Problem(nx, ny, 1, np.ones(nx * ny))
+    ref = sip.project_velocity(pr1, f)
+    assert np.abs(Pcd @ vert - ref).max() < 1e-13
+    P = multigrid.bilinear_prolongation(2, 3)
+    cx, cy = np.meshgrid(np.arange(3) / 2, np.arange(4) / 3)
+    fine_x, fine_y = np.meshgrid(np.arange(5) / 4, np.arange(7) / 6)
+    g = lambda x, y: 2 - x + 4 * y + x * y
+    coarse = np.stack([g(cx.ravel(), cy.ravel()), -g(cx.ravel(), cy.ravel())], 1).ravel()
+    fine = np.stack([g(fine_x.ravel(), fine_y.ravel()), -g(fine_x.ravel(), fine_y.ravel())], 1).ravel()
+    assert np.abs(P @ coarse - fine).max() < 1e-14
+
+
+@pytest.mark.parametrize("nh", [0, 1])
+def test_vcycle_symmetric(nh):
+    """P11: the V-cycle is a symmetric operator, so PCG is legitimate."""
+    pr = _prob(8, 8, 2, ("navier", "navier", "navier", "neumann"), seed=2, contrast=2.0)
+    A = sip.assemble_A(pr)
+    mg = multigrid.HPMultigrid(pr, A, nh, seed=9)
+    g = np.random.default_rng(1)
+    x, y = g.standard_normal(A.shape[0]), g.standard_normal(A.shape[0])
+    assert abs(mg(x) @ y - x @ mg(y)) < 1e-11 * abs(x @ mg(y))
+
+
+def test_exact_block_preconditioner_two_iterations():
+    """P9: with exact A^{-1} and the exact Schur complement the upper block
+    triangular preconditioner gives convergence in at most 2 iterations."""
+    pr = _prob(3, 3, 2, ("navier", "navier", "navier", "neumann"), seed=4)
+    A, B = sip.assemble_A(pr).toarray(), sip.assemble_B(pr).toarray()
+    Ainv = np.linalg.inv(A)
+    S = B.T @ Ainv @ B
+    Sinv = np.linalg.inv(S)
+    n_u = A.shape[0]
+    K = np.block([[A, B], [B.T, np.zeros((B.shape[1],) * 2)]])
+    b = np.random.default_rng(0).standard_normal(K.shape[0])
+
+    def prec(x):
+        yp = Sinv @ x[n_u:]
+        return np.concatenate([Ainv @ (x[:n_u] - B @ yp), yp])
+
+    x, its, hist = krylov.fgmres(lambda v: K @ v, prec, b, 1e-10)
+    assert its <= 3
+    assert np.linalg.norm(b - K @ x) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_fgmres_hpmg_solves_to_direct_solution():
+    """The oracle's block-preconditioned FGMRES with the two-level A_p(Q_1)
+    preconditioner reaches the sparse-direct solution (config 1 shape)."""
+    sol = exact.SmoothDirichlet()
+    pr = sip.Problem(8, 8, 2, np.ones(64), bc=("dirichlet",) * 4)
+    A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+    f = sip.rhs_force(pr, sol.f)
+    mg = multigrid.HPMultigrid(pr, A, 0, seed=7)
+    null = sip.pressure_constant(pr)
+    Pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3, null_p=null)
+    K = krylov.stokes_matrix(A, B)
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    x, its, _ = krylov.fgmres(lambda v: K @ v, Pc, b, 1e-10, null_p=null, n_u=A.shape[0])
+    u, p = krylov.solve_direct(pr, A, B, f)
+    assert np.linalg.norm(b - K @ x) <= 1e-10 * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(x[:A.shape[0]] - u) <= 1e-8 * np.linalg.norm(u)
