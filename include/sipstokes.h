@@ -1,0 +1,147 @@
+/*
+ * sipstokes.h -- C ABI of a GB300 (sm_103a) library for the symmetric interior
+ * penalty discontinuous Galerkin (SIP-DG) discretisation of heterogeneous
+ * 2D Stokes flow and its block / hp-multigrid preconditioned Krylov solver,
+ * after Charrier, May & Schnepp, arXiv 1607.03777.
+ *
+ * Discretisation (paper Sec. 3-4): a regular nx x ny Cartesian grid of
+ * [0,lx] x [0,ly]; velocity in discontinuous Q_k^2, pressure in
+ * discontinuous Q_{k-1}, 1 <= k <= 6; element-wise constant viscosity eta_K
+ * (assumption ASh1).  Basis: tensor products of orthonormal Legendre
+ * polynomials l_i = sqrt((2i+1)/2) P_i on the reference square (Sec. 5).
+ *
+ * Vector layouts (all FP64 unless the name ends in _f32):
+ *   velocity  u[e][c][j][i]  e = ey*nx + ex, c = component (x, y),
+ *                            i = x-degree (fastest), j = y-degree, 0..k
+ *                            -> n_u = nx*ny*2*(k+1)^2 entries
+ *   pressure  p[e][j][i]     0 <= i, j < k  -> n_p = nx*ny*k^2 entries
+ *   Q_1 (p-coarse) vectors   u1[e][c][j][i], i, j in {0, 1} -> 8 per element
+ *   continuous bilinear      v[(vy*(nx+1)+vx)][c] -> 2 (nx+1)(ny+1) entries
+ *
+ * Conventions:
+ *   - Vector arguments are caller-owned DEVICE pointers on the problem's
+ *     device, 8-byte (FP64) / 4-byte (FP32) aligned, and must not overlap
+ *     unless stated.  Host arrays are named *_host.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous with respect to the host unless they return a host value.
+ *   - Every call returns a sip_status; on failure a message is available from
+ *     sip_last_error() on the owning context.  No C++ exception crosses the ABI.
+ *   - Handles are opaque, created and destroyed by the library.
+ */
+#ifndef SIPSTOKES_H
+#define SIPSTOKES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIP_OK = 0,
+    SIP_ERR_INVALID_ARG = 1,   /* bad size, k, eta <= 0, non-finite input ... */
+    SIP_ERR_OOM = 2,           /* device allocation failed / over budget      */
+    SIP_ERR_CUDA = 3,          /* a CUDA runtime call failed                  */
+    SIP_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance  */
+    SIP_ERR_BREAKDOWN = 5,     /* Krylov breakdown or non-finite iterate      */
+    SIP_ERR_TIMEOUT = 6,       /* a served request passed its deadline        */
+    SIP_ERR_REJECTED = 7,      /* server admission refused the request        */
+    SIP_ERR_NOT_READY = 8      /* result not available yet                    */
+} sip_status;
+
+/* Boundary condition of one side of the rectangle (Sec. 2, eqs.
+ * neumann_bc / navier_dirichlet_bc).  SIP_BC_DIRICHLET (u = 0, imposed by
+ * the symmetric Nitsche analogue of the Navier terms) is an extension that
+ * the paper does not use. */
+typedef enum { SIP_BC_NAVIER = 0, SIP_BC_NEUMANN = 1, SIP_BC_DIRICHLET = 2 } sip_bc;
+
+/* Precision of the viscous preconditioner (smoother, transfers, coarse
+ * solve and inner Krylov).  The outer FGMRES, its residual, B, B^T and the
+ * S* scaling are always FP64. */
+typedef enum { SIP_PREC_FP64 = 0, SIP_PREC_MIXED = 1 } sip_precision;
+
+typedef struct sip_ctx sip_ctx;
+typedef struct sip_problem sip_problem;
+
+typedef struct {
+    int nx, ny;             /* elements per direction, >= 1                     */
+    double lx, ly;          /* domain size, > 0                                 */
+    int k;                  /* velocity degree 1..6 (pressure k-1)              */
+    int bc[4];              /* sip_bc of the left, right, bottom, top side      */
+    const double* eta_host; /* nx*ny element viscosities, > 0, copied           */
+    double penalty_scale;   /* multiplies sigma_e; 1.0 = the paper's choice     */
+    /* hp-multigrid (Sec. 6): coarse space Q^2_1 then n_hlevels coarsenings of
+     * the continuous bilinear problem; 0 = A_p(Q^2_1) (LU of A_1). */
+    int n_hlevels;
+    int cheb_steps_p;       /* Chebyshev / block-Jacobi steps per side, paper 2 */
+    int cheb_steps_h;       /* Chebyshev / point-Jacobi steps on h-levels, 3    */
+    int eig_iters;          /* GMRES steps of the eigen estimate, paper 10      */
+    double cheb_lo, cheb_hi;/* bound factors, paper 0.1 and 1.1                 */
+    uint64_t seed;          /* SplitMix64 stream of the eigen-estimate vector   */
+    sip_precision precision;
+} sip_problem_desc;
+
+/* Fill a descriptor with the paper's defaults (Sec. 6-7): Navier on every
+ * side, penalty_scale 1, n_hlevels 0, 2 p-level and 3 h-level smoothing
+ * steps, 10 eigen-estimate iterations, bounds 0.1 / 1.1, seed 0, FP64. */
+void sip_problem_desc_default(sip_problem_desc* desc);
+
+/* ---- context ------------------------------------------------------------ */
+/* Create a context bound to CUDA device `device`. */
+sip_status sip_ctx_create(int device, sip_ctx** out);
+void sip_ctx_destroy(sip_ctx* ctx);
+/* Message of the last failing call made through ctx (or one of its
+ * problems); valid until the next call on ctx.  Never NULL. */
+const char* sip_last_error(const sip_ctx* ctx);
+
+/* ---- problem ------------------------------------------------------------ */
+/* Create a problem: copies eta, derives the element-wise penalties and
+ * allocates the device state.  The multigrid set-up runs on first use (or
+ * through sip_problem_setup).  Errors: INVALID_ARG (nx, ny < 1, k outside
+ * 1..6, non-positive or non-finite eta / lengths, a mesh that cannot be
+ * coarsened n_hlevels times), OOM, CUDA. */
+sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* desc, sip_problem** out);
+void sip_problem_destroy(sip_problem* prob);
+/* Number of velocity and pressure dofs and the device bytes held. */
+sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p,
+                             int64_t* device_bytes);
+
+/* ---- operators (paper Sec. 4) ------------------------------------------- */
+/* y_u = A x_u: the SIP viscous operator, eq. stiffness_form -- volume term
+ * 2 eta eps(u):eps(v), interior-face consistency, symmetry and penalty
+ * terms, Navier-face terms -- applied matrix-free (closed-form 1D modal
+ * factors, no assembled matrix).  sigma_e = penalty_scale * 4 eta_e
+ * (k+1)^2 |e|/|K| x {1 interior, 2 boundary} (Lemma 4.4 with tau = 0,
+ * Lemma 4.1, eq. eta_face).  x_u and y_u must not overlap. */
+sip_status sip_apply_A(sip_problem* prob, const double* x_u, double* y_u, void* stream);
+/* The same operator in FP32 arithmetic (inputs and outputs FP32). */
+sip_status sip_apply_A_f32(sip_problem* prob, const float* x_u, float* y_u, void* stream);
+/* y_u = B p: (B p)_v = b_h(v, p), eq. divergence_form.  x_p: n_p, y_u: n_u. */
+sip_status sip_apply_B(sip_problem* prob, const double* x_p, double* y_u, void* stream);
+/* y_p = B^T u: (B^T u)_q = b_h(u, q).  x_u: n_u, y_p: n_p. */
+sip_status sip_apply_Bt(sip_problem* prob, const double* x_u, double* y_p, void* stream);
+
+/* ---- set-up helpers (paper Sec. 7.3) -------------------------------------- */
+/* Element-wise material of inclusions (Sec. 7.3): eta_K = max of eta over
+ * the open element, rho_K = min of rho, where eta(x) = max(eta_bg, eta_i over
+ * the closed inclusions containing x); an element takes an inclusion's
+ * density only when it lies inside that single inclusion.
+ * shapes_host: n_shapes records of 7 doubles (kind, a, b, c, d, eta_i, rho_i):
+ *   kind 0 = disc, centre (a, b), radius c (d unused);
+ *   kind 1 = box [a, b] x [c, d];
+ * with eta_i >= eta_bg and rho_i >= rho_bg.  eta_out, rho_out: device arrays
+ * of nx*ny.  Synchronises `stream` before returning. */
+sip_status sip_rasterise_inclusions(sip_ctx* ctx, int nx, int ny, double lx, double ly,
+                                    const double* shapes_host, int n_shapes, double eta_bg,
+                                    double rho_bg, double* eta_out, double* rho_out,
+                                    void* stream);
+/* f_u = the load vector of the body force f = (0, -g rho_K) (eq. rhs_f,
+ * Sec. 7.3); rho: device array of nx*ny. */
+sip_status sip_rhs_body_force(sip_problem* prob, const double* rho, double g, double* f_u,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIPSTOKES_H */

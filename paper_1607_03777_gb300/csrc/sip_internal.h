@@ -1,0 +1,161 @@
+// Internal declarations shared by the CUDA translation units of the
+// SIP-DG Stokes library.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/sipstokes.h"
+
+namespace sip {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+    sip_status status;
+    Error(sip_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define SIP_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::sip::Error(SIP_ERR_CUDA, std::string(#call) + ": " +            \
+                                                 cudaGetErrorString(e_));           \
+    } while (0)
+
+#define SIP_CHECK_LAUNCH() SIP_CUDA(cudaGetLastError())
+
+inline void require(bool ok, const std::string& msg) {
+    if (!ok) throw Error(SIP_ERR_INVALID_ARG, msg);
+}
+
+// ------------------------------------------------------------ 1D tables
+// Orthonormal Legendre l_i = sqrt((2i+1)/2) P_i on [-1, 1] (Sec. 5 basis).
+// Closed forms of the classical Legendre facts used:
+//   P_i(1) = 1, P_i(-1) = (-1)^i, P_i'(1) = i(i+1)/2, P_i'(-1) = (-1)^(i+1) i(i+1)/2
+//   P_q' = sum_{p<q, q-p odd} (2p+1) P_p       => int P_p P_q' = 2 for those p
+//   int P_a' P_b' = m(m+1), m = min(a,b), when a+b is even (0 otherwise)
+// G[a][b] = int l_a' l_b',  D[p][q] = int l_p l_q'.
+template <int N, typename T>
+struct Tab1D {
+    T lp[N], lm[N];   // l_i(+1), l_i(-1)
+    T dp[N], dm[N];   // l_i'(+1), l_i'(-1)
+    T G[N * N];
+    T D[N * N];
+};
+
+template <int N, typename T>
+Tab1D<N, T> make_tab() {
+    Tab1D<N, T> t;
+    for (int i = 0; i < N; ++i) {
+        double c = std::sqrt((2.0 * i + 1.0) / 2.0);
+        double sgn = (i % 2 == 0) ? 1.0 : -1.0;
+        t.lp[i] = T(c);
+        t.lm[i] = T(sgn * c);
+        t.dp[i] = T(c * i * (i + 1) / 2.0);
+        t.dm[i] = T(-sgn * c * i * (i + 1) / 2.0);
+    }
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            double ca = std::sqrt((2.0 * a + 1.0) / 2.0), cb = std::sqrt((2.0 * b + 1.0) / 2.0);
+            int m = a < b ? a : b;
+            double g = ((a + b) % 2 == 0 && m >= 1) ? double(m) * (m + 1) : 0.0;
+            t.G[a * N + b] = T(ca * cb * g);
+            double d = (b > a && (b - a) % 2 == 1) ? 2.0 : 0.0;
+            t.D[a * N + b] = T(ca * cb * d);
+        }
+    return t;
+}
+
+// ------------------------------------------------------------ operator
+// Geometry and penalty of one SIP operator on the grid.  pen_x / pen_y are
+// sigma_e / eta_e for an interior face with x- / y-normal:
+// penalty_scale * n_f (1+tau) (k_pen+1)^2 |e|/|K| with n_f = 4, tau = 0 and
+// |e|/|K| = 1/h_normal; boundary faces double it (eq. sipg_penalty).
+struct OpGeom {
+    int nx, ny;
+    double hx, hy;
+    int bc[4];
+    double pen_x, pen_y;
+};
+
+inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], int k_pen,
+                        double penalty_scale) {
+    OpGeom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.hx = lx / nx;
+    g.hy = ly / ny;
+    for (int i = 0; i < 4; ++i) g.bc[i] = bc[i];
+    double c = penalty_scale * 4.0 * double(k_pen + 1) * double(k_pen + 1);
+    g.pen_x = c / g.hx;
+    g.pen_y = c / g.hy;
+    return g;
+}
+
+// y = alpha * (A x) + beta * z (z may be null).  N = polynomial degree + 1
+// of the space the operator acts on (N = 2 for the Galerkin A_1).
+template <typename T>
+void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
+                      const T* z, T beta, cudaStream_t s);
+template <typename T>
+void launch_apply_B(int k, const OpGeom& g, const T* p, T* y, cudaStream_t s);
+template <typename T>
+void launch_apply_Bt(int k, const OpGeom& g, const T* u, T* y, cudaStream_t s);
+void launch_rhs_body_force(int k, const OpGeom& g, const double* rho, double grav, double* f,
+                           cudaStream_t s);
+void launch_rasterise(int nx, int ny, double lx, double ly, const double* shapes, int ns,
+                      double eta_bg, double rho_bg, double* eta, double* rho, cudaStream_t s);
+
+// ---------------------------------------------------------- device memory
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    DeviceBuffer() = default;
+    DeviceBuffer(const DeviceBuffer&) = delete;
+    DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+    ~DeviceBuffer() {
+        if (ptr) cudaFree(ptr);
+    }
+    void alloc(size_t b) {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (b == 0) return;
+        cudaError_t e = cudaMalloc(&ptr, b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+            throw Error(SIP_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed");
+        }
+        bytes = b;
+    }
+    template <typename T>
+    T* as() const {
+        return static_cast<T*>(ptr);
+    }
+};
+
+}  // namespace sip
+
+struct sip_ctx {
+    int device = 0;
+    std::string err;
+};
+
+struct sip_problem {
+    sip_ctx* ctx = nullptr;
+    sip_problem_desc desc{};
+    int k = 0, n = 0, nb = 0, mp = 0;
+    int64_t ne = 0, n_u = 0, n_p = 0;
+    sip::OpGeom geom{};      // the SIP operator of degree k
+    sip::OpGeom geom1{};     // the Galerkin Q_1 operator (fine-k penalty)
+    std::vector<double> eta_host;
+    sip::DeviceBuffer eta_d, eta_f;
+    int64_t device_bytes() const;
+};
