@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the SIP-DG Stokes solver library on one GB300.
+
+Metric: Stokes solves per second to a 1e-8 relative residual on the
+single-inclusion workload (128 x 128 elements, k = 3, a square inclusion of
+viscosity 1e4 and density 1.2 in a unit medium, Neumann top / Navier
+elsewhere, Q^2_1 coarse space + 3 h-coarsenings, 2+2 element-block-Jacobi /
+Chebyshev steps), FP64 form; the mixed-precision form, the SIP-apply
+bandwidth and the p50/p99 step latency are reported beside it.
+
+One step = a complete solve of a fresh viscosity field: copy of eta, the
+whole multigrid set-up (block-Jacobi inverses, eigenvalue estimates,
+Galerkin coarse operators, coarsest inverse), the load vector and the
+block-preconditioned FGMRES solve, with every input resident in HBM.  L2 is
+flushed (a 256 MB write) before every timed step.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+Under torchrun (N > 1) every rank solves its own instance (replicas,
+weak scaling); rank 0 prints the JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stokes_solves_per_s_to_1e-8_residual"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+def algorithmic_apply(prob_k, ne, word):
+    """Algorithmic bytes and flops of one SIP apply: read x, write y, read
+    eta_K per element; flops of the closed-form modal apply (volume
+    sum-factorisation 8 n^3 FMA + face traces / vectors ~56 n^2 FMA)."""
+    n = prob_k + 1
+    nb = 2 * n * n
+    bytes_ = ne * (2 * nb * word + word)
+    flops = ne * 2 * (8 * n ** 3 + 56 * n * n)
+    return bytes_, flops
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+
+    dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
+    torch.cuda.set_device(dev)
+    ctx = api.Context(dev.index)
+    wl = synth.single_box_inclusion()
+    n, k = wl.nx, wl.k
+    eta_d, rho_d = ctx.rasterise_inclusions(n, n, wl.shapes)
+    eta_h = eta_d.cpu().numpy()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        prob = api.Problem(ctx, n, n, k, eta_h, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
+                           precision=precision)
+        f = torch.empty(prob.n_u, dtype=torch.float64, device=dev)
+        u = torch.empty_like(f)
+        p = torch.empty(prob.n_p, dtype=torch.float64, device=dev)
+        return prob, f, u, p
+
+    def step(prob, f, u, p):
+        prob.update_eta(eta_d)
+        prob.rhs_body_force(rho_d, synth.GRAVITY, f)
+        return prob.solve(f, u, p, rtol=wl.rtol, inner_rtol=args.inner_rtol, max_outer=1000)
+
+    def timed(precision, steps, warmup, clocks=None):
+        prob, f, u, p = make(precision)
+        for _ in range(warmup):
+            step(prob, f, u, p)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        times, reps = [], []
+        if clocks:
+            clocks.start()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reps.append(step(prob, f, u, p))
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        clocks_out = clocks.stop() if clocks else None
+        torch.cuda.synchronize()
+        return prob, f, u, p, times, reps, clocks_out
+
+    clocks = ClockSampler(dev.index)
+    prob64, f64, u64, p64, t64, r64, clk = timed("fp64", args.steps, args.warmup, clocks)
+    total_ms = sum(t64)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # mixed-precision form on the same workload
+    prob32, f32, u32, p32, t32, r32, _ = timed("mixed", args.steps, max(1, args.warmup - 1))
+    err_mixed = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
+
+    # end to end through the public API with host buffers (pinned)
+    eta_pin = torch.from_numpy(eta_h).pin_memory()
+    rho_pin = rho_d.cpu().pin_memory()
+    u_pin = torch.empty(prob64.n_u, dtype=torch.float64).pin_memory()
+    p_pin = torch.empty(prob64.n_p, dtype=torch.float64).pin_memory()
+    eta_dd = torch.empty_like(eta_d)
+    rho_dd = torch.empty_like(rho_d)
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eta_dd.copy_(eta_pin, non_blocking=True)
+        rho_dd.copy_(rho_pin, non_blocking=True)
+        prob64.update_eta(eta_dd)
+        prob64.rhs_body_force(rho_dd, synth.GRAVITY, f64)
+        prob64.solve(f64, u64, p64, rtol=wl.rtol, inner_rtol=args.inner_rtol, max_outer=1000)
+        u_pin.copy_(u64, non_blocking=True)
+        p_pin.copy_(p64, non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+    e2e_value = world * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
+
+    # live timing of the dominant kernel: the FP64 SIP apply, on this stream
+    x = torch.randn(prob64.n_u, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        prob64.apply_A(x, y)
+    reps_apply = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps_apply):
+        prob64.apply_A(x, y)
+    e1.record(stream)
+    e1.synchronize()
+    apply_ms = e0.elapsed_time(e1) / reps_apply
+    ab, af = algorithmic_apply(k, n * n, 8)
+
+    launches = sum(r["kernel_launches"] for r in r64)
+    lat = sorted(t64)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "single_box_inclusion_128x128_k3_eta1e4_Q1+3h",
+                   "nx": n, "ny": n, "k": k, "n_hlevels": wl.n_hlevels, "rtol": wl.rtol,
+                   "inner_rtol": args.inner_rtol, "precision": "fp64",
+                   "step": "eta copy + multigrid set-up + load vector + FGMRES solve",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "solve_report": {key: r64[-1][key] for key in ("outer_its", "inner_avg", "inner_max",
+                                                       "rel_residual", "setup_ms", "solve_ms")},
+        "mixed": {"value": world * args.steps / (sum(t32) / 1000.0), "unit": UNIT,
+                  "ms_per_step": sum(t32) / args.steps,
+                  "rel_residual": r32[-1]["rel_residual"], "outer_its": r32[-1]["outer_its"],
+                  "inner_avg": r32[-1]["inner_avg"], "u_rel_diff_vs_fp64": err_mixed},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(eta_h.nbytes + rho_pin.numel() * 8),
+                "d2h_bytes_per_step": int((prob64.n_u + prob64.n_p) * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "sip_apply": {"kernel": "k_apply_sip<N=4,double>", "ms": apply_ms,
+                      "GB_per_s": ab / apply_ms / 1e6, "GFLOP_per_s": af / apply_ms / 1e6,
+                      "dof_per_s": prob64.n_u / (apply_ms / 1e3)},
+    }
+    out["roofline"] = roofline(out, ab, af, apply_ms)
+    return out
+
+
+def roofline(out, ab, af, apply_ms):
+    """FP64 on GB300 is bound by the FP64 pipe, not HBM: achieved FP64
+    FLOP/s of the SIP apply against the FP64 peak derived in the design doc."""
+    fp64_peak_tflops = float(os.environ.get("SIP_FP64_PEAK_TFLOPS", "1.25"))
+    achieved = af / apply_ms / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("k_apply_sip_fp64_128x128_k3")
+        except (ValueError, OSError):
+            traffic = None
+    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+            "kernel": "k_apply_sip<N=4,double>", "algorithmic_bytes": ab,
+            "hbm_GB_per_s": ab / apply_ms / 1e6}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(seconds_hint=20.0):
+    """Time the FP64 oracle on a bounded sample of the workload: the same
+    physics (box inclusion 1e4, k = 3, Q^2_1 + h-levels, rtol 1e-8) on a
+    16 x 16 mesh, scaled by the element count (128^2 / 16^2 = 64) to an
+    estimate for the full workload (the solver is O(n) per iteration)."""
+    import numpy as np
+    from oracle import krylov, materials, multigrid, sip
+    from paper_1607_03777_gb300 import synth
+    n = 16
+    wl = synth.single_box_inclusion(n=n, n_hlevels=0)
+    eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
+    t0 = time.perf_counter()
+    pr = sip.Problem(n, n, wl.k, eta, bc=wl.bc)
+    A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+    f = sip.rhs_body_force(pr, rho)
+    mg = multigrid.HPMultigrid(pr, A, 1, seed=1)
+    Pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3)
+    K = krylov.stokes_matrix(A, B)
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    x, its, _ = krylov.fgmres(lambda v: K @ v, Pc, b, 1e-8, maxit=1000)
+    dt = time.perf_counter() - t0
+    scale = (128 * 128) / (n * n)
+    return dt, scale, its
+
+
+def run_reference(args):
+    per = []
+    for i in range(args.warmup + args.steps):
+        dt, scale, its = oracle_sample()
+        if i >= args.warmup:
+            per.append(dt * scale)
+    value = len(per) / sum(per)
+    cores = 1
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(per) / len(per), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "single_box_inclusion_128x128_k3_eta1e4_Q1+3h"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "16x16 mesh of the same physics per step, time x 64 "
+                                       "(element-count ratio)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline():
+    dt, scale, its = oracle_sample()
+    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle solve of the same physics on a 16x16 mesh ({dt:.1f} s, "
+                      f"{its} outer its), time x {scale:.0f} (element-count ratio); "
+                      "SciPy sparse kernels, single-threaded"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_ours(args, local, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

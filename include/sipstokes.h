@@ -103,6 +103,10 @@ const char* sip_last_error(const sip_ctx* ctx);
  * coarsened n_hlevels times), OOM, CUDA. */
 sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* desc, sip_problem** out);
 void sip_problem_destroy(sip_problem* prob);
+/* Replace the element viscosities (host or device array of nx*ny, finite and
+ * positive) and mark the multigrid set-up stale: the next call that needs it
+ * rebuilds it in the buffers already held (no new device allocation). */
+sip_status sip_problem_update_eta(sip_problem* prob, const double* eta, void* stream);
 /* Number of velocity and pressure dofs and the device bytes held. */
 sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p,
                              int64_t* device_bytes);
@@ -121,6 +125,98 @@ sip_status sip_apply_A_f32(sip_problem* prob, const float* x_u, float* y_u, void
 sip_status sip_apply_B(sip_problem* prob, const double* x_p, double* y_u, void* stream);
 /* y_p = B^T u: (B^T u)_q = b_h(u, q).  x_u: n_u, y_p: n_p. */
 sip_status sip_apply_Bt(sip_problem* prob, const double* x_u, double* y_p, void* stream);
+
+/* ---- hp-multigrid pieces (paper Sec. 6) ------------------------------------
+ * The multigrid set-up runs once per problem, on the device, on first use or
+ * here: element-block Jacobi inverses (FP64 factorisation), eigenvalue
+ * estimates, Galerkin coarse operators and the coarsest-level inverse.
+ * The entry points below act on FP64 vectors with the FP64 hierarchy
+ * (built on demand also for SIP_PREC_MIXED problems). */
+sip_status sip_problem_setup(sip_problem* prob, void* stream);
+/* Largest eigenvalue estimate lambda* of the smoother's preconditioned
+ * operator: level -1 = p-level M^{-1}A (element-block Jacobi), level l >= 0 =
+ * continuous level l (point-Jacobi D^{-1}A_l); from eig_iters GMRES (Arnoldi)
+ * steps started from the SplitMix64 vector of stream seed (p-level) or
+ * seed + 1 + l (h-level l); the Chebyshev interval is [cheb_lo, cheb_hi] x
+ * lambda* (Sec. 6).  Synchronous. */
+sip_status sip_lambda_max(sip_problem* prob, int level, double* out);
+/* z_u = M^{-1} r_u, M = the diagonal element blocks of A (Sec. 6, eq. smoother). */
+sip_status sip_block_jacobi(sip_problem* prob, const double* r_u, double* z_u, void* stream);
+/* r1 = R r_u = P^T r_u: keep the hierarchical modes i, j <= 1 (Sec. 6). */
+sip_status sip_p_restrict(sip_problem* prob, const double* r_u, double* r1, void* stream);
+/* y_u += P e1: inject Q_1 modes into Q_k (zero fill of the rest). */
+sip_status sip_p_prolong_add(sip_problem* prob, const double* e1, double* y_u, void* stream);
+/* y1 = A_1 x1, A_1 = P^T A P: the SIP operator on the Q_1 modes with the
+ * penalty of degree k (Sec. 6 Galerkin coarse operator). */
+sip_status sip_apply_A1(sip_problem* prob, const double* x1, double* y1, void* stream);
+/* u1 = P_cd v: continuous bilinear vertex values -> element modal Q_1
+ * coefficients (Sec. 6.1.2); v has 2 (nx+1)(ny+1) entries. */
+sip_status sip_cd_prolong(sip_problem* prob, const double* v, double* u1, void* stream);
+/* v = R_dc u1 = P_cd^T u1. */
+sip_status sip_dc_restrict(sip_problem* prob, const double* u1, double* v, void* stream);
+/* Number of continuous levels (n_hlevels + 1 for A_hp, 0 for A_p) and the
+ * vertex grid of level l (l = 0 finest). */
+sip_status sip_hlevel_dims(sip_problem* prob, int level, int* n_levels, int* nvx, int* nvy);
+/* Copy the Galerkin 9-point 2x2-block stencil of level l into S (device,
+ * nvx*nvy*36 doubles, S[v][t][c][c'], t = (dy+1)*3 + (dx+1)): level 0 is
+ * A_1c = P_cd^T A_1 P_cd, level l+1 is P_h^T A_l P_h (bilinear P_h). */
+sip_status sip_hlevel_stencil(sip_problem* prob, int level, double* S, void* stream);
+/* y = A_l x on continuous level l (vectors of 2 nvx nvy). */
+sip_status sip_hlevel_apply(sip_problem* prob, int level, const double* x, double* y, void* stream);
+/* x = A_c^{-1} b on the coarsest level (LU / Cholesky set-up, dense inverse):
+ * A_1 itself for n_hlevels = 0, else the coarsest continuous level. */
+sip_status sip_coarse_solve(sip_problem* prob, const double* b, double* x, void* stream);
+/* z_u = one V-cycle of Algorithm 1 (y0 = 0) applied to r_u: Chebyshev /
+ * element-block Jacobi pre-smoothing, restriction to Q_1, coarse correction
+ * (LU of A_1, or P_cd + continuous h-cycle + R_dc), prolongation,
+ * post-smoothing. */
+sip_status sip_vcycle(sip_problem* prob, const double* r_u, double* z_u, void* stream);
+/* The same V-cycle computed entirely in FP32 (the mixed-precision form). */
+sip_status sip_vcycle_f32(sip_problem* prob, const float* r_u, float* z_u, void* stream);
+/* y_u ~ A^{-1} t_u by PCG preconditioned with the V-cycle, from y = 0 until
+ * ||A y - t|| < rtol ||t|| (Sec. 6) or max_it iterations; *its receives the
+ * count.  Synchronous. */
+sip_status sip_inner_solve(sip_problem* prob, const double* t_u, double* y_u, double rtol,
+                           int max_it, int* its, void* stream);
+
+/* ---- Stokes solve (paper Sec. 5-7) ---------------------------------------- */
+typedef struct {
+    double rtol;        /* stop when ||b - K x||_2 <= rtol ||b||_2 (true residual)  */
+    int max_outer;      /* FGMRES iteration cap (all restarts)                      */
+    int restart;        /* FGMRES restart length                                    */
+    double inner_rtol;  /* inner PCG relative tolerance (paper 1e-3)                */
+    int max_inner;      /* inner iteration cap                                      */
+} sip_solve_opts;
+
+typedef struct {
+    int status;            /* sip_status of the solve                           */
+    int outer_its;         /* FGMRES iterations                                 */
+    int inner_total;       /* inner PCG iterations, summed                      */
+    int inner_max;
+    double inner_avg;
+    double rel_residual;   /* ||b - K x||_2 / ||b||_2 recomputed in FP64        */
+    double setup_ms;       /* multigrid set-up time of this call (0 if reused)  */
+    double solve_ms;
+    double lambda_max_p;
+    int64_t kernel_launches;
+} sip_solve_report;
+
+/* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200. */
+void sip_solve_opts_default(sip_solve_opts* opts);
+/* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
+ * preconditioned FGMRES with the upper block-triangular preconditioner
+ * (eq. discretestokespc): y_p = S*^{-1} x_p with S* the pressure mass scaled
+ * by 1/eta_K (diagonal), y_u ~ A^{-1}(x_u - B y_p) by the inner PCG with the
+ * hp-multigrid V-cycle.  Orthogonalisation: classical Gram-Schmidt twice.
+ * Without a Neumann side the constant pressure is projected out of every
+ * pressure vector and p is returned with zero mean (Sec. 5).  g_p may be NULL
+ * (g = 0, eq. rhs_f).  Outer state, residuals and S* are FP64; the
+ * preconditioner runs in the problem's precision.  Returns the status also
+ * in report->status (NOT_CONVERGED / BREAKDOWN keep the last iterate in u, p).
+ * Synchronous. */
+sip_status sip_solve(sip_problem* prob, const double* f_u, const double* g_p, double* u,
+                     double* p, const sip_solve_opts* opts, sip_solve_report* report,
+                     void* stream);
 
 /* ---- set-up helpers (paper Sec. 7.3) -------------------------------------- */
 /* Element-wise material of inclusions (Sec. 7.3): eta_K = max of eta over

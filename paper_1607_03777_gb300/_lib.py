@@ -81,6 +81,27 @@ SIGNATURES = {
     "sip_apply_A_f32": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_B": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_Bt": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_problem_setup": (ctypes.c_int, [_VP, _VP]),
+    "sip_problem_update_eta": (ctypes.c_int, [_VP, _VP, _VP]),
+    "sip_lambda_max": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sip_block_jacobi": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_p_restrict": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_p_prolong_add": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_apply_A1": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_cd_prolong": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_dc_restrict": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_hlevel_dims": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sip_hlevel_stencil": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "sip_hlevel_apply": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "sip_coarse_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_vcycle": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_vcycle_f32": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_inner_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), _VP]),
+    "sip_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "sip_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(SolveOpts),
+                                 ctypes.POINTER(SolveReport), _VP]),
     "sip_rasterise_inclusions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, _VP, _VP]),

@@ -140,3 +140,93 @@ class Problem:
         self.ctx.check(self.ctx.lib.sip_rhs_body_force(self.handle, _ptr(rho, torch.float64),
                                                        float(g), _ptr(f, torch.float64),
                                                        _stream(stream)))
+
+    def update_eta(self, eta, stream=None):
+        """sip_problem_update_eta with a CUDA tensor or a host array."""
+        if isinstance(eta, torch.Tensor):
+            ptr = _ptr(eta, torch.float64)
+        else:
+            self._eta = np.ascontiguousarray(np.asarray(eta, dtype=np.float64).reshape(-1))
+            ptr = self._eta.ctypes.data_as(ctypes.c_void_p)
+        self.ctx.check(self.ctx.lib.sip_problem_update_eta(self.handle, ptr, _stream(stream)))
+
+    # -- hp-multigrid pieces -------------------------------------------------
+    def setup(self, stream=None):
+        self.ctx.check(self.ctx.lib.sip_problem_setup(self.handle, _stream(stream)))
+
+    def lambda_max(self, level=-1):
+        out = ctypes.c_double()
+        self.ctx.check(self.ctx.lib.sip_lambda_max(self.handle, int(level), ctypes.byref(out)))
+        return out.value
+
+    def _call4(self, name, a, b, dta=torch.float64, dtb=torch.float64, stream=None):
+        fn = getattr(self.ctx.lib, name)
+        self.ctx.check(fn(self.handle, _ptr(a, dta), _ptr(b, dtb), _stream(stream)))
+
+    def block_jacobi(self, r, z, stream=None):
+        self._call4("sip_block_jacobi", r, z, stream=stream)
+
+    def p_restrict(self, r, r1, stream=None):
+        self._call4("sip_p_restrict", r, r1, stream=stream)
+
+    def p_prolong_add(self, e1, y, stream=None):
+        self._call4("sip_p_prolong_add", e1, y, stream=stream)
+
+    def apply_A1(self, x1, y1, stream=None):
+        self._call4("sip_apply_A1", x1, y1, stream=stream)
+
+    def cd_prolong(self, v, u1, stream=None):
+        self._call4("sip_cd_prolong", v, u1, stream=stream)
+
+    def dc_restrict(self, u1, v, stream=None):
+        self._call4("sip_dc_restrict", u1, v, stream=stream)
+
+    def hlevel_dims(self, level=0):
+        nl, nvx, nvy = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.sip_hlevel_dims(self.handle, int(level), ctypes.byref(nl),
+                                                    ctypes.byref(nvx), ctypes.byref(nvy)))
+        return nl.value, nvx.value, nvy.value
+
+    def hlevel_stencil(self, level, S, stream=None):
+        self.ctx.check(self.ctx.lib.sip_hlevel_stencil(self.handle, int(level),
+                                                       _ptr(S, torch.float64), _stream(stream)))
+
+    def hlevel_apply(self, level, x, y, stream=None):
+        self.ctx.check(self.ctx.lib.sip_hlevel_apply(self.handle, int(level), _ptr(x, torch.float64),
+                                                     _ptr(y, torch.float64), _stream(stream)))
+
+    def coarse_solve(self, b, x, stream=None):
+        self._call4("sip_coarse_solve", b, x, stream=stream)
+
+    def vcycle(self, r, z, stream=None):
+        self._call4("sip_vcycle", r, z, stream=stream)
+
+    def vcycle_f32(self, r, z, stream=None):
+        self._call4("sip_vcycle_f32", r, z, torch.float32, torch.float32, stream=stream)
+
+    def inner_solve(self, t, y, rtol=1e-3, max_it=200, stream=None):
+        its = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.sip_inner_solve(self.handle, _ptr(t, torch.float64),
+                                                    _ptr(y, torch.float64), float(rtol), int(max_it),
+                                                    ctypes.byref(its), _stream(stream)))
+        return its.value
+
+    # -- Stokes solve --------------------------------------------------------
+    def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
+              max_inner=200, stream=None, check=True):
+        """sip_solve; returns the report as a dict (raises on failure when
+        ``check``)."""
+        o = SolveOpts()
+        self.ctx.lib.sip_solve_opts_default(ctypes.byref(o))
+        o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
+        o.inner_rtol, o.max_inner = inner_rtol, max_inner
+        rep = SolveReport()
+        st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
+                                    _ptr(g, torch.float64) if g is not None else None,
+                                    _ptr(u, torch.float64), _ptr(p, torch.float64),
+                                    ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        out = {name: getattr(rep, name) for name, _ in SolveReport._fields_}
+        if check:
+            self.ctx.check(st)
+        out["status"] = st
+        return out

@@ -3,7 +3,7 @@
 // this file.
 #include <cstring>
 
-#include "sip_internal.h"
+#include "sip_solver.h"
 
 using sip::Error;
 
@@ -32,9 +32,6 @@ inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 }  // namespace
 
-int64_t sip_problem::device_bytes() const {
-    return int64_t(eta_d.bytes + eta_f.bytes);
-}
 
 extern "C" {
 
@@ -155,6 +152,34 @@ sip_status sip_problem_sizes(const sip_problem* p, int64_t* n_u, int64_t* n_p,
     return SIP_OK;
 }
 
+sip_status sip_problem_update_eta(sip_problem* p, const double* eta, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(eta != nullptr, "null eta");
+        cudaPointerAttributes at{};
+        SIP_CUDA(cudaPointerGetAttributes(&at, eta));
+        const bool on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        const cudaStream_t s = as_stream(stream);
+        const size_t ne = size_t(p->ne);
+        if (on_dev) {
+            SIP_CUDA(cudaMemcpyAsync(p->eta_d.ptr, eta, ne * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+        } else {
+            for (size_t e = 0; e < ne; ++e)
+                sip::require(std::isfinite(eta[e]) && eta[e] > 0.0,
+                             "eta must be finite and positive");
+            SIP_CUDA(cudaMemcpyAsync(p->eta_d.ptr, eta, ne * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        }
+        if (on_dev && !sip::eta_valid(ne, p->eta_d.as<double>(), s))
+            throw Error(SIP_ERR_INVALID_ARG, "eta must be finite and positive");
+        sip::launch_cast<double, float>(ne, p->eta_d.as<double>(), p->eta_f.as<float>(), s);
+        if (p->mg64) p->mg64->ready = false;
+        if (p->mg32) p->mg32->ready = false;
+        if (p->ws) p->ws->sinv_ready = false;
+    });
+}
+
 sip_status sip_apply_A(sip_problem* p, const double* x, double* y, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
     return guarded(p->ctx, [&] {
@@ -234,6 +259,204 @@ sip_status sip_rhs_body_force(sip_problem* p, const double* rho, double g, doubl
         sip::require(std::isfinite(g), "non-finite gravity");
         sip::launch_rhs_body_force(p->k, p->geom, rho, g, f, as_stream(stream));
     });
+}
+
+// ------------------------------------------------------------ multigrid
+namespace {
+
+sip::Multigrid<double>& mg64(sip_problem* p, cudaStream_t s) {
+    SIP_CUDA(cudaSetDevice(p->ctx->device));
+    if (!p->mg64) {
+        p->mg64 = std::make_unique<sip::Multigrid<double>>();
+        p->mg64->P = p;
+    }
+    if (!p->mg64->ready) p->mg64->setup(s);
+    return *p->mg64;
+}
+
+sip::Multigrid<float>& mg32(sip_problem* p, cudaStream_t s) {
+    SIP_CUDA(cudaSetDevice(p->ctx->device));
+    if (!p->mg32) {
+        p->mg32 = std::make_unique<sip::Multigrid<float>>();
+        p->mg32->P = p;
+    }
+    if (!p->mg32->ready) p->mg32->setup(s);
+    return *p->mg32;
+}
+
+}  // namespace
+
+sip_status sip_problem_setup(sip_problem* p, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        SIP_CUDA(cudaSetDevice(p->ctx->device));
+        p->ensure_setup(as_stream(stream));
+    });
+}
+
+sip_status sip_lambda_max(sip_problem* p, int level, double* out) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(out != nullptr, "null output");
+        auto& m = mg64(p, nullptr);
+        sip::require(level == -1 || (level >= 0 && level < int(m.h.size()) - 1),
+                     "level must be -1 (p-level) or a smoothed h-level");
+        *out = level < 0 ? m.lmax_p : m.h[level].lmax;
+    });
+}
+
+sip_status sip_block_jacobi(sip_problem* p, const double* r, double* z, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(r && z && r != z, "bad vectors");
+        mg64(p, as_stream(stream)).bj(r, z, as_stream(stream));
+    });
+}
+
+sip_status sip_p_restrict(sip_problem* p, const double* r, double* r1, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(r && r1, "null vector");
+        sip::launch_p_restrict<double>(size_t(p->ne), p->n, r, r1, as_stream(stream));
+    });
+}
+
+sip_status sip_p_prolong_add(sip_problem* p, const double* e1, double* y, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(e1 && y, "null vector");
+        sip::launch_p_prolong_add<double>(size_t(p->ne), p->n, e1, y, as_stream(stream));
+    });
+}
+
+sip_status sip_apply_A1(sip_problem* p, const double* x1, double* y1, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(x1 && y1 && x1 != y1, "bad vectors");
+        sip::launch_apply_sip<double>(2, p->geom1, x1, y1, p->eta_d.as<double>(), 1.0, nullptr, 0.0,
+                                      as_stream(stream));
+    });
+}
+
+sip_status sip_cd_prolong(sip_problem* p, const double* v, double* u1, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(v && u1, "null vector");
+        sip::launch_pcd<double>(p->desc.nx, p->desc.ny, v, u1, as_stream(stream));
+    });
+}
+
+sip_status sip_dc_restrict(sip_problem* p, const double* u1, double* v, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(v && u1, "null vector");
+        sip::launch_rdc<double>(p->desc.nx, p->desc.ny, u1, v, as_stream(stream));
+    });
+}
+
+sip_status sip_hlevel_dims(sip_problem* p, int level, int* n_levels, int* nvx, int* nvy) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        auto& m = mg64(p, nullptr);
+        if (n_levels) *n_levels = int(m.h.size());
+        if (level >= 0) {
+            sip::require(level < int(m.h.size()), "no such level");
+            if (nvx) *nvx = m.h[level].nvx;
+            if (nvy) *nvy = m.h[level].nvy;
+        }
+    });
+}
+
+sip_status sip_hlevel_stencil(sip_problem* p, int level, double* S, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        auto& m = mg64(p, as_stream(stream));
+        sip::require(S != nullptr, "null output");
+        sip::require(level >= 0 && level < int(m.h.size()), "no such level");
+        SIP_CUDA(cudaMemcpyAsync(S, m.h[level].S.ptr, m.h[level].S.bytes, cudaMemcpyDeviceToDevice,
+                                 as_stream(stream)));
+    });
+}
+
+sip_status sip_hlevel_apply(sip_problem* p, int level, const double* x, double* y, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        auto& m = mg64(p, as_stream(stream));
+        sip::require(x && y && x != y, "bad vectors");
+        sip::require(level >= 0 && level < int(m.h.size()), "no such level");
+        m.hlevel_apply(level, x, y, as_stream(stream));
+    });
+}
+
+sip_status sip_coarse_solve(sip_problem* p, const double* b, double* x, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        auto& m = mg64(p, as_stream(stream));
+        sip::require(b && x && b != x, "bad vectors");
+        sip::launch_dense_symv<double>(m.nc, m.cinv.as<double>(), b, x, as_stream(stream));
+    });
+}
+
+sip_status sip_vcycle(sip_problem* p, const double* r, double* z, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(r && z && r != z, "bad vectors");
+        mg64(p, as_stream(stream)).vcycle(r, z, as_stream(stream));
+    });
+}
+
+sip_status sip_vcycle_f32(sip_problem* p, const float* r, float* z, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(r && z && r != z, "bad vectors");
+        mg32(p, as_stream(stream)).vcycle(r, z, as_stream(stream));
+    });
+}
+
+sip_status sip_inner_solve(sip_problem* p, const double* t, double* y, double rtol, int max_it,
+                           int* its, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded(p->ctx, [&] {
+        sip::require(t && y && t != y, "bad vectors");
+        sip::require(rtol > 0 && max_it >= 1, "bad tolerance or iteration cap");
+        const int n = mg64(p, as_stream(stream)).inner_pcg(t, y, rtol, max_it, as_stream(stream),
+                                                          nullptr);
+        SIP_CUDA(cudaStreamSynchronize(as_stream(stream)));
+        if (its) *its = n;
+    });
+}
+
+void sip_solve_opts_default(sip_solve_opts* o) {
+    if (!o) return;
+    o->rtol = 1e-8;
+    o->max_outer = 500;
+    o->restart = 100;
+    o->inner_rtol = 1e-3;
+    o->max_inner = 200;
+}
+
+sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
+                     const sip_solve_opts* opts, sip_solve_report* rep, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    sip_status st = SIP_OK;
+    const sip_status gst = guarded(p->ctx, [&] {
+        sip::require(f && u && pp, "null vector");
+        sip_solve_opts o;
+        sip_solve_opts_default(&o);
+        if (opts) o = *opts;
+        sip::require(std::isfinite(o.rtol) && o.rtol > 0 && o.max_outer >= 1 && o.restart >= 1 &&
+                         o.restart <= 250 &&
+                         std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1,
+                     "bad solve options");
+        SIP_CUDA(cudaSetDevice(p->ctx->device));
+        st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
+        if (st != SIP_OK) {
+            throw Error(st, st == SIP_ERR_NOT_CONVERGED ? "FGMRES did not reach the tolerance"
+                                                        : "Krylov breakdown");
+        }
+    });
+    if (gst != SIP_OK && rep) rep->status = gst;
+    return gst;
 }
 
 }  // extern "C"

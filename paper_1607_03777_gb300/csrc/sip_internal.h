@@ -28,7 +28,15 @@ struct Error : std::runtime_error {
                                                  cudaGetErrorString(e_));           \
     } while (0)
 
-#define SIP_CHECK_LAUNCH() SIP_CUDA(cudaGetLastError())
+// Host-side count of kernel launches issued by the library (each launcher
+// ends with SIP_CHECK_LAUNCH); graph replays add their captured kernel count.
+int64_t& launch_counter();
+
+#define SIP_CHECK_LAUNCH()                  \
+    do {                                    \
+        ++::sip::launch_counter();          \
+        SIP_CUDA(cudaGetLastError());       \
+    } while (0)
 
 inline void require(bool ok, const std::string& msg) {
     if (!ok) throw Error(SIP_ERR_INVALID_ARG, msg);
@@ -119,10 +127,27 @@ struct DeviceBuffer {
     DeviceBuffer() = default;
     DeviceBuffer(const DeviceBuffer&) = delete;
     DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+    DeviceBuffer(DeviceBuffer&& o) noexcept : ptr(o.ptr), bytes(o.bytes) {
+        o.ptr = nullptr;
+        o.bytes = 0;
+    }
+    DeviceBuffer& operator=(DeviceBuffer&& o) noexcept {
+        if (this != &o) {
+            if (ptr) cudaFree(ptr);
+            ptr = o.ptr;
+            bytes = o.bytes;
+            o.ptr = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
     ~DeviceBuffer() {
         if (ptr) cudaFree(ptr);
     }
+    // Ensure at least b bytes; an existing buffer that is large enough is
+    // kept (re-running a set-up on the same problem allocates nothing).
     void alloc(size_t b) {
+        if (ptr && bytes >= b) return;
         if (ptr) cudaFree(ptr);
         ptr = nullptr;
         bytes = 0;
@@ -146,16 +171,4 @@ struct DeviceBuffer {
 struct sip_ctx {
     int device = 0;
     std::string err;
-};
-
-struct sip_problem {
-    sip_ctx* ctx = nullptr;
-    sip_problem_desc desc{};
-    int k = 0, n = 0, nb = 0, mp = 0;
-    int64_t ne = 0, n_u = 0, n_p = 0;
-    sip::OpGeom geom{};      // the SIP operator of degree k
-    sip::OpGeom geom1{};     // the Galerkin Q_1 operator (fine-k penalty)
-    std::vector<double> eta_host;
-    sip::DeviceBuffer eta_d, eta_f;
-    int64_t device_bytes() const;
 };

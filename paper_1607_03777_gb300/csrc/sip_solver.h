@@ -1,0 +1,170 @@
+// Solver-side declarations: kernel launchers of the smoother, transfer and
+// Krylov translation units, and the multigrid / Krylov drivers.
+#pragma once
+
+#include <memory>
+
+#include "sip_internal.h"
+
+namespace sip {
+
+// ---- smoother.cu
+void launch_classify(int nx, int ny, const double* eta, int* emap, int* uniq_list, int* n_uniq,
+                     cudaStream_t s);
+template <typename T>
+void launch_build_blocks(int N, const OpGeom& g, const int* spec, int count, const double* eta,
+                         T* out, cudaStream_t s);
+template <typename T>
+void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
+                     const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s);
+
+// ---- transfer.cu
+template <typename T> void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s);
+template <typename T> void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s);
+template <typename T> void launch_pcd(int nx, int ny, const T* v, T* out, cudaStream_t s);
+template <typename T> void launch_rdc(int nx, int ny, const T* r, T* out, cudaStream_t s);
+template <typename T>
+void launch_stencil_apply(int nvx, int nvy, const T* S, const T* x, T* y, T alpha, const T* z,
+                          T beta, cudaStream_t s);
+template <typename T> void launch_stencil_dinv(size_t nv, const T* S, T* dinv, cudaStream_t s);
+template <typename T>
+void launch_jacobi_cheb(size_t n, const T* r, const T* dinv, T* d, T* x, T c1, T c2, bool x_zero,
+                        cudaStream_t s);
+template <typename T> void launch_ph_add(int nxc, int nyc, const T* xc, T* yf, cudaStream_t s);
+template <typename T> void launch_rh(int nxc, int nyc, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+void launch_probe_vertices(int nvx, int nvy, int col, int cp, T* x, cudaStream_t s);
+template <typename T> void launch_extract_stencil(int nvx, int nvy, const T* Y, T* S, cudaStream_t s);
+template <typename T> void launch_probe_elements(int nx, int ny, int col, int l, T* x, cudaStream_t s);
+template <typename T> void launch_dense_symv(int n, const T* M, const T* x, T* y, cudaStream_t s);
+void launch_band_chol_inverse(int n, int bw, const double* L, double* X, cudaStream_t s);
+template <typename T> void launch_convert(size_t n, const double* a, T* b, cudaStream_t s);
+
+// ---- krylov.cu
+size_t reduction_workspace_doubles(int max_vectors);
+template <typename T>
+void launch_mdot(int m, size_t n, const T* V, size_t ldv, const T* w, double* out, double* ws,
+                 cudaStream_t s);
+template <typename T>
+void launch_dot(size_t n, const T* x, const T* y, double* out, double* ws, cudaStream_t s);
+template <typename T>
+void launch_maxpy(int m, size_t n, const T* V, size_t ldv, const double* h, double sign, T* w,
+                  cudaStream_t s);
+template <typename T>
+void launch_pcg_update(size_t n, const T* d, const T* q, T* y, T* r, const double* num,
+                       const double* den, cudaStream_t s);
+template <typename T>
+void launch_pcg_dir(size_t n, const T* z, T* d, const double* num, const double* den,
+                    cudaStream_t s);
+template <typename T> void launch_axpby(size_t n, T a, const T* x, T b, T* y, cudaStream_t s);
+template <typename T> void launch_vmul(size_t n, const T* x, const T* sc, T* y, cudaStream_t s);
+template <typename Ti, typename To> void launch_cast(size_t n, const Ti* a, To* b, cudaStream_t s);
+void launch_zero_mean_pressure(size_t ne, int mp, double* p, double* ws, cudaStream_t s);
+void launch_splitmix_uniform(size_t n, uint64_t seed, double* out, cudaStream_t s);
+// true when every entry is finite and positive (synchronises s)
+bool eta_valid(size_t n, const double* eta, cudaStream_t s);
+
+// ---- host helpers (solver.cu)
+double hessenberg_max_real_eig(const std::vector<double>& H, int m);  // H: m x m row-major
+// Cholesky of a symmetric band matrix (lower band storage A[i][bw-1-(i-j)]),
+// in place; returns false if a pivot is not positive.
+bool band_cholesky(std::vector<double>& A, int n, int bw);
+
+// Small pinned host scratch for scalar read-backs.
+struct HostScalars {
+    double* p = nullptr;
+    HostScalars();
+    ~HostScalars();
+};
+
+template <typename T>
+struct HLevel {
+    int nx = 0, ny = 0;       // elements of this level's grid
+    int nvx = 0, nvy = 0;     // vertices
+    size_t n = 0;             // dofs = 2 nvx nvy
+    DeviceBuffer S, dinv, b, x, r, d;
+    double lmax = 0.0;
+};
+
+template <typename T>
+struct Multigrid {
+    sip_problem* P = nullptr;
+    int N = 0, nb = 0;
+    size_t ne = 0, n_u = 0;
+    // element-block Jacobi
+    DeviceBuffer emap, uniq_list, n_uniq_d, cls_inv, uniq_inv, eta_T;
+    int n_uniq = 0;
+    double lmax_p = 0.0;
+    // p-level work
+    DeviceBuffer pb, pr, pd, r1, e1, vin, vout;
+    // continuous hierarchy (h[0] = finest continuous level)
+    std::vector<HLevel<T>> h;
+    // coarsest direct solve (dense inverse)
+    DeviceBuffer cinv;
+    int nc = 0;
+    // reductions
+    DeviceBuffer ws, sc;
+    HostScalars hs;
+    DeviceBuffer cg_r, cg_d, cg_q;   // inner PCG vectors (outside the graph)
+    // set-up scratch, kept so that a repeated set-up allocates nothing
+    DeviceBuffer scr_V, scr_tmp, scr_b, scr_spec, scr_L, scr_X, scr_Y, scr_xv, scr_t1, scr_t2;
+    std::vector<DeviceBuffer> scr_S64;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int64_t graph_kernels = 0;
+    bool ready = false;
+
+    ~Multigrid();
+    void setup(cudaStream_t s);
+    // z = V(r): one V-cycle of Algorithm 1 with y0 = 0 (r, z of length n_u)
+    void vcycle(const T* r, T* z, cudaStream_t s);
+    void vcycle_direct(cudaStream_t s);   // vin -> vout, kernels only
+    void bj(const T* r, T* z, cudaStream_t s);
+    void coarse_solve(const T* b1, T* e1, cudaStream_t s);
+    void hlevel_apply(int l, const T* x, T* y, cudaStream_t s);
+    int inner_pcg(const T* t, T* y, double rtol, int maxit, cudaStream_t s, double* final_rel);
+    int64_t bytes() const;
+
+   private:
+    void smooth_p(const T* b, T* y, bool zero, cudaStream_t s);
+    void hcycle(int l, cudaStream_t s);
+    void smooth_h(int l, bool zero, cudaStream_t s);
+    double estimate_p(cudaStream_t s);
+    double estimate_h(int l, cudaStream_t s);
+    void build_blocks(cudaStream_t s);
+    void build_coarse_from_band(const std::vector<double>& band, int n, int bw, cudaStream_t s);
+};
+
+// FGMRES storage of one problem (FP64): Krylov basis V, flexible basis Z.
+struct Workspace {
+    int restart = 0;
+    size_t n = 0;
+    DeviceBuffer V, Z, w, x, r, b, tu, yu64, sinv, ws, sc, hbuf;
+    DeviceBuffer t32, y32;   // inner solve in FP32 (mixed precision)
+    HostScalars hs;
+    bool sinv_ready = false;
+    int64_t bytes() const;
+};
+
+sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
+                     double* p, const sip_solve_opts& o, sip_solve_report* rep,
+                     cudaStream_t s);
+
+}  // namespace sip
+
+struct sip_problem {
+    sip_ctx* ctx = nullptr;
+    sip_problem_desc desc{};
+    int k = 0, n = 0, nb = 0, mp = 0;
+    int64_t ne = 0, n_u = 0, n_p = 0;
+    sip::OpGeom geom{};      // the SIP operator of degree k
+    sip::OpGeom geom1{};     // the Galerkin Q_1 operator (fine-k penalty)
+    std::vector<double> eta_host;
+    sip::DeviceBuffer eta_d, eta_f;
+    std::unique_ptr<sip::Multigrid<double>> mg64;
+    std::unique_ptr<sip::Multigrid<float>> mg32;
+    std::unique_ptr<sip::Workspace> ws;
+    double setup_ms = 0.0;
+    int64_t device_bytes() const;
+    void ensure_setup(cudaStream_t s);
+};

@@ -1,0 +1,297 @@
+// Element-block Jacobi smoother of the p-level (Sec. 6): the diagonal blocks
+// M_K of A, their inverses, and the fused block-Jacobi / Chebyshev update.
+//
+// M_K depends on the element only through eta_K, the face kinds and the
+// face penalties.  When eta_K is at least the viscosity of every face
+// neighbour, all face penalties of K use eta_e = eta_K and M_K = eta_K M_ref,
+// where M_ref depends only on which sides of K lie on the boundary (a 4-bit
+// mask).  Such elements share one reference inverse per mask, scaled by
+// 1/eta_K; the remaining ("unique") elements get their own inverse.
+#include "sip_face.cuh"
+#include "sip_internal.h"
+
+namespace sip {
+
+namespace {
+
+template <int N>
+struct BlockArgs {
+    const int* spec;       // >= 0: element index; < 0: -(mask+1) reference block
+    const double* eta;
+    int nx, ny;
+    double hx, hy;
+    int bc[4];
+    double pen_x, pen_y;
+    Tab1D<N, double> tab;
+};
+
+// Entry M[r][s] of the element block: the local operator (neighbour
+// coefficients zero) applied to the unit vector s, row r.
+template <int N>
+__device__ double block_entry(int r, int s, double etaK, const int kind[4], const double sig[4],
+                              double hx, double hy, const Tab1D<N, double>& tb) {
+    constexpr int NN = N * N;
+    const int a = r % N, b = (r / N) % N, c = r / NN;
+    const int i = s % N, j = (s / N) % N, c2 = s / NN;
+    const double* G = tb.G;
+    const double* D = tb.D;
+    double vol = 0.0;
+    if (c == 0) {
+        if (c2 == 0) {
+            if (b == j) vol += 2.0 * hy / hx * G[a * N + i];
+            if (a == i) vol += hx / hy * G[b * N + j];
+        } else {
+            vol += D[j * N + b] * D[a * N + i];
+        }
+    } else {
+        if (c2 == 1) {
+            if (a == i) vol += 2.0 * hx / hy * G[b * N + j];
+            if (b == j) vol += hy / hx * G[a * N + i];
+        } else {
+            vol += D[i * N + a] * D[b * N + j];
+        }
+    }
+    double acc = etaK * vol;
+    double vo[2 * N], dv[2 * N], zero[2 * N];
+    for (int F = 0; F < 4; ++F) {
+        const int d = F < 2 ? 0 : 1;
+        const bool plus = (F % 2) == 1;
+        const double sgn = plus ? 1.0 : -1.0;
+        const double* l = plus ? tb.lp : tb.lm;
+        const double* dl = plus ? tb.dp : tb.dm;
+        for (int q = 0; q < 2 * N; ++q) vo[q] = dv[q] = zero[q] = 0.0;
+        if (d == 0) {  // trace along y of mode (j, i): value l_i(s) at m = j
+            vo[c2 * N + j] = l[i];
+            dv[c2 * N + j] = 2.0 / hx * dl[i];
+        } else {
+            vo[c2 * N + i] = l[j];
+            dv[c2 * N + i] = 2.0 / hy * dl[j];
+        }
+        const int mt = d == 0 ? b : a;   // test mode along the face
+        const int qt = d == 0 ? a : b;   // test mode along the normal
+        double P, Q;
+        face_pq<N, double>(kind[F], c, mt, d, sgn, d == 0 ? hx : hy, d == 0 ? hy : hx, etaK, 0.0,
+                           sig[F], vo, dv, zero, zero, D, P, Q);
+        acc += l[qt] * P + dl[qt] * Q;
+    }
+    return acc;
+}
+
+// One CTA per block: build M in shared memory, invert it by Gauss-Jordan
+// elimination (SPD: no pivoting needed), store M^{-1} as T.
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_build_blocks(const BlockArgs<N> a, T* out) {
+    constexpr int NB = 2 * N * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* M = reinterpret_cast<double*>(smem_raw);
+    __shared__ double colk[NB];
+    __shared__ double rowk[NB];
+    const int sp = a.spec[blockIdx.x];
+    double etaK;
+    int kind[4];
+    double sig[4];
+    if (sp >= 0) {
+        const int ex = sp % a.nx, ey = sp / a.nx;
+        etaK = a.eta[sp];
+        const int nbr[4] = {ex > 0 ? sp - 1 : -1, ex < a.nx - 1 ? sp + 1 : -1,
+                            ey > 0 ? sp - a.nx : -1, ey < a.ny - 1 ? sp + a.nx : -1};
+        for (int F = 0; F < 4; ++F) {
+            const double pen = F < 2 ? a.pen_x : a.pen_y;
+            if (nbr[F] >= 0) {
+                kind[F] = 0;
+                sig[F] = pen * fmax(etaK, a.eta[nbr[F]]);
+            } else {
+                kind[F] = 1 + a.bc[F];
+                sig[F] = 2.0 * pen * etaK;
+            }
+        }
+    } else {
+        const int mask = -sp - 1;
+        etaK = 1.0;
+        for (int F = 0; F < 4; ++F) {
+            const double pen = F < 2 ? a.pen_x : a.pen_y;
+            const bool bnd = (mask >> F) & 1;
+            kind[F] = bnd ? 1 + a.bc[F] : 0;
+            sig[F] = bnd ? 2.0 * pen : pen;
+        }
+    }
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x)
+        M[q] = block_entry<N>(q / NB, q % NB, etaK, kind, sig, a.hx, a.hy, a.tab);
+    __syncthreads();
+    for (int k = 0; k < NB; ++k) {
+        const double piv = 1.0 / M[k * NB + k];
+        for (int q = threadIdx.x; q < NB; q += blockDim.x) {
+            colk[q] = M[q * NB + k];
+            rowk[q] = M[k * NB + q];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+            const int i = q / NB, j = q % NB;
+            if (i == k && j == k)
+                M[q] = piv;
+            else if (i == k)
+                M[q] = rowk[j] * piv;
+            else if (j == k)
+                M[q] = -colk[i] * piv;
+            else
+                M[q] -= colk[i] * rowk[j] * piv;
+        }
+        __syncthreads();
+    }
+    T* o = out + size_t(blockIdx.x) * NB * NB;
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) o[q] = T(M[q]);
+}
+
+// Element classification: mask of boundary sides; class elements (eta_K not
+// below any face neighbour) map to -(mask+1), the others get a slot in the
+// unique list (order by atomic ticket; results do not depend on it).
+__global__ void k_classify(int nx, int ny, const double* eta, int* emap, int* uniq_list,
+                           int* n_uniq) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nx * ny) return;
+    const int ex = e % nx, ey = e / nx;
+    int mask = 0;
+    bool cls = true;
+    const double et = eta[e];
+    if (ex == 0) mask |= 1; else cls = cls && et >= eta[e - 1];
+    if (ex == nx - 1) mask |= 2; else cls = cls && et >= eta[e + 1];
+    if (ey == 0) mask |= 4; else cls = cls && et >= eta[e - nx];
+    if (ey == ny - 1) mask |= 8; else cls = cls && et >= eta[e + nx];
+    if (cls) {
+        emap[e] = -(mask + 1);
+    } else {
+        const int slot = atomicAdd(n_uniq, 1);
+        uniq_list[slot] = e;
+        emap[e] = slot;
+    }
+}
+
+// out = c2 * M_K^{-1} r_K (+ c1 * out_old); if x: x = (x_zero ? 0 : x) + out.
+// EB elements per CTA, the residual blocks staged in shared memory; thread
+// (element, row r) reads column r of the symmetric inverse (coalesced).
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ r, T* out, T* x,
+                                                  const int* __restrict__ emap,
+                                                  const T* __restrict__ cls_inv,
+                                                  const T* __restrict__ uniq_inv,
+                                                  const T* __restrict__ eta, T c1, T c2,
+                                                  int x_zero) {
+    constexpr int NB = 2 * N * N;
+    constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
+    __shared__ T sr[EB * NB];
+    const int e0 = blockIdx.x * EB;
+    const int cnt = min(EB, ne - e0) * NB;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) sr[q] = r[size_t(e0) * NB + q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int el = q / NB, row = q % NB;
+        const int e = e0 + el;
+        const int m = emap[e];
+        const T* Minv;
+        T scale;
+        if (m < 0) {
+            Minv = cls_inv + size_t(-m - 1) * NB * NB;
+            scale = T(1) / eta[e];
+        } else {
+            Minv = uniq_inv + size_t(m) * NB * NB;
+            scale = T(1);
+        }
+        const T* rr = sr + el * NB;
+        T acc = T(0);
+#pragma unroll 7
+        for (int s = 0; s < NB; ++s) acc += Minv[s * NB + row] * rr[s];
+        const size_t o = size_t(e) * NB + row;
+        T v = c2 * scale * acc;
+        if (c1 != T(0)) v += c1 * out[o];
+        out[o] = v;
+        if (x) x[o] = x_zero ? v : x[o] + v;
+    }
+}
+
+template <int N>
+BlockArgs<N> make_block_args(const OpGeom& g, const int* spec, const double* eta) {
+    BlockArgs<N> a;
+    a.spec = spec;
+    a.eta = eta;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.hx = g.hx;
+    a.hy = g.hy;
+    for (int i = 0; i < 4; ++i) a.bc[i] = g.bc[i];
+    a.pen_x = g.pen_x;
+    a.pen_y = g.pen_y;
+    a.tab = make_tab<N, double>();
+    return a;
+}
+
+template <int N, typename T>
+void build_blocks_n(const OpGeom& g, const int* spec, int count, const double* eta, T* out,
+                    cudaStream_t s) {
+    if (count == 0) return;
+    constexpr int NB = 2 * N * N;
+    const size_t smem = size_t(NB) * NB * sizeof(double);
+    SIP_CUDA(cudaFuncSetAttribute(k_build_blocks<N, T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    k_build_blocks<N, T><<<count, 256, smem, s>>>(make_block_args<N>(g, spec, eta), out);
+    SIP_CHECK_LAUNCH();
+}
+
+template <int N, typename T>
+void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
+                const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s) {
+    constexpr int NB = 2 * N * N;
+    constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
+    const int blocks = (ne + EB - 1) / EB;
+    k_bj_apply<N, T><<<blocks, 256, 0, s>>>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2,
+                                            x_zero ? 1 : 0);
+    SIP_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void launch_classify(int nx, int ny, const double* eta, int* emap, int* uniq_list, int* n_uniq,
+                     cudaStream_t s) {
+    const int ne = nx * ny;
+    k_classify<<<(ne + 255) / 256, 256, 0, s>>>(nx, ny, eta, emap, uniq_list, n_uniq);
+    SIP_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_build_blocks(int N, const OpGeom& g, const int* spec, int count, const double* eta,
+                         T* out, cudaStream_t s) {
+    switch (N) {
+        case 2: build_blocks_n<2, T>(g, spec, count, eta, out, s); break;
+        case 3: build_blocks_n<3, T>(g, spec, count, eta, out, s); break;
+        case 4: build_blocks_n<4, T>(g, spec, count, eta, out, s); break;
+        case 5: build_blocks_n<5, T>(g, spec, count, eta, out, s); break;
+        case 6: build_blocks_n<6, T>(g, spec, count, eta, out, s); break;
+        case 7: build_blocks_n<7, T>(g, spec, count, eta, out, s); break;
+        default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
+    }
+}
+template void launch_build_blocks<double>(int, const OpGeom&, const int*, int, const double*,
+                                          double*, cudaStream_t);
+template void launch_build_blocks<float>(int, const OpGeom&, const int*, int, const double*,
+                                         float*, cudaStream_t);
+
+template <typename T>
+void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
+                     const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s) {
+    switch (N) {
+        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
+    }
+}
+template void launch_bj_apply<double>(int, int, const double*, double*, double*, const int*,
+                                      const double*, const double*, const double*, double, double,
+                                      bool, cudaStream_t);
+template void launch_bj_apply<float>(int, int, const float*, float*, float*, const int*,
+                                     const float*, const float*, const float*, float, float, bool,
+                                     cudaStream_t);
+
+}  // namespace sip

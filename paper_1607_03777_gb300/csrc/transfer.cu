@@ -1,0 +1,360 @@
+// Inter-level transfers and h-level operators of the hp-multigrid (Sec. 6):
+//  - p-restriction / prolongation between Q_k and the hierarchical Q_1 modes
+//    (injection and its transpose);
+//  - P_cd / R_dc = P_cd^T between continuous bilinears at the vertices and
+//    element-wise modal Q_1 coefficients (nodal -> modal);
+//  - vertex-centred bilinear P_h / R_h = P_h^T between vertex grids;
+//  - the 9-point, 2x2-block stencil operators of the continuous levels, their
+//    point-Jacobi / Chebyshev update, and the probing that forms the Galerkin
+//    stencils;
+//  - a dense symmetric matrix-vector product for the coarsest-level inverse.
+#include "sip_internal.h"
+
+namespace sip {
+
+namespace {
+
+constexpr double kInvSqrt2 = 0.70710678118654752440;   // int L_p l_0 for the two end hats
+constexpr double kInvSqrt6 = 0.40824829046386301637;   // |int L_p l_1|
+
+template <typename T>
+__global__ void k_p_restrict(size_t ne, int N, const T* __restrict__ r, T* __restrict__ r1) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= ne * 8) return;
+    const size_t e = g / 8;
+    const int l = int(g % 8), c = l / 4, j = (l / 2) % 2, i = l % 2;
+    r1[g] = r[e * 2 * N * N + c * N * N + j * N + i];
+}
+
+template <typename T>
+__global__ void k_p_prolong_add(size_t ne, int N, const T* __restrict__ e1, T* __restrict__ y) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= ne * 8) return;
+    const size_t e = g / 8;
+    const int l = int(g % 8), c = l / 4, j = (l / 2) % 2, i = l % 2;
+    y[e * 2 * N * N + c * N * N + j * N + i] += e1[g];
+}
+
+// weight of corner p (0 = low end, 1 = high end) on mode i of the 1D
+// orthonormal basis: int L_p l_i over [-1, 1] with L_0 = (1-xi)/2, L_1 = (1+xi)/2
+__device__ __forceinline__ double hatw(int i, int p) {
+    return i == 0 ? kInvSqrt2 : (p == 0 ? -kInvSqrt6 : kInvSqrt6);
+}
+
+template <typename T>
+__global__ void k_pcd(int nx, int ny, const T* __restrict__ v, T* __restrict__ out) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t ne = size_t(nx) * ny;
+    if (g >= ne * 8) return;
+    const size_t e = g / 8;
+    const int l = int(g % 8), c = l / 4, j = (l / 2) % 2, i = l % 2;
+    const int ex = int(e % nx), ey = int(e / nx);
+    double acc = 0.0;
+    for (int q = 0; q < 2; ++q)
+        for (int p = 0; p < 2; ++p)
+            acc += hatw(i, p) * hatw(j, q) * double(v[2 * (size_t(ey + q) * (nx + 1) + ex + p) + c]);
+    out[g] = T(acc);
+}
+
+template <typename T>
+__global__ void k_rdc(int nx, int ny, const T* __restrict__ r, T* __restrict__ out) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nv = size_t(nx + 1) * (ny + 1);
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % (nx + 1)), vy = int(v / (nx + 1));
+    double acc = 0.0;
+    for (int q = 0; q < 2; ++q) {          // vertex is corner q (in y) of element row vy - q
+        const int ey = vy - q;
+        if (ey < 0 || ey >= ny) continue;
+        for (int p = 0; p < 2; ++p) {
+            const int ex = vx - p;
+            if (ex < 0 || ex >= nx) continue;
+            const T* re = r + (size_t(ey) * nx + ex) * 8 + c * 4;
+            for (int j = 0; j < 2; ++j)
+                for (int i = 0; i < 2; ++i) acc += hatw(i, p) * hatw(j, q) * double(re[j * 2 + i]);
+        }
+    }
+    out[g] = T(acc);
+}
+
+// y = alpha * S x + beta * z for the 9-point 2x2-block stencil on an
+// (nvx x nvy) vertex grid; S[v][t][c][c'], t = (dy+1)*3 + (dx+1).
+template <typename T>
+__global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ x,
+                                T* __restrict__ y, T alpha, const T* __restrict__ z, T beta) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nv = size_t(nvx) * nvy;
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    const T* sv = S + v * 36;
+    T acc = T(0);
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int wy = vy + dy;
+        if (wy < 0 || wy >= nvy) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int wx = vx + dx;
+            if (wx < 0 || wx >= nvx) continue;
+            const int t = (dy + 1) * 3 + (dx + 1);
+            const T* xw = x + 2 * (size_t(wy) * nvx + wx);
+            acc += sv[t * 4 + c * 2 + 0] * xw[0] + sv[t * 4 + c * 2 + 1] * xw[1];
+        }
+    }
+    T out = alpha * acc;
+    if (z) out += beta * z[g];
+    y[g] = out;
+}
+
+template <typename T>
+__global__ void k_stencil_dinv(size_t nv, const T* __restrict__ S, T* __restrict__ dinv) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    dinv[g] = T(1) / S[(g / 2) * 36 + 4 * 4 + c * 2 + c];
+}
+
+// d = c1 d + c2 D^{-1} r;  x = (x_zero ? 0 : x) + d
+template <typename T>
+__global__ void k_jacobi_cheb(size_t n, const T* __restrict__ r, const T* __restrict__ dinv, T* d,
+                              T* x, T c1, T c2, int x_zero) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    T v = c2 * dinv[g] * r[g];
+    if (c1 != T(0)) v += c1 * d[g];
+    d[g] = v;
+    if (x) x[g] = x_zero ? v : x[g] + v;
+}
+
+// fine (2 nxc + 1)^2 <- coarse (nxc + 1)^2 vertex grid, bilinear (add to y)
+template <typename T>
+__global__ void k_ph_add(int nxc, int nyc, const T* __restrict__ xc, T* __restrict__ yf) {
+    const int nfx = 2 * nxc + 1, nfy = 2 * nyc + 1;
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= size_t(nfx) * nfy * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int fx = int(v % nfx), fy = int(v / nfx);
+    T acc = T(0);
+    const int ix0 = fx / 2, ix1 = (fx + 1) / 2, iy0 = fy / 2, iy1 = (fy + 1) / 2;
+    const T wx = (fx % 2) ? T(0.5) : T(1), wy = (fy % 2) ? T(0.5) : T(1);
+    if (fx % 2 == 0 && fy % 2 == 0) {
+        acc = xc[2 * (size_t(iy0) * (nxc + 1) + ix0) + c];
+    } else if (fy % 2 == 0) {
+        acc = wx * (xc[2 * (size_t(iy0) * (nxc + 1) + ix0) + c] + xc[2 * (size_t(iy0) * (nxc + 1) + ix1) + c]);
+    } else if (fx % 2 == 0) {
+        acc = wy * (xc[2 * (size_t(iy0) * (nxc + 1) + ix0) + c] + xc[2 * (size_t(iy1) * (nxc + 1) + ix0) + c]);
+    } else {
+        acc = wx * wy * (xc[2 * (size_t(iy0) * (nxc + 1) + ix0) + c] + xc[2 * (size_t(iy0) * (nxc + 1) + ix1) + c] +
+                         xc[2 * (size_t(iy1) * (nxc + 1) + ix0) + c] + xc[2 * (size_t(iy1) * (nxc + 1) + ix1) + c]);
+    }
+    yf[g] += acc;
+}
+
+// R_h = P_h^T: coarse vertex gathers fine vertices 2I-1 .. 2I+1 with weights 1/2, 1, 1/2
+template <typename T>
+__global__ void k_rh(int nxc, int nyc, const T* __restrict__ rf, T* __restrict__ rc) {
+    const int nfx = 2 * nxc + 1, nfy = 2 * nyc + 1;
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= size_t(nxc + 1) * (nyc + 1) * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int I = int(v % (nxc + 1)), J = int(v / (nxc + 1));
+    T acc = T(0);
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int fy = 2 * J + dy;
+        if (fy < 0 || fy >= nfy) continue;
+        const T wy = dy == 0 ? T(1) : T(0.5);
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int fx = 2 * I + dx;
+            if (fx < 0 || fx >= nfx) continue;
+            const T wx = dx == 0 ? T(1) : T(0.5);
+            acc += wx * wy * rf[2 * (size_t(fy) * nfx + fx) + c];
+        }
+    }
+    rc[g] = acc;
+}
+
+// probe vector: 1 on vertices of colour (vx % 3, vy % 3) == (col % 3, col / 3), component cp
+template <typename T>
+__global__ void k_probe_vertices(int nvx, int nvy, int col, int cp, T* x) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= size_t(nvx) * nvy * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    x[g] = (c == cp && vx % 3 == col % 3 && vy % 3 == col / 3) ? T(1) : T(0);
+}
+
+// S[v][t][c][cp] from the 18 probe results Y[col*2 + cp][v][c]
+template <typename T>
+__global__ void k_extract_stencil(int nvx, int nvy, const T* __restrict__ Y, T* __restrict__ S) {
+    const size_t nv = size_t(nvx) * nvy;
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= nv * 36) return;
+    const size_t v = g / 36;
+    const int rem = int(g % 36), t = rem / 4, c = (rem / 2) % 2, cp = rem % 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    const int wx = vx + (t % 3) - 1, wy = vy + (t / 3) - 1;
+    T val = T(0);
+    if (wx >= 0 && wx < nvx && wy >= 0 && wy < nvy) {
+        const int col = (wy % 3) * 3 + (wx % 3);
+        val = Y[(size_t(col) * 2 + cp) * nv * 2 + 2 * v + c];
+    }
+    S[g] = val;
+}
+
+// probe vector on the Q_1 DG space: unit on local dof l of every element of
+// colour (ex % 3, ey % 3) == (col % 3, col / 3)
+template <typename T>
+__global__ void k_probe_elements(int nx, int ny, int col, int l, T* x) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= size_t(nx) * ny * 8) return;
+    const size_t e = g / 8;
+    const int ex = int(e % nx), ey = int(e / nx);
+    x[g] = (int(g % 8) == l && ex % 3 == col % 3 && ey % 3 == col / 3) ? T(1) : T(0);
+}
+
+// y = M x for a dense symmetric n x n matrix (row-major); one warp per row
+template <typename T>
+__global__ void k_dense_symv(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+    if (warp >= n) return;
+    const T* row = M + size_t(warp) * n;
+    T acc = T(0);
+    for (int j = lane; j < n; j += 32) acc += row[j] * x[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[warp] = acc;
+}
+
+// Dense inverse from a banded Cholesky factor L (lower, band width bw,
+// stored L[i][bw-1-(i-j)] for i-bw < j <= i): thread = column of the inverse.
+__global__ void k_band_chol_inverse(int n, int bw, const double* __restrict__ L, double* X) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    double* x = X + size_t(col) * n;   // column col of X, stored as a row (X symmetric)
+    for (int i = 0; i < n; ++i) {      // L y = e_col
+        double s = (i == col) ? 1.0 : 0.0;
+        const int j0 = i - bw + 1 > 0 ? i - bw + 1 : 0;
+        for (int j = j0; j < i; ++j) s -= L[size_t(i) * bw + (bw - 1 - (i - j))] * x[j];
+        x[i] = s / L[size_t(i) * bw + (bw - 1)];
+    }
+    for (int i = n - 1; i >= 0; --i) { // L^T x = y
+        double s = x[i];
+        const int j1 = i + bw - 1 < n - 1 ? i + bw - 1 : n - 1;
+        for (int j = i + 1; j <= j1; ++j) s -= L[size_t(j) * bw + (bw - 1 - (j - i))] * x[j];
+        x[i] = s / L[size_t(i) * bw + (bw - 1)];
+    }
+}
+
+template <typename T>
+__global__ void k_convert(size_t n, const double* __restrict__ a, T* __restrict__ b) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = T(a[g]);
+}
+
+inline unsigned nblk(size_t n, int t = 256) { return unsigned((n + t - 1) / t); }
+
+}  // namespace
+
+template <typename T>
+void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s) {
+    k_p_restrict<T><<<nblk(ne * 8), 256, 0, s>>>(ne, N, r, r1);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s) {
+    k_p_prolong_add<T><<<nblk(ne * 8), 256, 0, s>>>(ne, N, e1, y);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_pcd(int nx, int ny, const T* v, T* out, cudaStream_t s) {
+    k_pcd<T><<<nblk(size_t(nx) * ny * 8), 256, 0, s>>>(nx, ny, v, out);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_rdc(int nx, int ny, const T* r, T* out, cudaStream_t s) {
+    k_rdc<T><<<nblk(size_t(nx + 1) * (ny + 1) * 2), 256, 0, s>>>(nx, ny, r, out);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_stencil_apply(int nvx, int nvy, const T* S, const T* x, T* y, T alpha, const T* z,
+                          T beta, cudaStream_t s) {
+    k_stencil_apply<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_stencil_dinv(size_t nv, const T* S, T* dinv, cudaStream_t s) {
+    k_stencil_dinv<T><<<nblk(nv * 2), 256, 0, s>>>(nv, S, dinv);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_jacobi_cheb(size_t n, const T* r, const T* dinv, T* d, T* x, T c1, T c2, bool x_zero,
+                        cudaStream_t s) {
+    k_jacobi_cheb<T><<<nblk(n), 256, 0, s>>>(n, r, dinv, d, x, c1, c2, x_zero ? 1 : 0);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_ph_add(int nxc, int nyc, const T* xc, T* yf, cudaStream_t s) {
+    k_ph_add<T><<<nblk(size_t(2 * nxc + 1) * (2 * nyc + 1) * 2), 256, 0, s>>>(nxc, nyc, xc, yf);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_rh(int nxc, int nyc, const T* rf, T* rc, cudaStream_t s) {
+    k_rh<T><<<nblk(size_t(nxc + 1) * (nyc + 1) * 2), 256, 0, s>>>(nxc, nyc, rf, rc);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_probe_vertices(int nvx, int nvy, int col, int cp, T* x, cudaStream_t s) {
+    k_probe_vertices<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, col, cp, x);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_extract_stencil(int nvx, int nvy, const T* Y, T* S, cudaStream_t s) {
+    k_extract_stencil<T><<<nblk(size_t(nvx) * nvy * 36), 256, 0, s>>>(nvx, nvy, Y, S);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_probe_elements(int nx, int ny, int col, int l, T* x, cudaStream_t s) {
+    k_probe_elements<T><<<nblk(size_t(nx) * ny * 8), 256, 0, s>>>(nx, ny, col, l, x);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_dense_symv(int n, const T* M, const T* x, T* y, cudaStream_t s) {
+    k_dense_symv<T><<<nblk(size_t(n) * 32, 128), 128, 0, s>>>(n, M, x, y);
+    SIP_CHECK_LAUNCH();
+}
+void launch_band_chol_inverse(int n, int bw, const double* L, double* X, cudaStream_t s) {
+    k_band_chol_inverse<<<nblk(n, 32), 32, 0, s>>>(n, bw, L, X);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_convert(size_t n, const double* a, T* b, cudaStream_t s) {
+    k_convert<T><<<nblk(n), 256, 0, s>>>(n, a, b);
+    SIP_CHECK_LAUNCH();
+}
+
+#define SIP_INST(T)                                                                              \
+    template void launch_p_restrict<T>(size_t, int, const T*, T*, cudaStream_t);                \
+    template void launch_p_prolong_add<T>(size_t, int, const T*, T*, cudaStream_t);             \
+    template void launch_pcd<T>(int, int, const T*, T*, cudaStream_t);                          \
+    template void launch_rdc<T>(int, int, const T*, T*, cudaStream_t);                          \
+    template void launch_stencil_apply<T>(int, int, const T*, const T*, T*, T, const T*, T,     \
+                                          cudaStream_t);                                         \
+    template void launch_stencil_dinv<T>(size_t, const T*, T*, cudaStream_t);                   \
+    template void launch_jacobi_cheb<T>(size_t, const T*, const T*, T*, T*, T, T, bool,         \
+                                        cudaStream_t);                                           \
+    template void launch_ph_add<T>(int, int, const T*, T*, cudaStream_t);                       \
+    template void launch_rh<T>(int, int, const T*, T*, cudaStream_t);                           \
+    template void launch_probe_vertices<T>(int, int, int, int, T*, cudaStream_t);               \
+    template void launch_extract_stencil<T>(int, int, const T*, T*, cudaStream_t);              \
+    template void launch_probe_elements<T>(int, int, int, int, T*, cudaStream_t);               \
+    template void launch_dense_symv<T>(int, const T*, const T*, T*, cudaStream_t);              \
+    template void launch_convert<T>(size_t, const double*, T*, cudaStream_t);
+SIP_INST(double)
+SIP_INST(float)
+#undef SIP_INST
+
+}  // namespace sip

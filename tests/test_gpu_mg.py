@@ -1,0 +1,233 @@
+"""GPU parity of the hp-multigrid pieces, the inner PCG and the Stokes solve
+against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+from oracle import exact, krylov, materials, multigrid, sip
+from paper_1607_03777_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+SINK = synth.SINKER_BC
+BCS = [("navier",) * 4, SINK, ("dirichlet",) * 4, ("neumann", "dirichlet", "navier", "neumann")]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def pair(ctx, nx, ny, k, bc, eta, nh=0, seed=3, precision="fp64"):
+    prob = api.Problem(ctx, nx, ny, k, eta, bc=bc, n_hlevels=nh, seed=seed, precision=precision)
+    ref = sip.Problem(nx, ny, k, eta, bc=bc)
+    return prob, ref
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_block_jacobi(ctx, k):
+    for i, bc in enumerate(BCS):
+        nx, ny = 5, 4
+        eta = synth.random_eta(nx * ny, 40 + i, (0.0, 3.0))
+        eta[3] = eta.max() * 2       # a class element next to unique ones
+        prob, ref = pair(ctx, nx, ny, k, bc, eta)
+        A = sip.assemble_A(ref)
+        inv = multigrid.invert_blocks(multigrid.block_jacobi_blocks(A, ref.num.nb))
+        r = synth.random_vector(prob.n_u, 50 + i)
+        z = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        prob.block_jacobi(dev(r), z)
+        assert rel(host(z), multigrid.block_apply(inv, r)) < 1e-9, bc
+
+
+def test_block_jacobi_uniform_eta_uses_classes(ctx):
+    """All elements share one viscosity: every block is a scaled reference
+    block (class path) and the result still matches the oracle."""
+    for bc in BCS[:2]:
+        prob, ref = pair(ctx, 6, 6, 3, bc, np.full(36, 7.5))
+        A = sip.assemble_A(ref)
+        inv = multigrid.invert_blocks(multigrid.block_jacobi_blocks(A, ref.num.nb))
+        r = synth.random_vector(prob.n_u, 1)
+        z = torch.empty_like(dev(r))
+        prob.block_jacobi(dev(r), z)
+        assert rel(host(z), multigrid.block_apply(inv, r)) < 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_lambda_max_p(ctx, k):
+    nx = ny = 6
+    eta = synth.random_eta(nx * ny, 7, (0.0, 2.0))
+    prob, ref = pair(ctx, nx, ny, k, SINK, eta, seed=11)
+    A = sip.assemble_A(ref)
+    inv = multigrid.invert_blocks(multigrid.block_jacobi_blocks(A, ref.num.nb))
+    lam_ref = multigrid.estimate_lambda_max(lambda v: A @ v, lambda v: multigrid.block_apply(inv, v),
+                                            A.shape[0], seed=11)
+    assert abs(prob.lambda_max(-1) - lam_ref) < 1e-9 * lam_ref
+
+
+def test_p_transfers_exact(ctx):
+    prob, _ = pair(ctx, 4, 3, 3, SINK, np.ones(12))
+    r = synth.random_vector(prob.n_u, 3)
+    r1 = torch.empty(12 * 8, dtype=torch.float64, device="cuda")
+    prob.p_restrict(dev(r), r1)
+    P = multigrid.p_prolongation(3, 12, 1)
+    assert np.array_equal(host(r1), P.T @ r)
+    y = dev(r)
+    e1 = synth.random_vector(96, 4)
+    prob.p_prolong_add(dev(e1), y)
+    assert np.array_equal(host(y), r + P @ e1)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_apply_A1_galerkin(ctx, k):
+    for bc in BCS:
+        nx, ny = 5, 3
+        eta = synth.random_eta(nx * ny, k, (0.0, 3.0))
+        prob, ref = pair(ctx, nx, ny, k, bc, eta)
+        A = sip.assemble_A(ref)
+        P = multigrid.p_prolongation(k, nx * ny, 1)
+        A1 = P.T @ A @ P
+        x = synth.random_vector(nx * ny * 8, 9)
+        y = torch.empty(nx * ny * 8, dtype=torch.float64, device="cuda")
+        prob.apply_A1(dev(x), y)
+        assert rel(host(y), A1 @ x) < 1e-10, bc
+
+
+def test_pcd_rdc(ctx):
+    nx, ny = 6, 5
+    prob, _ = pair(ctx, nx, ny, 2, SINK, np.ones(nx * ny))
+    Pcd = multigrid.continuous_to_dg(nx, ny)
+    v = synth.random_vector(2 * (nx + 1) * (ny + 1), 1)
+    u1 = torch.empty(nx * ny * 8, dtype=torch.float64, device="cuda")
+    prob.cd_prolong(dev(v), u1)
+    assert rel(host(u1), Pcd @ v) < 1e-14
+    w = synth.random_vector(nx * ny * 8, 2)
+    vv = torch.empty(2 * (nx + 1) * (ny + 1), dtype=torch.float64, device="cuda")
+    prob.dc_restrict(dev(w), vv)
+    assert rel(host(vv), Pcd.T @ w) < 1e-14
+
+
+@pytest.mark.parametrize("bc", [SINK, ("navier",) * 4, ("dirichlet",) * 4])
+def test_hlevel_stencils_and_coarse(ctx, bc):
+    nx = ny = 16
+    k = 2
+    eta, _ = materials.rasterise_inclusions(nx, ny, synth.single_box_inclusion(nx, k, 1e3).shapes)
+    prob, ref = pair(ctx, nx, ny, k, bc, eta, nh=2, seed=5)
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, 2, seed=5)
+    nl, _, _ = prob.hlevel_dims(0)
+    assert nl == 3
+    mats = [lv.A for lv in mg.h.levels] + [mg.h.coarse_A]
+    for l in range(3):
+        _, nvx, nvy = prob.hlevel_dims(l)
+        x = synth.random_vector(2 * nvx * nvy, 20 + l)
+        y = torch.empty_like(dev(x))
+        prob.hlevel_apply(l, dev(x), y)
+        assert rel(host(y), mats[l] @ x) < 1e-10, l
+        if l < 2:
+            assert abs(prob.lambda_max(l) - mg.h.levels[l].lmax) < 1e-9 * mg.h.levels[l].lmax
+    # coarsest direct solve
+    _, nvx, nvy = prob.hlevel_dims(2)
+    b = synth.random_vector(2 * nvx * nvy, 5)
+    x = torch.empty_like(dev(b))
+    prob.coarse_solve(dev(b), x)
+    assert rel(host(x), np.linalg.solve(mg.h.coarse_A, b)) < 1e-9
+
+
+@pytest.mark.parametrize("nh,k,bc", [(0, 2, ("dirichlet",) * 4), (2, 3, SINK), (1, 2, ("navier",) * 4)])
+def test_vcycle_fp64(ctx, nh, k, bc):
+    nx = ny = 16
+    eta, _ = materials.rasterise_inclusions(nx, ny, synth.single_box_inclusion(nx, k, 1e3).shapes)
+    prob, ref = pair(ctx, nx, ny, k, bc, eta, nh=nh, seed=9)
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, nh, seed=9)
+    assert abs(prob.lambda_max(-1) - mg.lmax) < 1e-9 * mg.lmax
+    r = synth.random_vector(prob.n_u, 77)
+    z = torch.empty_like(dev(r))
+    prob.vcycle(dev(r), z)
+    assert rel(host(z), mg(r)) < 1e-9
+    prob.vcycle(dev(r), z)      # repeatable (graph replay)
+    assert rel(host(z), mg(r)) < 1e-9
+
+
+def test_vcycle_fp32(ctx):
+    nx = ny = 16
+    k = 3
+    eta, _ = materials.rasterise_inclusions(nx, ny, synth.single_box_inclusion(nx, k, 1e3).shapes)
+    prob, ref = pair(ctx, nx, ny, k, SINK, eta, nh=2, seed=9, precision="mixed")
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, 2, seed=9)
+    r = synth.random_vector(prob.n_u, 78).astype(np.float32)
+    z = torch.empty(prob.n_u, dtype=torch.float32, device="cuda")
+    prob.vcycle_f32(dev(r, torch.float32), z)
+    assert rel(host(z), mg(r.astype(np.float64))) < 2e-4
+
+
+def test_inner_pcg(ctx):
+    nx = ny = 16
+    k = 2
+    eta, rho = materials.rasterise_inclusions(nx, ny, synth.single_box_inclusion(nx, k, 1e2).shapes)
+    prob, ref = pair(ctx, nx, ny, k, SINK, eta, nh=1, seed=2)
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, 1, seed=2)
+    t = sip.rhs_body_force(ref, rho)
+    y_ref, its_ref = krylov.pcg(lambda v: A @ v, mg, t, 1e-6, 200)
+    y = torch.empty_like(dev(t))
+    its = prob.inner_solve(dev(t), y, rtol=1e-6, max_it=200)
+    assert abs(its - its_ref) <= 1
+    assert np.linalg.norm(A @ host(y) - t) < 1e-6 * np.linalg.norm(t)
+    assert rel(host(y), y_ref) < 1e-5
+
+
+def _true_residual(ref, u, p, f):
+    A, B = sip.assemble_A(ref), sip.assemble_B(ref)
+    K = krylov.stokes_matrix(A, B)
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    x = np.concatenate([u, p])
+    return np.linalg.norm(b - K @ x) / np.linalg.norm(b), A, B
+
+
+def test_solve_dirichlet_mms_two_level(ctx):
+    """8x8, k = 2, Dirichlet manufactured solution, A_p(Q^2_1) two-level
+    preconditioner, rtol 1e-10: GPU solution = sparse-direct oracle solution."""
+    sol = exact.SmoothDirichlet()
+    nx = ny = 8
+    prob, ref = pair(ctx, nx, ny, 2, ("dirichlet",) * 4, np.ones(64), nh=0, seed=7)
+    f = sip.rhs_force(ref, sol.f)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-10)
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.5e-10, rep
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-8
+    assert rel(host(p), p_ref) < 1e-7    # p is less well conditioned than u
+    assert abs(host(p)[::4].mean()) < 1e-12      # zero-mean pressure
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_box_inclusion(ctx, precision):
+    """Single box inclusion 1e4 (Neumann top, Navier elsewhere), Q^2_1 + 1
+    h-coarsening, rtol 1e-8: true FP64 residual (oracle matrices) <= 1e-8 and
+    the solution matches the sparse-direct oracle."""
+    nx = ny = 16
+    k = 3
+    wl = synth.single_box_inclusion(nx, k, 1e4, n_hlevels=1)
+    eta, rho = materials.rasterise_inclusions(nx, ny, wl.shapes)
+    prob, ref = pair(ctx, nx, ny, k, wl.bc, eta, nh=1, seed=1, precision=precision)
+    f = sip.rhs_body_force(ref, rho)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-8, inner_rtol=1e-3, max_outer=1000)
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.05e-8, rep
+    assert abs(rep["rel_residual"] - res) < 1e-9
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-5
