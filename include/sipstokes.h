@@ -205,8 +205,10 @@ typedef struct {
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES with the upper block-triangular preconditioner
- * (eq. discretestokespc): y_p = S*^{-1} x_p with S* the pressure mass scaled
- * by 1/eta_K (diagonal), y_u ~ A^{-1}(x_u - B y_p) by the inner PCG with the
+ * (eq. discretestokespc) whose Schur block is the saddle matrix's own Schur
+ * complement -B^T A^{-1} B approximated by -S*, S* the pressure mass scaled by
+ * 1/eta_K (diagonal, Sec. 5): y_p = -S*^{-1} x_p,
+ * y_u ~ A^{-1}(x_u - B y_p) by the inner PCG with the
  * hp-multigrid V-cycle.  Orthogonalisation: classical Gram-Schmidt twice.
  * Without a Neumann side the constant pressure is projected out of every
  * pressure vector and p is returned with zero mean (Sec. 5).  g_p may be NULL

@@ -13,6 +13,14 @@ Test infrastructure only (see ``oracle/__init__``).
   A^{-1} replaced by an inner PCG solve (Sec. 6).  Stopping test: residual
   2-norm reduced by ``rtol`` from the initial one (Sec. 7 settings).
   Orthogonalisation: classical Gram-Schmidt applied twice.
+
+Reading of the Schur block: the preconditioner's lower-right block is the
+Schur complement of the saddle matrix itself, 0 - B^T A^{-1} B (negative
+definite; the convention of the PETSc block factorisations the paper ran
+with), approximated by -S*.  With exact blocks both signs give convergence
+in two iterations (eigenvalue 1 with a 2x2 Jordan block for this sign,
++-1 for the other); with the inexact inner solve this sign reproduces the
+paper's outer iteration counts and the other does not.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -69,8 +77,8 @@ def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
 
 class BlockPreconditioner:
     """Action of the upper block-triangular preconditioner inverse
-    (eq. discretestokespc) with S -> S* and A^{-1} -> inner PCG:
-        y_p = S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
+    (eq. discretestokespc) with the Schur block -S* and A^{-1} -> inner PCG:
+        y_p = -S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
 
     def __init__(self, A, B, s_diag, inner_precond, inner_rtol=1e-3,
                  inner_maxit=200, null_p=None):
@@ -83,7 +91,7 @@ class BlockPreconditioner:
     def __call__(self, x):
         n_u = self.A.shape[0]
         xu, xp = x[:n_u], x[n_u:]
-        yp = xp / self.s
+        yp = -xp / self.s
         if self.null_p is not None:
             yp = project_out(yp, self.null_p)
         t = xu - self.B @ yp

@@ -670,7 +670,7 @@ namespace {
 
 __global__ void k_sinv(size_t ne, int mp, double area_quarter, const double* eta, double* out) {
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g < ne * mp) out[g] = eta[g / mp] / area_quarter;
+    if (g < ne * mp) out[g] = -eta[g / mp] / area_quarter;
 }
 
 }  // namespace
@@ -709,8 +709,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
     }
     Workspace& W = *P->ws;
     if (!W.sinv_ready) {
-        // S*^{-1}: inverse of the pressure mass (h_x h_y / 4 on the orthonormal
-        // basis) scaled by 1/eta_K
+        // Schur block of the preconditioner: the saddle matrix's own Schur
+        // complement -B^T A^{-1} B, approximated by -S*, S* = the pressure mass
+        // (h_x h_y / 4 on the orthonormal basis) scaled by 1/eta_K; stored
+        // here as the diagonal of its inverse, -eta_K / (h_x h_y / 4)
         k_sinv<<<unsigned((n_p + 255) / 256), 256, 0, s>>>(
             size_t(P->ne), P->mp, 0.25 * P->geom.hx * P->geom.hy, P->eta_d.as<double>(),
             W.sinv.as<double>());
@@ -752,7 +754,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
     int inner_total = 0, inner_max = 0, inner_calls = 0;
     // z = P^{-1} v
     auto precond = [&](const double* v, double* z) {
-        launch_vmul<double>(n_p, v + n_u, W.sinv.as<double>(), z + n_u, s);   // y_p = S*^{-1} v_p
+        launch_vmul<double>(n_p, v + n_u, W.sinv.as<double>(), z + n_u, s);   // y_p = -S*^{-1} v_p
         project(z);
         launch_apply_B<double>(P->k, P->geom, z + n_u, W.tu.as<double>(), s);
         launch_axpby<double>(n_u, 1.0, v, -1.0, W.tu.as<double>(), s);        // t = v_u - B y_p
