@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -173,6 +175,9 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1000.0)
+    if args.profile_only:
+        return {"metric": METRIC, "value": value, "unit": UNIT, "profile_only": True,
+                "solve_report": r64[-1]}
 
     # mixed-precision form on the same workload
     prob32, f32, u32, p32, t32, r32, _ = timed("mixed", args.steps, max(1, args.warmup - 1))

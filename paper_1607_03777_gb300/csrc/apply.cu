@@ -31,6 +31,9 @@ struct ApplyArgs {
     T alpha, beta;
     int nx, ny;
     T hx, hy;
+    T two_over_hx, two_over_hy;
+    T c2hy_hx, chx_hy, c2hx_hy, chy_hx;   // 2hy/hx, hx/hy, 2hx/hy, hy/hx
+    FaceGeo<T> fgx, fgy;                  // faces with x- and y-normal
     int bc[4];
     T pen_x, pen_y;
     Tab1D<N, T> tab;
@@ -70,7 +73,6 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
     const int nx = a.nx, ny = a.ny;
     const int ex0 = blockIdx.x * EX, ey = blockIdx.y;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const T hx = a.hx, hy = a.hy;
 
     // ---- stage 0: load rows ey-1, ey, ey+1, columns ex0-1 .. ex0+EX
     {
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
             d += u[i] * dt[i];
         }
         tv[q] = v;
-        td[q] = d * (T(2) / hx);
+        td[q] = d * a.two_over_hx;
     }
     // ---- stage 1b: traces on the bottom / top faces of each tile element
     for (int q = tid; q < EX * 8 * N; q += nt) {
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
             d += u[j * N] * dt[j];
         }
         hv[q] = v;
-        hd[q] = d * (T(2) / hy);
+        hd[q] = d * a.two_over_hy;
     }
     // ---- stage 1c: volume cross-term intermediates
     //   wx[t][j][a] = sum_i D[a][i] uy[j][i],  wy[t][b][i] = sum_j D[b][j] ux[j][i]
@@ -156,7 +158,8 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
         if (ex >= nx) continue;
         const T etaK = seta[EXH + t + 1];
         const T *vo, *dv, *vn, *dn;
-        T etaN = T(0), s, hn, ht, pen;
+        T etaN = T(0), s, pen;
+        const FaceGeo<T>* fg;
         int nc, kind, nbr_ok;
         if (F < 2) {  // vertical faces: d = x
             const int f = t + F;                  // face index; L: f = t, R: f = t + 1
@@ -169,8 +172,7 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
             nbr_ok = F == 0 ? (ex > 0) : (ex < nx - 1);
             kind = nbr_ok ? 0 : 1 + a.bc[F];
             if (nbr_ok) etaN = seta[EXH + t + (F == 0 ? 0 : 2)];
-            hn = hx;
-            ht = hy;
+            fg = &a.fgx;
             nc = 0;
             pen = a.pen_x;
         } else {  // horizontal faces: d = y
@@ -183,15 +185,14 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
             nbr_ok = face == 0 ? (ey > 0) : (ey < ny - 1);
             kind = nbr_ok ? 0 : 1 + a.bc[F];
             if (nbr_ok) etaN = seta[(face == 0 ? 0 : 2) * EXH + t + 1];
-            hn = hy;
-            ht = hx;
+            fg = &a.fgy;
             nc = 1;
             pen = a.pen_y;
         }
         const T eta_e = kind == 0 ? (etaK > etaN ? etaK : etaN) : etaK;
         const T sigma = pen * eta_e * (kind == 0 ? T(1) : T(2));
         T P, Q;
-        face_pq<N, T>(kind, c, m, nc, s, hn, ht, etaK, etaN, sigma, vo, dv, vn, dn, a.tab.D, P, Q);
+        face_pq<N, T>(kind, c, m, nc, s, *fg, etaK, etaN, sigma, vo, dv, vn, dn, a.tab.D, P, Q);
         pq[((t * 4 + F) * 2 + 0) * 2 * N + c * N + m] = P;
         pq[((t * 4 + F) * 2 + 1) * 2 * N + c * N + m] = Q;
     }
@@ -214,8 +215,8 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
                 v2 += G[b * N + i] * u[i * N + av];
                 v3 += D[i * N + b] * wx[t * NN + i * N + av];
             }
-            v1 *= T(2) * hy / hx;
-            v2 *= hx / hy;
+            v1 *= a.c2hy_hx;
+            v2 *= a.chx_hy;
         } else {
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
                 v2 += G[av * N + i] * u[NN + b * N + i];
                 v3 += D[i * N + av] * wy[t * NN + b * N + i];
             }
-            v1 *= T(2) * hx / hy;
-            v2 *= hy / hx;
+            v1 *= a.c2hx_hy;
+            v2 *= a.chy_hx;
         }
         T acc = etaK * (v1 + v2 + v3);
         const T* pL = pq + ((t * 4 + 0) * 2) * 2 * N + c * N;
@@ -256,6 +257,14 @@ void apply_sip_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const
     a.ny = g.ny;
     a.hx = T(g.hx);
     a.hy = T(g.hy);
+    a.two_over_hx = T(2.0 / g.hx);
+    a.two_over_hy = T(2.0 / g.hy);
+    a.c2hy_hx = T(2.0 * g.hy / g.hx);
+    a.chx_hy = T(g.hx / g.hy);
+    a.c2hx_hy = T(2.0 * g.hx / g.hy);
+    a.chy_hx = T(g.hy / g.hx);
+    a.fgx = make_face_geo<T>(g.hx, g.hy);
+    a.fgy = make_face_geo<T>(g.hy, g.hx);
     for (int i = 0; i < 4; ++i) a.bc[i] = g.bc[i];
     a.pen_x = T(g.pen_x);
     a.pen_y = T(g.pen_y);

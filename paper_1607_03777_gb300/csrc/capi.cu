@@ -127,12 +127,10 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
             p->geom1 = p->geom;   // the Galerkin A_1 keeps the fine-k penalty
             p->eta_host = eta;
             p->eta_d.alloc(ne * sizeof(double));
-            p->eta_f.alloc(ne * sizeof(float));
-            std::vector<float> ef(eta.begin(), eta.end());
             SIP_CUDA(cudaMemcpy(p->eta_d.ptr, eta.data(), ne * sizeof(double),
                                 cudaMemcpyHostToDevice));
-            SIP_CUDA(cudaMemcpy(p->eta_f.ptr, ef.data(), ne * sizeof(float),
-                                cudaMemcpyHostToDevice));
+            p->derive_eta(nullptr);
+            SIP_CUDA(cudaDeviceSynchronize());
         } catch (...) {
             delete p;
             throw;
@@ -173,7 +171,7 @@ sip_status sip_problem_update_eta(sip_problem* p, const double* eta, void* strea
         }
         if (on_dev && !sip::eta_valid(ne, p->eta_d.as<double>(), s))
             throw Error(SIP_ERR_INVALID_ARG, "eta must be finite and positive");
-        sip::launch_cast<double, float>(ne, p->eta_d.as<double>(), p->eta_f.as<float>(), s);
+        p->derive_eta(s);
         if (p->mg64) p->mg64->ready = false;
         if (p->mg32) p->mg32->ready = false;
         if (p->ws) p->ws->sinv_ready = false;

@@ -119,6 +119,8 @@ struct Multigrid {
     // z = V(r): one V-cycle of Algorithm 1 with y0 = 0 (r, z of length n_u)
     void vcycle(const T* r, T* z, cudaStream_t s);
     void vcycle_direct(cudaStream_t s);   // vin -> vout, kernels only
+    // z = V(r) for FP64 vectors: r rounded to T, the cycle in T, z widened
+    void vcycle_widen(const double* r, double* z, cudaStream_t s);
     void bj(const T* r, T* z, cudaStream_t s);
     void coarse_solve(const T* b1, T* e1, cudaStream_t s);
     void hlevel_apply(int l, const T* x, T* y, cudaStream_t s);
@@ -140,11 +142,14 @@ struct Workspace {
     int restart = 0;
     size_t n = 0;
     DeviceBuffer V, Z, w, x, r, b, tu, yu64, sinv, ws, sc, hbuf;
-    DeviceBuffer t32, y32;   // inner solve in FP32 (mixed precision)
-    HostScalars hs;
+    DeviceBuffer cg_r, cg_d, cg_q, cg_z, sc_in;   // FP64 inner PCG of the mixed form
+    HostScalars hs, hs_in;
     bool sinv_ready = false;
     int64_t bytes() const;
 };
+
+int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, double rtol,
+                    int maxit, cudaStream_t s);
 
 sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,
@@ -160,7 +165,9 @@ struct sip_problem {
     sip::OpGeom geom{};      // the SIP operator of degree k
     sip::OpGeom geom1{};     // the Galerkin Q_1 operator (fine-k penalty)
     std::vector<double> eta_host;
-    sip::DeviceBuffer eta_d, eta_f;
+    sip::DeviceBuffer eta_d, eta_f, eta_inv_d, eta_inv_f;
+    // refresh the FP32 copy and the FP64 / FP32 reciprocals of eta_d
+    void derive_eta(cudaStream_t s);
     std::unique_ptr<sip::Multigrid<double>> mg64;
     std::unique_ptr<sip::Multigrid<float>> mg32;
     std::unique_ptr<sip::Workspace> ws;

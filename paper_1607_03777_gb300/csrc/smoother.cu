@@ -70,7 +70,7 @@ __device__ double block_entry(int r, int s, double etaK, const int kind[4], cons
         const int mt = d == 0 ? b : a;   // test mode along the face
         const int qt = d == 0 ? a : b;   // test mode along the normal
         double P, Q;
-        face_pq<N, double>(kind[F], c, mt, d, sgn, d == 0 ? hx : hy, d == 0 ? hy : hx, etaK, 0.0,
+        face_pq<N, double>(kind[F], c, mt, d, sgn, make_face_geo<double>(d == 0 ? hx : hy, d == 0 ? hy : hx), etaK, 0.0,
                            sig[F], vo, dv, zero, zero, D, P, Q);
         acc += l[qt] * P + dl[qt] * Q;
     }
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
                                                   const int* __restrict__ emap,
                                                   const T* __restrict__ cls_inv,
                                                   const T* __restrict__ uniq_inv,
-                                                  const T* __restrict__ eta, T c1, T c2,
+                                                  const T* __restrict__ eta_inv, T c1, T c2,
                                                   int x_zero) {
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
         T scale;
         if (m < 0) {
             Minv = cls_inv + size_t(-m - 1) * NB * NB;
-            scale = T(1) / eta[e];
+            scale = eta_inv[e];
         } else {
             Minv = uniq_inv + size_t(m) * NB * NB;
             scale = T(1);

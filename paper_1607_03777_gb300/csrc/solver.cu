@@ -35,6 +35,12 @@ template <>
 const double* eta_of<double>(sip_problem* P) { return P->eta_d.as<double>(); }
 template <>
 const float* eta_of<float>(sip_problem* P) { return P->eta_f.as<float>(); }
+template <typename T>
+const T* eta_inv_of(sip_problem* P);
+template <>
+const double* eta_inv_of<double>(sip_problem* P) { return P->eta_inv_d.as<double>(); }
+template <>
+const float* eta_inv_of<float>(sip_problem* P) { return P->eta_inv_f.as<float>(); }
 
 // Chebyshev recurrence for SPD operators on [lo, hi] (Saad, Iterative
 // Methods for Sparse Linear Systems, Sec. 12.3): coefficients of step s
@@ -225,7 +231,7 @@ void Multigrid<T>::build_blocks(cudaStream_t s) {
 template <typename T>
 void Multigrid<T>::bj(const T* r, T* z, cudaStream_t s) {
     launch_bj_apply<T>(N, int(ne), r, z, nullptr, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(),
-                       eta_of<T>(P), T(0), T(1), true, s);
+                       eta_inv_of<T>(P), T(0), T(1), true, s);
 }
 
 // Arnoldi (GMRES) estimate of the largest eigenvalue of M^{-1} A (Sec. 6):
@@ -523,13 +529,14 @@ void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
     else
         launch_apply_sip<T>(N, P->geom, y, r, eta, T(-1), b, T(1), s);   // r = b - A y
     double rho = 1.0 / ch.sigma;
-    launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(), eta,
+    const T* einv = eta_inv_of<T>(P);
+    launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(), einv,
                        T(0), T(1.0 / ch.theta), zero, s);
     for (int st = 1; st < P->desc.cheb_steps_p; ++st) {
         launch_apply_sip<T>(N, P->geom, dd, r, eta, T(-1), r, T(1), s);  // r -= A d
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
         launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(),
-                           eta, T(rn * rho), T(2.0 * rn / ch.delta), false, s);
+                           einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s);
         rho = rn;
     }
 }
@@ -656,14 +663,64 @@ int Multigrid<T>::inner_pcg(const T* t, T* y, double rtol, int maxit, cudaStream
     return std::min(it, maxit);
 }
 
+template <typename T>
+void Multigrid<T>::vcycle_widen(const double* r, double* z, cudaStream_t s) {
+    launch_cast<double, T>(n_u, r, vin.template as<T>(), s);
+    SIP_CUDA(cudaGraphLaunch(graph, s));
+    launch_counter() += graph_kernels;
+    launch_cast<T, double>(n_u, vout.template as<T>(), z, s);
+}
+
 template struct Multigrid<double>;
 template struct Multigrid<float>;
+
+// Inner PCG of the mixed form: FP64 iterate, residual, operator and dot
+// products; the V-cycle (smoother, transfers, coarse solve) in FP32, the
+// residual rounded to FP32 on the way in and the correction widened on the
+// way out.  Same stopping test as the FP64 form.
+int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, double rtol,
+                    int maxit, cudaStream_t s) {
+    Multigrid<float>& mg = *P->mg32;
+    const size_t n_u = size_t(P->n_u);
+    double* r = W.cg_r.as<double>();
+    double* dd = W.cg_d.as<double>();
+    double* q = W.cg_q.as<double>();
+    double* z = W.cg_z.as<double>();
+    double* scd = W.sc_in.as<double>();   // [0] rz, [1] dq, [2] rr, [3] rz_new
+    double* wsd = W.ws.as<double>();
+    double* hp = W.hs_in.p;
+    const double* eta = P->eta_d.as<double>();
+    SIP_CUDA(cudaMemsetAsync(y, 0, n_u * sizeof(double), s));
+    launch_dot<double>(n_u, t, t, scd + 2, wsd, s);
+    const double nt = std::sqrt(read_scalar(scd + 2, hp, s));
+    if (nt == 0.0) return 0;
+    if (!std::isfinite(nt)) throw Error(SIP_ERR_BREAKDOWN, "non-finite inner right-hand side");
+    launch_axpby<double>(n_u, 1.0, t, 0.0, r, s);
+    mg.vcycle_widen(r, z, s);
+    launch_dot<double>(n_u, r, z, scd + 0, wsd, s);
+    launch_axpby<double>(n_u, 1.0, z, 0.0, dd, s);
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+        launch_apply_sip<double>(P->n, P->geom, dd, q, eta, 1.0, nullptr, 0.0, s);
+        launch_dot<double>(n_u, dd, q, scd + 1, wsd, s);
+        launch_pcg_update<double>(n_u, dd, q, y, r, scd + 0, scd + 1, s);
+        launch_dot<double>(n_u, r, r, scd + 2, wsd, s);
+        const double rr = std::sqrt(read_scalar(scd + 2, hp, s));
+        if (!std::isfinite(rr)) throw Error(SIP_ERR_BREAKDOWN, "non-finite inner residual");
+        if (rr < rtol * nt || it == maxit) break;
+        mg.vcycle_widen(r, z, s);
+        launch_dot<double>(n_u, r, z, scd + 3, wsd, s);
+        launch_pcg_dir<double>(n_u, z, dd, scd + 3, scd + 0, s);
+        SIP_CUDA(cudaMemcpyAsync(scd + 0, scd + 3, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    return std::min(it, maxit);
+}
 
 // ---------------------------------------------------------------- FGMRES
 int64_t Workspace::bytes() const {
     return int64_t(V.bytes + Z.bytes + w.bytes + x.bytes + r.bytes + b.bytes + tu.bytes +
-                   yu64.bytes + sinv.bytes + ws.bytes + sc.bytes + hbuf.bytes + t32.bytes +
-                   y32.bytes);
+                   yu64.bytes + sinv.bytes + ws.bytes + sc.bytes + hbuf.bytes + cg_r.bytes +
+                   cg_d.bytes + cg_q.bytes + cg_z.bytes + sc_in.bytes);
 }
 
 namespace {
@@ -701,10 +758,6 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         w->ws.alloc(reduction_workspace_doubles(restart + 2) * sizeof(double));
         w->sc.alloc(size_t(restart + 8) * sizeof(double));
         w->hbuf.alloc(size_t(restart + 8) * sizeof(double));
-        if (mixed) {
-            w->t32.alloc(n_u * sizeof(float));
-            w->y32.alloc(n_u * sizeof(float));
-        }
         P->ws = std::move(w);
     }
     Workspace& W = *P->ws;
@@ -719,9 +772,9 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         SIP_CHECK_LAUNCH();
         W.sinv_ready = true;
     }
-    if (mixed && !W.t32.ptr) {
-        W.t32.alloc(n_u * sizeof(float));
-        W.y32.alloc(n_u * sizeof(float));
+    if (mixed) {
+        for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
+        W.sc_in.alloc(8 * sizeof(double));
     }
     double* V = W.V.as<double>();
     double* Z = W.Z.as<double>();
@@ -760,10 +813,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         launch_axpby<double>(n_u, 1.0, v, -1.0, W.tu.as<double>(), s);        // t = v_u - B y_p
         int its;
         if (mixed) {
-            launch_cast<double, float>(n_u, W.tu.as<double>(), W.t32.as<float>(), s);
-            its = P->mg32->inner_pcg(W.t32.as<float>(), W.y32.as<float>(), o.inner_rtol, o.max_inner,
-                                     s, nullptr);
-            launch_cast<float, double>(n_u, W.y32.as<float>(), z, s);
+            its = inner_pcg_mixed(P, W, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s);
         } else {
             its = P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s, nullptr);
         }
@@ -896,11 +946,33 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
 }  // namespace sip
 
 int64_t sip_problem::device_bytes() const {
-    int64_t b = int64_t(eta_d.bytes + eta_f.bytes);
+    int64_t b = int64_t(eta_d.bytes + eta_f.bytes + eta_inv_d.bytes + eta_inv_f.bytes);
     if (mg64) b += mg64->bytes();
     if (mg32) b += mg32->bytes();
     if (ws) b += ws->bytes();
     return b;
+}
+
+namespace {
+__global__ void k_derive_eta(size_t n, const double* eta, float* ef, double* inv, float* invf) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const double e = eta[g];
+    ef[g] = float(e);
+    inv[g] = 1.0 / e;
+    invf[g] = float(1.0 / e);
+}
+}  // namespace
+
+void sip_problem::derive_eta(cudaStream_t s) {
+    const size_t n = size_t(ne);
+    eta_f.alloc(n * sizeof(float));
+    eta_inv_d.alloc(n * sizeof(double));
+    eta_inv_f.alloc(n * sizeof(float));
+    k_derive_eta<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, eta_d.as<double>(), eta_f.as<float>(),
+                                                         eta_inv_d.as<double>(),
+                                                         eta_inv_f.as<float>());
+    SIP_CHECK_LAUNCH();
 }
 
 void sip_problem::ensure_setup(cudaStream_t s) {
