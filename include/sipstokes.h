@@ -234,6 +234,27 @@ sip_status sip_rasterise_inclusions(sip_ctx* ctx, int nx, int ny, double lx, dou
                                     const double* shapes_host, int n_shapes, double eta_bg,
                                     double rho_bg, double* eta_out, double* rho_out,
                                     void* stream);
+/* Allocation-free variant of sip_rasterise_inclusions (the paper has no
+ * counterpart: this is a service to callers that must not allocate device
+ * memory -- e.g. code running inside a framework that owns all device memory
+ * through its own pool and budget, or a latency-bound loop where cudaMalloc /
+ * cudaFree would synchronise the whole device).  Same arguments, same results.
+ * The inclusion records are staged in a fixed device array compiled into the
+ * library (SIP_NOALLOC_MAX_SHAPES records, 224 KiB on every GPU that loads
+ * the library, held until the process exits) instead of a fresh allocation;
+ * n_shapes > SIP_NOALLOC_MAX_SHAPES is rejected with SIP_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address, so make
+ * that first call before any stream capture.  All calls share the one
+ * array: calls whose copies and kernels may overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  The
+ * records are copied with cudaMemcpyAsync on `stream`; the call does not
+ * synchronise the stream (a pinned shapes_host must stay valid until the
+ * stream has passed the copy). */
+#define SIP_NOALLOC_MAX_SHAPES 4096
+sip_status sip_rasterise_inclusions_noalloc(sip_ctx* ctx, int nx, int ny, double lx, double ly,
+                                            const double* shapes_host, int n_shapes,
+                                            double eta_bg, double rho_bg, double* eta_out,
+                                            double* rho_out, void* stream);
 /* f_u = the load vector of the body force f = (0, -g rho_K) (eq. rhs_f,
  * Sec. 7.3); rho: device array of nx*ny. */
 sip_status sip_rhs_body_force(sip_problem* prob, const double* rho, double g, double* f_u,

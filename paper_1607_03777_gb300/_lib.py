@@ -105,6 +105,10 @@ SIGNATURES = {
     "sip_rasterise_inclusions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, _VP, _VP]),
+    "sip_rasterise_inclusions_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_double, ctypes.c_double, _VP,
+                                                        ctypes.c_int, ctypes.c_double,
+                                                        ctypes.c_double, _VP, _VP, _VP]),
     "sip_rhs_body_force": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _VP]),
 }
 

@@ -9,6 +9,8 @@
 // along the face: for the face of K with outward normal s e_d the test mode
 // (q along d, m along the face) receives l_q(s) P[m] + l_q'(s) Q[m], where P
 // and Q combine the traces of K and its neighbour.
+#include <mutex>
+
 #include "sip_face.cuh"
 #include "sip_internal.h"
 
@@ -518,4 +520,81 @@ void launch_rasterise(int nx, int ny, double lx, double ly, const double* shapes
     SIP_CHECK_LAUNCH();
 }
 
+// ------------------------------------------------- allocation-free rasteriser
+// Device-side home of the inclusion records for sip_rasterise_inclusions_noalloc.
+// Every GPU that loads this library holds it (SIP_NOALLOC_MAX_SHAPES records
+// of 7 doubles, 224 KiB) until the process exits.  In host code the name
+// below is only a host-side stand-in: its device address comes from
+// cudaGetSymbolAddress, taken once per device.
+static __device__ __align__(256) double g_noalloc_shapes[SIP_NOALLOC_MAX_SHAPES * 7];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static record array on the current device; resolved
+// on the first call per device (the caller made that device current).
+double* noalloc_shapes_on(int device) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_shapes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(SIP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[device] = static_cast<double*>(p);
+    }
+    return g_noalloc_ptr[device];
+}
+
+}  // namespace
+
 }  // namespace sip
+
+extern "C" sip_status sip_rasterise_inclusions_noalloc(sip_ctx* ctx, int nx, int ny, double lx,
+                                                       double ly, const double* shapes_host,
+                                                       int n_shapes, double eta_bg, double rho_bg,
+                                                       double* eta_out, double* rho_out,
+                                                       void* stream) {
+    if (!ctx) return SIP_ERR_INVALID_ARG;
+    try {
+        using sip::require;
+        require(nx >= 1 && ny >= 1 && std::isfinite(lx) && std::isfinite(ly) && lx > 0 && ly > 0,
+                "bad mesh");
+        require(n_shapes >= 0 && (n_shapes == 0 || shapes_host), "bad inclusion list");
+        require(n_shapes <= SIP_NOALLOC_MAX_SHAPES,
+                "sip_rasterise_inclusions_noalloc takes at most SIP_NOALLOC_MAX_SHAPES (4096) "
+                "inclusion records");
+        require(eta_out && rho_out, "null output");
+        require(std::isfinite(eta_bg) && eta_bg > 0 && std::isfinite(rho_bg),
+                "bad background material");
+        for (int i = 0; i < n_shapes; ++i) {
+            const double* s = shapes_host + 7 * i;
+            for (int j = 0; j < 7; ++j) require(std::isfinite(s[j]), "non-finite inclusion record");
+            require(s[0] == 0.0 || s[0] == 1.0, "unknown inclusion kind");
+            require(s[0] != 0.0 || s[3] >= 0, "negative radius");
+            require(s[5] >= eta_bg && s[6] >= rho_bg,
+                    "inclusions must be at least as viscous and dense as the background");
+        }
+        require(ctx->device >= 0 && ctx->device < sip::kMaxDevices, "device index out of range");
+        SIP_CUDA(cudaSetDevice(ctx->device));
+        double* dev_shapes = sip::noalloc_shapes_on(ctx->device);
+        const cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (n_shapes > 0)
+            SIP_CUDA(cudaMemcpyAsync(dev_shapes, shapes_host, size_t(n_shapes) * 7 * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        sip::launch_rasterise(nx, ny, lx, ly, dev_shapes, n_shapes, eta_bg, rho_bg, eta_out,
+                              rho_out, s);
+        ctx->err.clear();
+        return SIP_OK;
+    } catch (const sip::Error& e) {
+        ctx->err = e.what();
+        return e.status;
+    } catch (const std::exception& e) {
+        ctx->err = e.what();
+        return SIP_ERR_CUDA;
+    }
+}
