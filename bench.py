@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
+                    help="solve: the headline line; batch / serve: the batched and served "
+                         "forms on bounded samples of their workloads (extra lines)")
+    ap.add_argument("--count", type=int, default=32,
+                    help="instances (batch) or requests (serve) in the bounded sample")
     return ap.parse_args()
 
 
@@ -247,7 +252,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int((prob64.n_u + prob64.n_p) * 8)},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "sip_apply": {"kernel": "k_apply_sip<N=4,double>", "ms": apply_ms,
+        "sip_apply": {"kernel": DOMINANT, "ms": apply_ms,
                       "GB_per_s": ab / apply_ms / 1e6, "GFLOP_per_s": af / apply_ms / 1e6,
                       "dof_per_s": prob64.n_u / (apply_ms / 1e3)},
     }
@@ -255,22 +260,41 @@ def run_ours(args, rank, world):
     return out
 
 
+# FP64 peak of one GB300, derived from unit counts and clocks: 152 SMs x
+# 2 FP64 FMA per SM per clock x 2 FLOP x 2.07 GHz (maximum SM clock)
+# = 1.259 TFLOP/s (NVIDIA's figure: 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+DOMINANT = "k_apply_elem<4,double>"
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_apply_elem_fp64_128x128_k3.md")
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    summary (dram__bytes_read.sum + dram__bytes_write.sum), or None."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    vals = {}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    for line in open(TRAFFIC_PROFILE):
+        for key in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            if f"`{key}`" in line:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                vals[key] = float(cells[1]) * scale.get(cells[2], 1.0)
+    if len(vals) != 2:
+        return None
+    return vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]
+
+
 def roofline(out, ab, af, apply_ms):
     """FP64 on GB300 is bound by the FP64 pipe, not HBM: achieved FP64
-    FLOP/s of the SIP apply against the FP64 peak derived in the design doc."""
-    fp64_peak_tflops = float(os.environ.get("SIP_FP64_PEAK_TFLOPS", "1.25"))
+    FLOP/s of the SIP apply (algorithmic FLOPs / live launch time) against the
+    FP64 peak derived from unit counts and clocks."""
     achieved = af / apply_ms / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("k_apply_sip_fp64_128x128_k3")
-        except (ValueError, OSError):
-            traffic = None
-    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak_tflops, "traffic": traffic,
-            "kernel": "k_apply_sip<N=4,double>", "algorithmic_bytes": ab,
-            "hbm_GB_per_s": ab / apply_ms / 1e6}
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": captured_traffic(),
+            "kernel": DOMINANT, "algorithmic_bytes": ab, "algorithmic_flops": af,
+            "hbm_GB_per_s": ab / apply_ms / 1e6,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
 
 
 # ------------------------------------------------------------------ oracle
@@ -328,11 +352,91 @@ def cpu_baseline():
                       "SciPy sparse kernels, single-threaded"}
 
 
+def run_batch(args):
+    """Batched form: independent instances (side in {32, 64, 128, 256}, k in
+    {2..5}, 16 discs, contrast 10^U[2,6]) solved concurrently, mixed precision;
+    the first ``--count`` instances of the seeded list."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    ctx = api.Context(0)
+    insts = synth.batch_instances(128)[:args.count]
+    probs, fs, us, ps = [], [], [], []
+    for wl in insts:
+        eta, rho = ctx.rasterise_inclusions(wl.nx, wl.ny, wl.shapes)
+        pr = api.Problem(ctx, wl.nx, wl.ny, wl.k, eta.cpu().numpy(), bc=wl.bc,
+                         n_hlevels=wl.n_hlevels, seed=4, precision=wl.precision)
+        f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
+        pr.rhs_body_force(rho, synth.GRAVITY, f)
+        probs.append(pr)
+        fs.append(f)
+        us.append(torch.empty_like(f))
+        ps.append(torch.empty(pr.n_p, dtype=torch.float64, device="cuda"))
+    for pr in probs:
+        pr.setup()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, reps = api.solve_batch(ctx, probs, fs, us, ps, n_streams=8, rtol=1e-8)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for pr, f, u, p in zip(probs, fs, us, ps):
+        pr.solve(f, u, p, rtol=1e-8)
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t1
+    return {"metric": "batched_stokes_solves_per_s", "value": len(insts) / dt, "unit": UNIT,
+            "one_at_a_time": len(insts) / dt1, "instances": len(insts), "status": st,
+            "max_rel_residual": max(r["rel_residual"] for r in reps),
+            "config": {"workload": "batch_instances(seed 4)", "count": len(insts),
+                       "precision": "mixed", "streams": 8}}
+
+
+def run_serve(args):
+    """Served form: Poisson arrivals at 200 requests/s (side log-uniform in
+    [32, 512], k in {2..6}, 16 discs, contrast 10^U[0,6]); the first
+    ``--count`` requests of the seeded stream, replayed in real time."""
+    import numpy as np
+    from paper_1607_03777_gb300 import api, synth
+    ctx = api.Context(0)
+    arrivals, wls = synth.request_stream()
+    arrivals, wls = arrivals[:args.count], wls[:args.count]
+    free = 200 << 30
+    srv = api.Server(ctx, budget_bytes=free, max_slots=8)
+    keep = []
+    eta_rho = []
+    for wl in wls:   # element materials on the device, copied to the host once
+        eta, rho = ctx.rasterise_inclusions(wl.nx, wl.ny, wl.shapes)
+        eta_rho.append((eta.cpu().numpy(), rho.cpu().numpy()))
+    t0 = time.perf_counter()
+    for i, (ta, wl) in enumerate(zip(arrivals, wls)):
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        eta, rho = eta_rho[i]
+        keep.append(srv.submit(i, wl.nx, wl.ny, wl.k, eta, rho, g=synth.GRAVITY, bc=wl.bc,
+                               n_hlevels=wl.n_hlevels, seed=5, precision=wl.precision))
+    srv.drain()
+    dt = time.perf_counter() - t0
+    done = srv.poll(cap=max(256, len(wls)))
+    lat = np.array([r["solve_ms"] for _, r in done])
+    ok = sum(1 for _, r in done if r["status"] == 0)
+    srv.close()
+    return {"metric": "served_stokes_solves_per_s", "value": len(done) / dt, "unit": UNIT,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "requests": len(done), "converged": ok,
+            "config": {"workload": "request_stream(seed 5, 200 req/s)", "count": len(wls),
+                       "slots": 8, "precision": "mixed"}}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.mode != "solve":
+        if rank == 0:
+            out = run_batch(args) if args.mode == "batch" else run_serve(args)
+            print(json.dumps(out), flush=True)
+        return 0
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)

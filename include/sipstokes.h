@@ -56,10 +56,17 @@ typedef enum {
  * the paper does not use. */
 typedef enum { SIP_BC_NAVIER = 0, SIP_BC_NEUMANN = 1, SIP_BC_DIRICHLET = 2 } sip_bc;
 
-/* Precision of the viscous preconditioner (smoother, transfers, coarse
- * solve and inner Krylov).  The outer FGMRES, its residual, B, B^T and the
- * S* scaling are always FP64. */
-typedef enum { SIP_PREC_FP64 = 0, SIP_PREC_MIXED = 1 } sip_precision;
+/* Precision of the viscous preconditioner.  The outer FGMRES, its residual,
+ * B, B^T and the S* scaling are always FP64.
+ *   SIP_PREC_FP64            everything FP64;
+ *   SIP_PREC_MIXED           V-cycle (smoother, transfers, coarse solve) FP32,
+ *                            inner PCG iterate and operator FP64;
+ *   SIP_PREC_MIXED_F32_INNER V-cycle and inner PCG both FP32. */
+typedef enum {
+    SIP_PREC_FP64 = 0,
+    SIP_PREC_MIXED = 1,
+    SIP_PREC_MIXED_F32_INNER = 2
+} sip_precision;
 
 typedef struct sip_ctx sip_ctx;
 typedef struct sip_problem sip_problem;
@@ -219,6 +226,50 @@ void sip_solve_opts_default(sip_solve_opts* opts);
 sip_status sip_solve(sip_problem* prob, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts* opts, sip_solve_report* report,
                      void* stream);
+
+/* ---- batches and serving ----------------------------------------------------
+ * Not in the paper (it solves one problem at a time on one CPU core): many
+ * independent Stokes problems of different mesh sizes, degrees and viscosity
+ * fields solved concurrently on one GPU.  Every solve in flight owns a
+ * stream, its device-resident multigrid and Krylov state and its captured
+ * V-cycle graph; solves in flight together overlap on the device.  Device
+ * memory of in-flight work is stream-ordered (no device-wide
+ * synchronisation between requests). */
+typedef struct sip_server sip_server;
+
+/* Solve problems[i] with right-hand side f_u[i] into u[i], p[i] (device
+ * pointers), n_streams solves in flight at a time (<= 0: 8).  reports may be
+ * NULL or hold n entries.  Returns SIP_OK when every solve converged, else
+ * the status of a failing one (each report holds its own).  Synchronous. */
+sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* problems,
+                           const double* const* f_u, double* const* u, double* const* p,
+                           const sip_solve_opts* opts, sip_solve_report* reports, int n_streams);
+/* Device bytes a problem of this description holds after a solve with the
+ * given FGMRES restart length (the server's admission estimate). */
+int64_t sip_problem_footprint(const sip_problem_desc* desc, int restart);
+/* A request server on ctx's device: at most max_slots solves in flight and
+ * at most budget_bytes of estimated device footprint admitted at once.
+ * Requests are admitted first in, first out as slots and memory free up. */
+sip_status sip_server_create(sip_ctx* ctx, int64_t budget_bytes, int max_slots, sip_server** out);
+/* Queue one request: the problem desc (eta_host copied), the element
+ * densities rho_host (copied; body force (0, -g rho_K)), host outputs u_host
+ * (n_u) and p_host (n_p) that must stay valid until the request is reported
+ * done, options (NULL = defaults).  Non-blocking.  A request whose footprint
+ * exceeds the whole budget is refused (SIP_ERR_REJECTED, also reported by
+ * poll). */
+sip_status sip_server_submit(sip_server* server, const sip_problem_desc* desc,
+                             const double* rho_host, double g, double* u_host, double* p_host,
+                             const sip_solve_opts* opts, uint64_t request_id);
+/* Move up to cap finished requests into ids / reports (report.solve_ms =
+ * submit-to-result latency in ms); *n_done receives the count. */
+sip_status sip_server_poll(sip_server* server, uint64_t* ids, sip_solve_report* reports, int cap,
+                           int* n_done);
+/* Block until every queued and running request has finished. */
+sip_status sip_server_drain(sip_server* server);
+sip_status sip_server_stats(sip_server* server, int* queued, int* running,
+                            int64_t* bytes_in_use);
+/* Stop the workers (queued requests are dropped, running ones finish). */
+void sip_server_destroy(sip_server* server);
 
 /* ---- set-up helpers (paper Sec. 7.3) -------------------------------------- */
 /* Element-wise material of inclusions (Sec. 7.3): eta_K = max of eta over

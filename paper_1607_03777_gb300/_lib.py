@@ -17,7 +17,7 @@ STATUS_NAMES = {
     7: "SIP_ERR_REJECTED", 8: "SIP_ERR_NOT_READY",
 }
 BC = {"navier": 0, "neumann": 1, "dirichlet": 2}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "mixed_f32_inner": 2}
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 
@@ -102,6 +102,17 @@ SIGNATURES = {
     "sip_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "sip_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveReport), _VP]),
+    "sip_solve_batch": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
+                                       ctypes.POINTER(SolveOpts), _VP, ctypes.c_int]),
+    "sip_problem_footprint": (ctypes.c_int64, [ctypes.POINTER(ProblemDesc), ctypes.c_int]),
+    "sip_server_create": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "sip_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(ProblemDesc), _VP, ctypes.c_double,
+                                         _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.c_uint64]),
+    "sip_server_poll": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "sip_server_drain": (ctypes.c_int, [_VP]),
+    "sip_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), _I64P]),
+    "sip_server_destroy": (None, [_VP]),
     "sip_rasterise_inclusions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, _VP, _VP, _VP]),

@@ -230,3 +230,116 @@ class Problem:
             self.ctx.check(st)
         out["status"] = st
         return out
+
+
+# ---------------------------------------------------------------- batches, serving
+def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_scale=1.0,
+              n_hlevels=0, cheb_steps_p=2, cheb_steps_h=3, eig_iters=10, cheb_lo=0.1,
+              cheb_hi=1.1, seed=0, precision="fp64"):
+    """A filled sip_problem_desc and the host eta array it points to (keep
+    both alive while the C side may read them)."""
+    d = ProblemDesc()
+    ctx.lib.sip_problem_desc_default(ctypes.byref(d))
+    eta = np.ascontiguousarray(np.asarray(eta, dtype=np.float64).reshape(-1))
+    d.nx, d.ny, d.lx, d.ly, d.k = nx, ny, lx, ly, k
+    for i, b in enumerate(bc):
+        d.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    d.eta_host = eta.ctypes.data_as(_lib.c_double_p)
+    d.penalty_scale, d.n_hlevels = penalty_scale, n_hlevels
+    d.cheb_steps_p, d.cheb_steps_h, d.eig_iters = cheb_steps_p, cheb_steps_h, eig_iters
+    d.cheb_lo, d.cheb_hi, d.seed = cheb_lo, cheb_hi, seed
+    d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    return d, eta
+
+
+def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200):
+    o = SolveOpts()
+    lib.sip_solve_opts_default(ctypes.byref(o))
+    o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
+    o.inner_rtol, o.max_inner = inner_rtol, max_inner
+    return o
+
+
+def _report(rep):
+    return {name: getattr(rep, name) for name, _ in SolveReport._fields_}
+
+
+def footprint(ctx, restart=100, **desc_kw):
+    d, _keep = make_desc(ctx, **desc_kw)
+    return int(ctx.lib.sip_problem_footprint(ctypes.byref(d), int(restart)))
+
+
+def solve_batch(ctx, problems, fs, us, ps, n_streams=8, stream=None, **opt_kw):
+    """sip_solve_batch over lists of Problems and CUDA tensors; returns
+    (status, [report dicts])."""
+    n = len(problems)
+    arr = lambda vals: (ctypes.c_void_p * n)(*vals)
+    hp = arr([p.handle.value for p in problems])
+    hf = arr([_ptr(f, torch.float64).value for f in fs])
+    hu = arr([_ptr(u, torch.float64).value for u in us])
+    hpp = arr([_ptr(p, torch.float64).value for p in ps])
+    reps = (SolveReport * n)()
+    o = _opts(ctx.lib, **opt_kw)
+    torch.cuda.current_stream().synchronize()
+    st = ctx.lib.sip_solve_batch(ctx.handle, n, hp, hf, hu, hpp, ctypes.byref(o), reps, int(n_streams))
+    return st, [_report(r) for r in reps]
+
+
+class Server:
+    """sip_server: continuous batching of Stokes solve requests."""
+
+    def __init__(self, ctx, budget_bytes, max_slots=8):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.sip_server_create(ctx.handle, int(budget_bytes), int(max_slots),
+                                            ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, request_id, nx, ny, k, eta, rho, g=10.0, opts=None, **desc_kw):
+        """Queue a request; returns (status, u_host, p_host) with the host
+        output arrays that the server fills."""
+        d, eta_keep = make_desc(self.ctx, nx, ny, k, eta, **desc_kw)
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
+        n = k + 1
+        u = np.zeros(nx * ny * 2 * n * n)
+        p = np.zeros(nx * ny * k * k)
+        o = _opts(self.ctx.lib, **(opts or {}))
+        st = self.ctx.lib.sip_server_submit(self.handle, ctypes.byref(d),
+                                            rho.ctypes.data_as(ctypes.c_void_p), float(g),
+                                            u.ctypes.data_as(ctypes.c_void_p),
+                                            p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                            ctypes.c_uint64(request_id))
+        self._keep[request_id] = (u, p)
+        return st, u, p
+
+    def poll(self, cap=256):
+        ids = (ctypes.c_uint64 * cap)()
+        reps = (SolveReport * cap)()
+        n = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.sip_server_poll(self.handle, ids, reps, cap, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            out.append((int(ids[i]), _report(reps[i])))
+            self._keep.pop(int(ids[i]), None)
+        return out
+
+    def drain(self):
+        self.ctx.check(self.ctx.lib.sip_server_drain(self.handle))
+
+    def stats(self):
+        q, r, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        self.ctx.check(self.ctx.lib.sip_server_stats(self.handle, ctypes.byref(q), ctypes.byref(r),
+                                                     ctypes.byref(b)))
+        return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.sip_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

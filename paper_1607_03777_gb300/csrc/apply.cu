@@ -9,6 +9,7 @@
 // along the face: for the face of K with outward normal s e_d the test mode
 // (q along d, m along the face) receives l_q(s) P[m] + l_q'(s) Q[m], where P
 // and Q combine the traces of K and its neighbour.
+#include <cstdlib>
 #include <mutex>
 
 #include "sip_face.cuh"
@@ -273,12 +274,12 @@ void apply_sip_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const
     a.tab = make_tab<N, T>();
     constexpr int EX = TileCfg<N>::EX;
     const size_t smem = apply_smem_elems<N, T>() * sizeof(T);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [smem] {   // once per process, thread-safe
         SIP_CUDA(cudaFuncSetAttribute(k_apply_sip<N, T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     dim3 grid((g.nx + EX - 1) / EX, g.ny);
     k_apply_sip<N, T><<<grid, 256, smem, s>>>(a);
     SIP_CHECK_LAUNCH();
@@ -457,6 +458,13 @@ __global__ void k_rasterise(int nx, int ny, double hx, double hy, const double* 
 template <typename T>
 void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                       const T* z, T beta, cudaStream_t s) {
+    // low degrees: one thread per element with compile-time tables
+    // (SIP_APPLY_KERNEL=tile selects the shared-memory tile kernel for all N)
+    static const bool use_elem = [] {
+        const char* v = std::getenv("SIP_APPLY_KERNEL");
+        return !(v && std::string(v) == "tile");
+    }();
+    if (use_elem && launch_apply_sip_elem<T>(N, g, x, y, eta, alpha, z, beta, s)) return;
     switch (N) {
         case 2: apply_sip_n<2, T>(g, x, y, eta, alpha, z, beta, s); break;
         case 3: apply_sip_n<3, T>(g, x, y, eta, alpha, z, beta, s); break;

@@ -29,6 +29,13 @@ sip_status guarded(sip_ctx* ctx, F&& f) {
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// guarded() with the library's allocations ordered on the caller's stream
+template <typename F>
+sip_status guarded_s(sip_ctx* ctx, void* stream, F&& f) {
+    sip::AllocStreamScope scope(as_stream(stream));
+    return guarded(ctx, std::forward<F>(f));
+}
+
 
 }  // namespace
 
@@ -96,6 +103,14 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
                          "unknown boundary condition");
         sip::require(d->eta_host != nullptr, "eta_host is null");
         sip::require(d->n_hlevels >= 0, "n_hlevels must be >= 0");
+        sip::require(d->precision >= SIP_PREC_FP64 && d->precision <= SIP_PREC_MIXED_F32_INNER,
+                     "unknown precision");
+        sip::require(d->cheb_steps_p >= 1 && d->cheb_steps_h >= 1 && d->eig_iters >= 1 &&
+                         d->eig_iters <= 100,
+                     "smoothing steps and eigen-estimate iterations must be positive (<= 100)");
+        sip::require(std::isfinite(d->cheb_lo) && std::isfinite(d->cheb_hi) && d->cheb_lo > 0 &&
+                         d->cheb_hi > d->cheb_lo,
+                     "Chebyshev bound factors must satisfy 0 < lo < hi");
         {
             int cx = d->nx, cy = d->ny;
             for (int l = 0; l < d->n_hlevels; ++l) {
@@ -126,11 +141,12 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
             p->geom = sip::make_geom(d->nx, d->ny, d->lx, d->ly, d->bc, d->k, d->penalty_scale);
             p->geom1 = p->geom;   // the Galerkin A_1 keeps the fine-k penalty
             p->eta_host = eta;
+            const cudaStream_t s = sip::alloc_stream();
             p->eta_d.alloc(ne * sizeof(double));
-            SIP_CUDA(cudaMemcpy(p->eta_d.ptr, eta.data(), ne * sizeof(double),
-                                cudaMemcpyHostToDevice));
-            p->derive_eta(nullptr);
-            SIP_CUDA(cudaDeviceSynchronize());
+            SIP_CUDA(cudaMemcpyAsync(p->eta_d.ptr, eta.data(), ne * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+            p->derive_eta(s);
+            SIP_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
             delete p;
             throw;
@@ -139,7 +155,14 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
     });
 }
 
-void sip_problem_destroy(sip_problem* p) { delete p; }
+void sip_problem_destroy(sip_problem* p) {
+    if (!p) return;
+    // the problem's buffers may still be in use on any stream the caller
+    // used: wait for the device before returning them to the pool
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    delete p;
+}
 
 sip_status sip_problem_sizes(const sip_problem* p, int64_t* n_u, int64_t* n_p,
                              int64_t* device_bytes) {
@@ -152,7 +175,7 @@ sip_status sip_problem_sizes(const sip_problem* p, int64_t* n_u, int64_t* n_p,
 
 sip_status sip_problem_update_eta(sip_problem* p, const double* eta, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(eta != nullptr, "null eta");
         cudaPointerAttributes at{};
         SIP_CUDA(cudaPointerGetAttributes(&at, eta));
@@ -180,7 +203,7 @@ sip_status sip_problem_update_eta(sip_problem* p, const double* eta, void* strea
 
 sip_status sip_apply_A(sip_problem* p, const double* x, double* y, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(x && y, "null vector");
         sip::require(x != y, "x and y must not overlap");
         sip::launch_apply_sip<double>(p->n, p->geom, x, y, p->eta_d.as<double>(), 1.0, nullptr,
@@ -190,7 +213,7 @@ sip_status sip_apply_A(sip_problem* p, const double* x, double* y, void* stream)
 
 sip_status sip_apply_A_f32(sip_problem* p, const float* x, float* y, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(x && y, "null vector");
         sip::require(x != y, "x and y must not overlap");
         sip::launch_apply_sip<float>(p->n, p->geom, x, y, p->eta_f.as<float>(), 1.0f, nullptr,
@@ -200,7 +223,7 @@ sip_status sip_apply_A_f32(sip_problem* p, const float* x, float* y, void* strea
 
 sip_status sip_apply_B(sip_problem* p, const double* xp, double* yu, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(xp && yu, "null vector");
         sip::launch_apply_B<double>(p->k, p->geom, xp, yu, as_stream(stream));
     });
@@ -208,7 +231,7 @@ sip_status sip_apply_B(sip_problem* p, const double* xp, double* yu, void* strea
 
 sip_status sip_apply_Bt(sip_problem* p, const double* xu, double* yp, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(xu && yp, "null vector");
         sip::launch_apply_Bt<double>(p->k, p->geom, xu, yp, as_stream(stream));
     });
@@ -219,7 +242,7 @@ sip_status sip_rasterise_inclusions(sip_ctx* ctx, int nx, int ny, double lx, dou
                                     double rho_bg, double* eta_out, double* rho_out,
                                     void* stream) {
     if (!ctx) return SIP_ERR_INVALID_ARG;
-    return guarded(ctx, [&] {
+    return guarded_s(ctx, stream, [&] {
         sip::require(nx >= 1 && ny >= 1 && std::isfinite(lx) && std::isfinite(ly) && lx > 0 &&
                          ly > 0,
                      "bad mesh");
@@ -252,7 +275,7 @@ sip_status sip_rasterise_inclusions(sip_ctx* ctx, int nx, int ny, double lx, dou
 sip_status sip_rhs_body_force(sip_problem* p, const double* rho, double g, double* f,
                               void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(rho && f, "null vector");
         sip::require(std::isfinite(g), "non-finite gravity");
         sip::launch_rhs_body_force(p->k, p->geom, rho, g, f, as_stream(stream));
@@ -286,7 +309,7 @@ sip::Multigrid<float>& mg32(sip_problem* p, cudaStream_t s) {
 
 sip_status sip_problem_setup(sip_problem* p, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         p->ensure_setup(as_stream(stream));
     });
@@ -305,7 +328,7 @@ sip_status sip_lambda_max(sip_problem* p, int level, double* out) {
 
 sip_status sip_block_jacobi(sip_problem* p, const double* r, double* z, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(r && z && r != z, "bad vectors");
         mg64(p, as_stream(stream)).bj(r, z, as_stream(stream));
     });
@@ -313,7 +336,7 @@ sip_status sip_block_jacobi(sip_problem* p, const double* r, double* z, void* st
 
 sip_status sip_p_restrict(sip_problem* p, const double* r, double* r1, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(r && r1, "null vector");
         sip::launch_p_restrict<double>(size_t(p->ne), p->n, r, r1, as_stream(stream));
     });
@@ -321,7 +344,7 @@ sip_status sip_p_restrict(sip_problem* p, const double* r, double* r1, void* str
 
 sip_status sip_p_prolong_add(sip_problem* p, const double* e1, double* y, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(e1 && y, "null vector");
         sip::launch_p_prolong_add<double>(size_t(p->ne), p->n, e1, y, as_stream(stream));
     });
@@ -329,7 +352,7 @@ sip_status sip_p_prolong_add(sip_problem* p, const double* e1, double* y, void* 
 
 sip_status sip_apply_A1(sip_problem* p, const double* x1, double* y1, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(x1 && y1 && x1 != y1, "bad vectors");
         sip::launch_apply_sip<double>(2, p->geom1, x1, y1, p->eta_d.as<double>(), 1.0, nullptr, 0.0,
                                       as_stream(stream));
@@ -338,7 +361,7 @@ sip_status sip_apply_A1(sip_problem* p, const double* x1, double* y1, void* stre
 
 sip_status sip_cd_prolong(sip_problem* p, const double* v, double* u1, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(v && u1, "null vector");
         sip::launch_pcd<double>(p->desc.nx, p->desc.ny, v, u1, as_stream(stream));
     });
@@ -346,7 +369,7 @@ sip_status sip_cd_prolong(sip_problem* p, const double* v, double* u1, void* str
 
 sip_status sip_dc_restrict(sip_problem* p, const double* u1, double* v, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(v && u1, "null vector");
         sip::launch_rdc<double>(p->desc.nx, p->desc.ny, u1, v, as_stream(stream));
     });
@@ -367,7 +390,7 @@ sip_status sip_hlevel_dims(sip_problem* p, int level, int* n_levels, int* nvx, i
 
 sip_status sip_hlevel_stencil(sip_problem* p, int level, double* S, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         auto& m = mg64(p, as_stream(stream));
         sip::require(S != nullptr, "null output");
         sip::require(level >= 0 && level < int(m.h.size()), "no such level");
@@ -378,7 +401,7 @@ sip_status sip_hlevel_stencil(sip_problem* p, int level, double* S, void* stream
 
 sip_status sip_hlevel_apply(sip_problem* p, int level, const double* x, double* y, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         auto& m = mg64(p, as_stream(stream));
         sip::require(x && y && x != y, "bad vectors");
         sip::require(level >= 0 && level < int(m.h.size()), "no such level");
@@ -388,7 +411,7 @@ sip_status sip_hlevel_apply(sip_problem* p, int level, const double* x, double* 
 
 sip_status sip_coarse_solve(sip_problem* p, const double* b, double* x, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         auto& m = mg64(p, as_stream(stream));
         sip::require(b && x && b != x, "bad vectors");
         sip::launch_dense_symv<double>(m.nc, m.cinv.as<double>(), b, x, as_stream(stream));
@@ -397,7 +420,7 @@ sip_status sip_coarse_solve(sip_problem* p, const double* b, double* x, void* st
 
 sip_status sip_vcycle(sip_problem* p, const double* r, double* z, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(r && z && r != z, "bad vectors");
         mg64(p, as_stream(stream)).vcycle(r, z, as_stream(stream));
     });
@@ -405,7 +428,7 @@ sip_status sip_vcycle(sip_problem* p, const double* r, double* z, void* stream) 
 
 sip_status sip_vcycle_f32(sip_problem* p, const float* r, float* z, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(r && z && r != z, "bad vectors");
         mg32(p, as_stream(stream)).vcycle(r, z, as_stream(stream));
     });
@@ -414,7 +437,7 @@ sip_status sip_vcycle_f32(sip_problem* p, const float* r, float* z, void* stream
 sip_status sip_inner_solve(sip_problem* p, const double* t, double* y, double rtol, int max_it,
                            int* its, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;
-    return guarded(p->ctx, [&] {
+    return guarded_s(p->ctx, stream, [&] {
         sip::require(t && y && t != y, "bad vectors");
         sip::require(rtol > 0 && max_it >= 1, "bad tolerance or iteration cap");
         const int n = mg64(p, as_stream(stream)).inner_pcg(t, y, rtol, max_it, as_stream(stream),

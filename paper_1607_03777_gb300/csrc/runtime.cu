@@ -1,0 +1,353 @@
+// Batched and served Stokes solves: many independent problems of different
+// mesh sizes, degrees and viscosity fields on one GPU.
+//
+// Each in-flight solve owns a CUDA stream, its device-resident multigrid and
+// Krylov state and a captured V-cycle graph; solves in flight at the same
+// time overlap on the device.  The server admits queued requests first-in
+// first-out whenever a slot is free and the request's device footprint fits
+// in the remaining budget, so requests that arrive while others run join as
+// capacity frees up (continuous batching).
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+
+#include "sip_solver.h"
+
+using sip::Error;
+
+namespace {
+
+double wall_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+namespace sip {
+
+// Device bytes of a problem after its first solve (multigrid, FGMRES basis
+// of `restart` vectors, work vectors), from the sizes alone.
+int64_t estimate_problem_bytes(const sip_problem_desc& d, int restart) {
+    const int64_t ne = int64_t(d.nx) * d.ny;
+    const int64_t n = d.k + 1, nb = 2 * n * n, mp = int64_t(d.k) * d.k;
+    const int64_t n_u = ne * nb, n_p = ne * mp, nk = n_u + n_p;
+    const bool mixed = d.precision != SIP_PREC_FP64;
+    const int64_t w = mixed ? 4 : 8;
+    int64_t b = ne * (8 + 4 + 8 + 4);                      // eta, eta_f, 1/eta (FP64, FP32)
+    // multigrid: block inverses (class + unique worst case is bounded by the
+    // elements with a stiffer neighbour; count them all), work vectors
+    b += 16 * nb * nb * w + ne * nb * nb * w / 4;
+    b += 10 * n_u * w + 16 * ne * w + ne * 8;
+    int64_t nv = int64_t(d.nx + 1) * (d.ny + 1);
+    for (int l = 0; l <= d.n_hlevels; ++l) {
+        b += nv * (36 + 8) * w + nv * 36 * 8;             // stencils (+ FP64 set-up copy)
+        nv = nv / 4 + 1;
+    }
+    b += int64_t(d.eig_iters + 1) * n_u * 8;               // Arnoldi basis of the set-up
+    b += int64_t(2 * restart + 1) * nk * 8 + 8 * nk * 8;  // FGMRES V, Z and work vectors
+    return b;
+}
+
+}  // namespace sip
+
+// ------------------------------------------------------------------ batch
+namespace {
+
+struct Job {
+    sip_problem* prob;
+    const double* f;
+    double* u;
+    double* p;
+    sip_solve_report* rep;
+    sip_status st = SIP_OK;
+    std::string err;
+};
+
+void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n_streams) {
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+        cudaSetDevice(device);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s = nullptr;
+        }
+        sip::AllocStreamScope scope(s);
+        for (size_t i = next++; i < jobs.size(); i = next++) {
+            Job& j = jobs[i];
+            try {
+                sip_solve_report local{};
+                j.st = sip::run_solve(j.prob, j.f, nullptr, j.u, j.p, o, j.rep ? j.rep : &local, s);
+            } catch (const Error& e) {
+                j.st = e.status;
+                j.err = e.what();
+                if (j.rep) j.rep->status = e.status;
+            } catch (const std::exception& e) {
+                j.st = SIP_ERR_CUDA;
+                j.err = e.what();
+                if (j.rep) j.rep->status = SIP_ERR_CUDA;
+            }
+        }
+        if (s) cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    const int nt = std::max(1, std::min<int>(n_streams, int(jobs.size())));
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ server
+struct ServerRequest {
+    uint64_t id = 0;
+    sip_problem_desc desc{};
+    std::vector<double> eta, rho;
+    double g = 0.0;
+    double* u_host = nullptr;
+    double* p_host = nullptr;
+    sip_solve_opts opts{};
+    int64_t bytes = 0;
+    double t_submit = 0.0;
+};
+
+struct ServerDone {
+    uint64_t id;
+    sip_solve_report rep;
+};
+
+struct sip_server {
+    sip_ctx* ctx = nullptr;
+    int64_t budget = 0;
+    int64_t in_use = 0;
+    int slots = 0;
+    int busy = 0;
+    bool stop = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_idle;
+    std::deque<ServerRequest> queue;
+    std::vector<ServerDone> done;
+    std::vector<std::thread> workers;
+    std::vector<double> latencies_ms;
+
+    void worker_loop();
+    sip_status solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep);
+};
+
+sip_status sip_server::solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep) {
+    sip_problem* prob = nullptr;
+    sip_problem_desc d = r.desc;
+    d.eta_host = r.eta.data();
+    sip_status st = sip_problem_create(ctx, &d, &prob);
+    if (st != SIP_OK) return st;
+    double *f = nullptr, *u = nullptr, *p = nullptr, *rho = nullptr;
+    try {
+        const size_t n_u = size_t(prob->n_u), n_p = size_t(prob->n_p), ne = size_t(prob->ne);
+        SIP_CUDA(cudaMallocAsync(&f, n_u * sizeof(double), s));
+        SIP_CUDA(cudaMallocAsync(&u, n_u * sizeof(double), s));
+        SIP_CUDA(cudaMallocAsync(&p, n_p * sizeof(double), s));
+        SIP_CUDA(cudaMallocAsync(&rho, ne * sizeof(double), s));
+        SIP_CUDA(cudaMemcpyAsync(rho, r.rho.data(), ne * sizeof(double), cudaMemcpyHostToDevice, s));
+        sip::launch_rhs_body_force(prob->k, prob->geom, rho, r.g, f, s);
+        st = sip::run_solve(prob, f, nullptr, u, p, r.opts, &rep, s);
+        SIP_CUDA(cudaMemcpyAsync(r.u_host, u, n_u * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SIP_CUDA(cudaMemcpyAsync(r.p_host, p, n_p * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SIP_CUDA(cudaStreamSynchronize(s));
+    } catch (const Error& e) {
+        st = e.status;
+    } catch (const std::exception&) {
+        st = SIP_ERR_CUDA;
+    }
+    for (double* q : {f, u, p, rho})
+        if (q) cudaFreeAsync(q, s);
+    // all of this request's work ran on s: wait for s only (no device-wide
+    // synchronisation), then return the buffers to the stream-ordered pool
+    cudaStreamSynchronize(s);
+    delete prob;
+    return st;
+}
+
+void sip_server::worker_loop() {
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s = nullptr;
+    }
+    sip::AllocStreamScope scope(s);
+    for (;;) {
+        ServerRequest r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            // FIFO admission: the head request runs when its footprint fits
+            cv_work.wait(lk, [&] {
+                return stop || (!queue.empty() && in_use + queue.front().bytes <= budget);
+            });
+            if (stop && queue.empty()) break;
+            if (queue.empty()) continue;
+            r = std::move(queue.front());
+            queue.pop_front();
+            in_use += r.bytes;
+            ++busy;
+        }
+        sip_solve_report rep{};
+        const sip_status st = solve_one(r, s, rep);
+        rep.status = st;
+        const double lat = wall_ms() - r.t_submit;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            in_use -= r.bytes;
+            --busy;
+            rep.solve_ms = lat;   // for served requests: submit-to-result latency
+            done.push_back({r.id, rep});
+            latencies_ms.push_back(lat);
+        }
+        cv_work.notify_all();
+        cv_idle.notify_all();
+    }
+    if (s) cudaStreamDestroy(s);
+}
+
+extern "C" {
+
+sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* probs, const double* const* f_u,
+                           double* const* u, double* const* p, const sip_solve_opts* opts,
+                           sip_solve_report* reports, int n_streams) {
+    if (!ctx) return SIP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!probs || !f_u || !u || !p))) {
+        ctx->err = "bad batch arguments";
+        return SIP_ERR_INVALID_ARG;
+    }
+    sip_solve_opts o;
+    sip_solve_opts_default(&o);
+    if (opts) o = *opts;
+    std::vector<Job> jobs(n);
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i] || !f_u[i] || !u[i] || !p[i] || probs[i]->ctx != ctx) {
+            ctx->err = "bad batch entry " + std::to_string(i);
+            return SIP_ERR_INVALID_ARG;
+        }
+        jobs[i] = Job{probs[i], f_u[i], u[i], p[i], reports ? &reports[i] : nullptr};
+    }
+    run_jobs(ctx->device, jobs, o, n_streams < 1 ? 8 : n_streams);
+    sip_status worst = SIP_OK;
+    for (auto& j : jobs)
+        if (j.st != SIP_OK) {
+            worst = j.st;
+            ctx->err = j.err.empty() ? "a batched solve did not converge" : j.err;
+        }
+    if (worst == SIP_OK) ctx->err.clear();
+    return worst;
+}
+
+sip_status sip_server_create(sip_ctx* ctx, int64_t budget_bytes, int max_slots, sip_server** out) {
+    if (!ctx || !out || budget_bytes <= 0 || max_slots < 1 || max_slots > 256)
+        return SIP_ERR_INVALID_ARG;
+    auto* sv = new (std::nothrow) sip_server();
+    if (!sv) return SIP_ERR_OOM;
+    sv->ctx = ctx;
+    sv->budget = budget_bytes;
+    sv->slots = max_slots;
+    try {
+        for (int i = 0; i < max_slots; ++i) sv->workers.emplace_back([sv] { sv->worker_loop(); });
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->stop = true;
+        }
+        sv->cv_work.notify_all();
+        for (auto& t : sv->workers) t.join();
+        delete sv;
+        return SIP_ERR_OOM;
+    }
+    *out = sv;
+    return SIP_OK;
+}
+
+int64_t sip_problem_footprint(const sip_problem_desc* desc, int restart) {
+    if (!desc) return -1;
+    return sip::estimate_problem_bytes(*desc, restart < 1 ? 100 : restart);
+}
+
+sip_status sip_server_submit(sip_server* sv, const sip_problem_desc* desc, const double* rho_host,
+                             double g, double* u_host, double* p_host, const sip_solve_opts* opts,
+                             uint64_t request_id) {
+    if (!sv || !desc || !desc->eta_host || !rho_host || !u_host || !p_host)
+        return SIP_ERR_INVALID_ARG;
+    ServerRequest r;
+    r.id = request_id;
+    r.desc = *desc;
+    r.desc.eta_host = nullptr;
+    const size_t ne = size_t(desc->nx) * size_t(desc->ny);
+    if (desc->nx < 1 || desc->ny < 1 || desc->k < 1 || desc->k > 6) return SIP_ERR_INVALID_ARG;
+    r.eta.assign(desc->eta_host, desc->eta_host + ne);
+    r.rho.assign(rho_host, rho_host + ne);
+    r.g = g;
+    r.u_host = u_host;
+    r.p_host = p_host;
+    sip_solve_opts_default(&r.opts);
+    if (opts) r.opts = *opts;
+    r.bytes = sip::estimate_problem_bytes(r.desc, std::min(r.opts.restart, r.opts.max_outer));
+    r.t_submit = wall_ms();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (r.bytes > sv->budget) {
+            sip_solve_report rep{};
+            rep.status = SIP_ERR_REJECTED;
+            sv->done.push_back({r.id, rep});
+            return SIP_ERR_REJECTED;
+        }
+        sv->queue.push_back(std::move(r));
+    }
+    sv->cv_work.notify_all();
+    return SIP_OK;
+}
+
+sip_status sip_server_poll(sip_server* sv, uint64_t* ids, sip_solve_report* reps, int cap,
+                           int* n_done) {
+    if (!sv || !n_done || cap < 0 || (cap > 0 && (!ids || !reps))) return SIP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int n = std::min<int>(cap, int(sv->done.size()));
+    for (int i = 0; i < n; ++i) {
+        ids[i] = sv->done[i].id;
+        reps[i] = sv->done[i].rep;
+    }
+    sv->done.erase(sv->done.begin(), sv->done.begin() + n);
+    *n_done = n;
+    return SIP_OK;
+}
+
+sip_status sip_server_drain(sip_server* sv) {
+    if (!sv) return SIP_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->cv_idle.wait(lk, [&] { return sv->queue.empty() && sv->busy == 0; });
+    return SIP_OK;
+}
+
+sip_status sip_server_stats(sip_server* sv, int* queued, int* running, int64_t* bytes_in_use) {
+    if (!sv) return SIP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (queued) *queued = int(sv->queue.size());
+    if (running) *running = sv->busy;
+    if (bytes_in_use) *bytes_in_use = sv->in_use;
+    return SIP_OK;
+}
+
+void sip_server_destroy(sip_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->queue.clear();
+    }
+    sv->cv_work.notify_all();
+    for (auto& t : sv->workers) t.join();
+    delete sv;
+}
+
+}  // extern "C"

@@ -46,7 +46,8 @@ __host__ __device__ __forceinline__ void face_pq(int kind, int c, int m, int nc,
             T Fn = s * (etaK * dv[nc * N + m] + etaN * dn[nc * N + m]);
             T DTw = T(0);
 #pragma unroll
-            for (int mm = 0; mm < N; ++mm) DTw += D[mm * N + m] * (vo[tc * N + mm] - vn[tc * N + mm]);
+            for (int mm = 0; mm < N; ++mm)
+                if (D[mm * N + m] != T(0)) DTw += D[mm * N + m] * (vo[tc * N + mm] - vn[tc * N + mm]);
             T wn = vo[nc * N + m] - vn[nc * N + m];
             P = -half_ht * Fn - etaK * s * T(0.5) * DTw + sigma * half_ht * wn;
             Q = -etaK * s * fg.ht_over_hn * wn;
@@ -54,8 +55,10 @@ __host__ __device__ __forceinline__ void face_pq(int kind, int c, int m, int nc,
             T tno = T(0), tnn = T(0);
 #pragma unroll
             for (int mm = 0; mm < N; ++mm) {
-                tno += D[m * N + mm] * vo[nc * N + mm];
-                tnn += D[m * N + mm] * vn[nc * N + mm];
+                if (D[m * N + mm] != T(0)) {
+                    tno += D[m * N + mm] * vo[nc * N + mm];
+                    tnn += D[m * N + mm] * vn[nc * N + mm];
+                }
             }
             tno *= fg.two_over_ht;
             tnn *= fg.two_over_ht;
@@ -73,14 +76,16 @@ __host__ __device__ __forceinline__ void face_pq(int kind, int c, int m, int nc,
         if (c == nc) {
             T DTv = T(0);
 #pragma unroll
-            for (int mm = 0; mm < N; ++mm) DTv += D[mm * N + m] * vo[tc * N + mm];
+            for (int mm = 0; mm < N; ++mm)
+                if (D[mm * N + m] != T(0)) DTv += D[mm * N + m] * vo[tc * N + mm];
             P = -half_ht * (s * T(2) * etaK * dv[nc * N + m]) - etaK * s * DTv +
                 sigma * half_ht * vo[nc * N + m];
             Q = T(-2) * etaK * s * fg.ht_over_hn * vo[nc * N + m];
         } else {
             T tno = T(0);
 #pragma unroll
-            for (int mm = 0; mm < N; ++mm) tno += D[m * N + mm] * vo[nc * N + mm];
+            for (int mm = 0; mm < N; ++mm)
+                if (D[m * N + mm] != T(0)) tno += D[m * N + mm] * vo[nc * N + mm];
             tno *= fg.two_over_ht;
             T Ft = s * etaK * (dv[tc * N + m] + tno);
             P = -half_ht * Ft + sigma * half_ht * vo[tc * N + m];

@@ -111,6 +111,10 @@ inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], i
 template <typename T>
 void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                       const T* z, T beta, cudaStream_t s);
+// Thread-per-element variant for N <= 4; returns false for other N.
+template <typename T>
+bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
+                           const T* z, T beta, cudaStream_t s);
 template <typename T>
 void launch_apply_B(int k, const OpGeom& g, const T* p, T* y, cudaStream_t s);
 template <typename T>
@@ -121,38 +125,54 @@ void launch_rasterise(int nx, int ny, double lx, double ly, const double* shapes
                       double eta_bg, double rho_bg, double* eta, double* rho, cudaStream_t s);
 
 // ---------------------------------------------------------- device memory
+// Stream on which this host thread's library allocations are ordered
+// (stream-ordered allocator, cudaMallocAsync / cudaFreeAsync: no device-wide
+// synchronisation, so independent solves on other streams keep running).
+// Defaults to the legacy default stream.
+cudaStream_t& alloc_stream();
+
+struct AllocStreamScope {
+    cudaStream_t prev;
+    explicit AllocStreamScope(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStreamScope() { alloc_stream() = prev; }
+};
+
 struct DeviceBuffer {
     void* ptr = nullptr;
     size_t bytes = 0;
+    cudaStream_t st = nullptr;   // stream the allocation is ordered on
     DeviceBuffer() = default;
     DeviceBuffer(const DeviceBuffer&) = delete;
     DeviceBuffer& operator=(const DeviceBuffer&) = delete;
-    DeviceBuffer(DeviceBuffer&& o) noexcept : ptr(o.ptr), bytes(o.bytes) {
+    DeviceBuffer(DeviceBuffer&& o) noexcept : ptr(o.ptr), bytes(o.bytes), st(o.st) {
         o.ptr = nullptr;
         o.bytes = 0;
     }
     DeviceBuffer& operator=(DeviceBuffer&& o) noexcept {
         if (this != &o) {
-            if (ptr) cudaFree(ptr);
+            release();
             ptr = o.ptr;
             bytes = o.bytes;
+            st = o.st;
             o.ptr = nullptr;
             o.bytes = 0;
         }
         return *this;
     }
-    ~DeviceBuffer() {
-        if (ptr) cudaFree(ptr);
+    ~DeviceBuffer() { release(); }
+    void release() {
+        if (ptr) cudaFreeAsync(ptr, st);
+        ptr = nullptr;
+        bytes = 0;
     }
     // Ensure at least b bytes; an existing buffer that is large enough is
     // kept (re-running a set-up on the same problem allocates nothing).
     void alloc(size_t b) {
         if (ptr && bytes >= b) return;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
+        release();
         if (b == 0) return;
-        cudaError_t e = cudaMalloc(&ptr, b);
+        st = alloc_stream();
+        cudaError_t e = cudaMallocAsync(&ptr, b, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             ptr = nullptr;

@@ -143,6 +143,7 @@ struct Workspace {
     size_t n = 0;
     DeviceBuffer V, Z, w, x, r, b, tu, yu64, sinv, ws, sc, hbuf;
     DeviceBuffer cg_r, cg_d, cg_q, cg_z, sc_in;   // FP64 inner PCG of the mixed form
+    DeviceBuffer t32, y32;                        // FP32 inner PCG (SIP_PREC_MIXED_F32_INNER)
     HostScalars hs, hs_in;
     bool sinv_ready = false;
     int64_t bytes() const;

@@ -16,6 +16,11 @@ int64_t& launch_counter() {
     return n;
 }
 
+cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
 namespace {
 
 __global__ void k_splitmix(size_t n, uint64_t seed, double* out) {
@@ -88,14 +93,37 @@ bool eta_valid(size_t n, const double* eta, cudaStream_t s) {
     return bad == 0;
 }
 
+// Pinned blocks for scalar read-backs come from a per-thread free list:
+// pinned allocation synchronises the device, so it happens once per block
+// and thread, never in a steady-state solve.
+namespace {
+struct PinnedPool {
+    std::vector<double*> free_blocks;
+    ~PinnedPool() {
+        for (double* p : free_blocks) cudaFreeHost(p);
+    }
+};
+PinnedPool& pinned_pool() {
+    static thread_local PinnedPool pool;
+    return pool;
+}
+}  // namespace
+
 HostScalars::HostScalars() {
+    auto& pool = pinned_pool();
+    if (!pool.free_blocks.empty()) {
+        p = pool.free_blocks.back();
+        pool.free_blocks.pop_back();
+        return;
+    }
     if (cudaMallocHost(&p, 256 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
+        p = nullptr;
         throw Error(SIP_ERR_OOM, "pinned host allocation failed");
     }
 }
 HostScalars::~HostScalars() {
-    if (p) cudaFreeHost(p);
+    if (p) pinned_pool().free_blocks.push_back(p);
 }
 
 // ---------------------------------------------------------------- host math
@@ -740,7 +768,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
     const double setup0 = P->setup_ms;
     P->ensure_setup(s);
     const double setup_ms = P->setup_ms - setup0;
-    const bool mixed = P->desc.precision == SIP_PREC_MIXED;
+    const bool f32_inner = P->desc.precision == SIP_PREC_MIXED_F32_INNER;
+    const bool mixed = P->desc.precision == SIP_PREC_MIXED || f32_inner;
     const size_t n_u = size_t(P->n_u), n_p = size_t(P->n_p), n = n_u + n_p;
     const bool singular = P->desc.bc[0] != SIP_BC_NEUMANN && P->desc.bc[1] != SIP_BC_NEUMANN &&
                           P->desc.bc[2] != SIP_BC_NEUMANN && P->desc.bc[3] != SIP_BC_NEUMANN;
@@ -772,7 +801,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         SIP_CHECK_LAUNCH();
         W.sinv_ready = true;
     }
-    if (mixed) {
+    if (f32_inner) {
+        W.t32.alloc(n_u * sizeof(float));
+        W.y32.alloc(n_u * sizeof(float));
+    } else if (mixed) {
         for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
         W.sc_in.alloc(8 * sizeof(double));
     }
@@ -812,7 +844,12 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         launch_apply_B<double>(P->k, P->geom, z + n_u, W.tu.as<double>(), s);
         launch_axpby<double>(n_u, 1.0, v, -1.0, W.tu.as<double>(), s);        // t = v_u - B y_p
         int its;
-        if (mixed) {
+        if (f32_inner) {
+            launch_cast<double, float>(n_u, W.tu.as<double>(), W.t32.as<float>(), s);
+            its = P->mg32->inner_pcg(W.t32.as<float>(), W.y32.as<float>(), o.inner_rtol,
+                                     o.max_inner, s, nullptr);
+            launch_cast<float, double>(n_u, W.y32.as<float>(), z, s);
+        } else if (mixed) {
             its = inner_pcg_mixed(P, W, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s);
         } else {
             its = P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s, nullptr);
@@ -978,7 +1015,7 @@ void sip_problem::derive_eta(cudaStream_t s) {
 void sip_problem::ensure_setup(cudaStream_t s) {
     const double t0 = sip::now_ms();
     bool did = false;
-    if (desc.precision == SIP_PREC_MIXED) {
+    if (desc.precision == SIP_PREC_MIXED || desc.precision == SIP_PREC_MIXED_F32_INNER) {
         if (!mg32) {
             mg32 = std::make_unique<sip::Multigrid<float>>();
             mg32->P = this;

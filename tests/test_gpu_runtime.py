@@ -1,0 +1,98 @@
+"""Batched and served solves: every result equals the same solve run alone
+(through the C ABI), admission by device footprint, request bookkeeping."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1607_03777_gb300 import _lib, api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(count, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(g.choice([16, 32]))
+        k = int(g.choice([2, 3]))
+        shapes = synth.random_discs(4, 0.08, (1.0, 3.0), int(g.integers(0, 2 ** 31)), shared_eta=True)
+        out.append((n, k, shapes, "mixed" if i % 2 else "fp64"))
+    return out
+
+
+def _alone(ctx, n, k, shapes, precision):
+    eta, rho = ctx.rasterise_inclusions(n, n, shapes)
+    prob = api.Problem(ctx, n, n, k, eta.cpu().numpy(), bc=synth.SINKER_BC,
+                       n_hlevels=synth.levels_to_17(n) if n > 16 else 1, seed=2,
+                       precision=precision)
+    f = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    prob.rhs_body_force(rho, synth.GRAVITY, f)
+    u = torch.empty_like(f)
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(f, u, p, rtol=1e-8)
+    return prob, f, u, p, rep, eta.cpu().numpy(), rho.cpu().numpy()
+
+
+def test_batch_matches_alone(ctx):
+    inst = _instances(6, 1)
+    alone = [_alone(ctx, *x) for x in inst]
+    probs = [a[0] for a in alone]
+    fs = [a[1] for a in alone]
+    us = [torch.empty_like(a[2]) for a in alone]
+    ps = [torch.empty_like(a[3]) for a in alone]
+    st, reps = api.solve_batch(ctx, probs, fs, us, ps, n_streams=4, rtol=1e-8)
+    assert st == _lib.SIP_OK
+    for a, u, p, r in zip(alone, us, ps, reps):
+        assert r["status"] == 0 and r["rel_residual"] <= 1e-8
+        assert torch.equal(u, a[2]) and torch.equal(p, a[3])
+
+
+def test_server_matches_alone_and_reports_latency(ctx):
+    inst = _instances(8, 2)
+    alone = [_alone(ctx, *x) for x in inst]
+    srv = api.Server(ctx, budget_bytes=8 << 30, max_slots=3)
+    outs = {}
+    for rid, (x, a) in enumerate(zip(inst, alone)):
+        n, k, shapes, precision = x
+        st, u, p = srv.submit(rid, n, n, k, a[5], a[6], g=synth.GRAVITY, bc=synth.SINKER_BC,
+                              n_hlevels=synth.levels_to_17(n) if n > 16 else 1, seed=2,
+                              precision=precision)
+        assert st == _lib.SIP_OK
+        outs[rid] = (u, p)
+    srv.drain()
+    done = dict(srv.poll())
+    assert sorted(done) == list(range(len(inst)))
+    for rid, a in enumerate(alone):
+        rep = done[rid]
+        assert rep["status"] == 0 and rep["rel_residual"] <= 1e-8
+        assert rep["solve_ms"] > 0
+        u, p = outs[rid]
+        assert np.array_equal(u, a[2].cpu().numpy()) and np.array_equal(p, a[3].cpu().numpy())
+    assert srv.stats() == {"queued": 0, "running": 0, "bytes_in_use": 0}
+    srv.close()
+
+
+def test_server_admission_rejects_oversized_request(ctx):
+    n, k = 32, 3
+    need = api.footprint(ctx, nx=n, ny=n, k=k, eta=np.ones(n * n), n_hlevels=1)
+    assert need > 0
+    srv = api.Server(ctx, budget_bytes=need // 2, max_slots=2)
+    st, _, _ = srv.submit(7, n, n, k, np.ones(n * n), np.ones(n * n), n_hlevels=1)
+    assert st == 7     # SIP_ERR_REJECTED
+    got = srv.poll()
+    assert got and got[0][0] == 7 and got[0][1]["status"] == 7
+    srv.close()
+
+
+def test_server_queues_beyond_slots(ctx):
+    """More requests than slots: all are admitted in turn and finish."""
+    srv = api.Server(ctx, budget_bytes=8 << 30, max_slots=1)
+    n, k = 16, 2
+    eta = synth.random_eta(n * n, 3, (0.0, 2.0))
+    for rid in range(4):
+        srv.submit(rid, n, n, k, eta, np.ones(n * n), n_hlevels=1, bc=synth.SINKER_BC)
+    srv.drain()
+    done = srv.poll()
+    assert sorted(i for i, _ in done) == [0, 1, 2, 3]
+    assert all(r["status"] == 0 for _, r in done)
+    srv.close()
