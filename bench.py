@@ -109,15 +109,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(value, world, device=None):
+    """Largest per-rank value over all ranks (the slowest rank's time);
+    identity on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, total_ms):
+    """Solves per second of the whole job: every rank solves ``steps``
+    independent instances; the job takes as long as its slowest rank."""
+    return world * steps / (total_ms / 1000.0)
+
+
 # ------------------------------------------------------------------ ours
 def algorithmic_apply(prob_k, ne, word):
-    """Algorithmic bytes and flops of one SIP apply: read x, write y, read
-    eta_K per element; flops of the closed-form modal apply (volume
-    sum-factorisation 8 n^3 FMA + face traces / vectors ~56 n^2 FMA)."""
+    """Algorithmic bytes and flops of one SIP apply, per element: read x,
+    write y (2 n^2 coefficients each) and read eta_K; 16 n^3 flops for the
+    volume terms by sum-factorisation plus 128 n^2 for the face terms
+    (n = k + 1).  Neighbour re-reads are not algorithmic."""
     n = prob_k + 1
     nb = 2 * n * n
     bytes_ = ne * (2 * nb * word + word)
-    flops = ne * 2 * (8 * n ** 3 + 56 * n * n)
+    flops = ne * (16 * n ** 3 + 128 * n * n)
     return bytes_, flops
 
 
@@ -174,12 +194,8 @@ def run_ours(args, rank, world):
 
     clocks = ClockSampler(dev.index)
     prob64, f64, u64, p64, t64, r64, clk = timed("fp64", args.steps, args.warmup, clocks)
-    total_ms = sum(t64)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(t64), world, dev)
+    value = whole_job_rate(args.steps, world, total_ms)
     if args.profile_only:
         return {"metric": METRIC, "value": value, "unit": UNIT, "profile_only": True,
                 "solve_report": r64[-1]}
@@ -212,20 +228,23 @@ def run_ours(args, rank, world):
             e2e_ms.append((time.perf_counter() - t0) * 1000.0)
     e2e_value = world * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
 
-    # live timing of the dominant kernel: the FP64 SIP apply, on this stream
+    # live timing of the dominant kernel, the FP64 SIP apply, on this
+    # stream: one event pair per launch, L2 flushed between launches
     x = torch.randn(prob64.n_u, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     for _ in range(5):
-        prob64.apply_A(x, y)
+        prob64.apply_A(x, y, stream=stream)
     reps_apply = 50
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps_apply):
-        prob64.apply_A(x, y)
-    e1.record(stream)
-    e1.synchronize()
-    apply_ms = e0.elapsed_time(e1) / reps_apply
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps_apply)]
+    for e0, e1 in ev:
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        e0.record(stream)
+        prob64.apply_A(x, y, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps_apply
     ab, af = algorithmic_apply(k, n * n, 8)
 
     launches = sum(r["kernel_launches"] for r in r64)
@@ -264,8 +283,11 @@ def run_ours(args, rank, world):
 # 2 FP64 FMA per SM per clock x 2 FLOP x 2.07 GHz (maximum SM clock)
 # = 1.259 TFLOP/s (NVIDIA's figure: 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-DOMINANT = "k_apply_elem<4,double>"
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_apply_elem_fp64_128x128_k3.md")
+# the kernel sip_apply_A launches for k = 3 in FP64 (component split,
+# 16-byte vector accesses; SIP_APPLY_KERNEL=elem1 / tile select the others)
+DOMINANT = {"elem1": "k_apply_elem<4,double>", "tile": "k_apply_sip<4,double>"}.get(
+    os.environ.get("SIP_APPLY_KERNEL", ""), "k_apply_elem2<4,double,true>")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md")
 
 
 def captured_traffic():

@@ -193,6 +193,10 @@ typedef struct {
     int restart;        /* FGMRES restart length                                    */
     double inner_rtol;  /* inner PCG relative tolerance (paper 1e-3)                */
     int max_inner;      /* inner iteration cap                                      */
+    int inner_loop;     /* 0: each inner PCG solve is one CUDA graph launch whose   *
+                         *    loop runs on the device (default); 1: host-driven     *
+                         *    loop, one read-back per iteration.  Same arithmetic:  *
+                         *    both give bit-identical iterates.                     */
 } sip_solve_opts;
 
 typedef struct {
@@ -208,7 +212,8 @@ typedef struct {
     int64_t kernel_launches;
 } sip_solve_report;
 
-/* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200. */
+/* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
+ * inner_loop 0. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES with the upper block-triangular preconditioner

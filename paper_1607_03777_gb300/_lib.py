@@ -47,6 +47,7 @@ class SolveOpts(ctypes.Structure):
         ("restart", ctypes.c_int),
         ("inner_rtol", ctypes.c_double),
         ("max_inner", ctypes.c_int),
+        ("inner_loop", ctypes.c_int),
     ]
 
 

@@ -213,13 +213,11 @@ class Problem:
 
     # -- Stokes solve --------------------------------------------------------
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
-              max_inner=200, stream=None, check=True):
+              max_inner=200, inner_loop="device", stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
-        ``check``)."""
-        o = SolveOpts()
-        self.ctx.lib.sip_solve_opts_default(ctypes.byref(o))
-        o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
-        o.inner_rtol, o.max_inner = inner_rtol, max_inner
+        ``check``).  ``inner_loop`` = "device" (one graph launch per inner
+        solve) or "host" (host-driven loop)."""
+        o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -252,11 +250,16 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
     return d, eta
 
 
-def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200):
+INNER_LOOP = {"device": 0, "host": 1}
+
+
+def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
+          inner_loop="device"):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
     o.inner_rtol, o.max_inner = inner_rtol, max_inner
+    o.inner_loop = INNER_LOOP[inner_loop] if isinstance(inner_loop, str) else int(inner_loop)
     return o
 
 

@@ -104,6 +104,30 @@ __device__ __forceinline__ void face_traces(const T (&u)[2][N][N], int F, T two_
         }
 }
 
+// Component c only of face_traces (c uniform within a warp).
+template <int N, typename T>
+__device__ __forceinline__ void face_traces_comp(const T (&u)[2][N][N], int F, int c,
+                                                 T two_over_h, T* out /* [2][2][N] */) {
+    const bool plus = (F & 1) != 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        T ev = T(0), od = T(0), evd = T(0), odd = T(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const T uq = F < 2 ? u[c][m][q] : u[c][q][m];
+            if (q % 2 == 0) {
+                ev += T(kT<N>.lp[q]) * uq;
+                if (q > 0) evd += T(kT<N>.dp[q]) * uq;
+            } else {
+                od += T(kT<N>.lp[q]) * uq;
+                odd += T(kT<N>.dp[q]) * uq;
+            }
+        }
+        out[0 * 2 * N + c * N + m] = plus ? ev + od : ev - od;
+        out[1 * 2 * N + c * N + m] = (plus ? evd + odd : odd - evd) * two_over_h;
+    }
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
     constexpr int TR = 4 * N;                 // [2 val/der][2 comp][N] per face
@@ -307,6 +331,299 @@ __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
             }
 }
 
+// Component-split variant: one warp = one velocity component of 32
+// consecutive elements of a row (warps 2r and 2r+1 share row r of the tile),
+// so every element is served by two threads and twice as many warps keep the
+// narrow FP64 pipe busy.  The component is uniform within a warp: no
+// divergence.  Each thread reads both components (the volume cross terms and
+// the face terms couple them), writes its component's traces to shared memory
+// and computes its component's outputs.
+constexpr int TY2 = 2;                        // tile rows
+constexpr int T2THREADS = 64 * TY2;           // 2 warps per tile row
+constexpr int NHALO2 = 2 * TX + 2 * TY2;
+
+// 16-byte vector accesses to one element's coefficients.  A thread reads a
+// whole element (2 N^2 contiguous values), so scalar loads cost one L1
+// wavefront per value and warp; 16-byte loads cut that by 2 (FP64) or 4
+// (FP32).  Usable when an element and a component block are multiples of 16
+// bytes (N = 2, 4) and the vectors are 16-byte aligned (checked at launch).
+template <typename T> struct Vec16;
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+    __device__ static double2 make(const double* p) { return make_double2(p[0], p[1]); }
+};
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static float get(const float4& v, int i) {
+        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    }
+    __device__ static float4 make(const float* p) { return make_float4(p[0], p[1], p[2], p[3]); }
+};
+
+template <int N, typename T>
+constexpr bool vec_ok() {
+    return (N * N * sizeof(T)) % 16 == 0;
+}
+
+template <int N, typename T, bool VEC>
+__device__ __forceinline__ void load_elem(const T* __restrict__ src, T (&u)[2][N][N]) {
+    constexpr int NN = N * N;
+    if constexpr (VEC && vec_ok<N, T>()) {
+        using V = Vec16<T>;
+        const typename V::type* s = reinterpret_cast<const typename V::type*>(src);
+#pragma unroll
+        for (int k = 0; k < 2 * NN / V::n; ++k) {
+            const typename V::type v = __ldg(s + k);
+#pragma unroll
+            for (int t = 0; t < V::n; ++t) {
+                const int f = k * V::n + t;
+                u[f / NN][(f % NN) / N][f % N] = V::get(v, t);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) u[c][j][i] = src[c * NN + j * N + i];
+    }
+}
+
+// dst[j][i] = alpha y[j][i] (+ beta zz[j][i]) over one component block
+template <int N, typename T, bool VEC>
+__device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
+                                           const T (&y)[N][N]) {
+    if constexpr (VEC && vec_ok<N, T>()) {
+        using V = Vec16<T>;
+        typename V::type* d = reinterpret_cast<typename V::type*>(dst);
+#pragma unroll
+        for (int k = 0; k < N * N / V::n; ++k) {
+            T v[V::n];
+            if (zz) {
+                const typename V::type zv = __ldg(reinterpret_cast<const typename V::type*>(zz) + k);
+#pragma unroll
+                for (int t = 0; t < V::n; ++t) {
+                    const int f = k * V::n + t;
+                    v[t] = alpha * y[f / N][f % N] + beta * V::get(zv, t);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < V::n; ++t) {
+                    const int f = k * V::n + t;
+                    v[t] = alpha * y[f / N][f % N];
+                }
+            }
+            d[k] = V::make(v);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T v = alpha * y[j][i];
+                if (zz) v += beta * zz[j * N + i];
+                dst[j * N + i] = v;
+            }
+    }
+}
+
+// Work of one component C (compile-time, so the register arrays stay in
+// registers) in phase A: own traces of component C and the volume terms of y_C.
+template <int N, typename T, int C>
+__device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)[2][N][N], T etaK,
+                                              T (*tr)[4 * N], T (&y)[N][N]) {
+#pragma unroll
+    for (int F = 0; F < 4; ++F)
+        face_traces_comp<N, T>(u, F, C, F < 2 ? a.two_over_hx : a.two_over_hy, tr[F]);
+    const T sx = C == 0 ? a.c2hy_hx : a.chy_hx;   // weight of G along x on u_C
+    const T sy = C == 0 ? a.chx_hy : a.c2hx_hy;   // weight of G along y on u_C
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int av = 0; av < N; ++av) {
+            T gx = T(0), gy = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                if (kT<N>.G[av][i] != 0.0) gx += T(kT<N>.G[av][i]) * u[C][b][i];
+                if (kT<N>.G[b][i] != 0.0) gy += T(kT<N>.G[b][i]) * u[C][i][av];
+            }
+            y[b][av] = sx * gx + sy * gy;
+        }
+    T w[N][N];
+    if (C == 0) {
+        // y_x[b][a] += sum_j D[j][b] sum_i D[a][i] u_y[j][i]
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int av = 0; av < N; ++av) {
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+                    if (kT<N>.D[av][i] != 0.0) s += T(kT<N>.D[av][i]) * u[1][j][i];
+                w[j][av] = s;
+            }
+#pragma unroll
+        for (int b = 0; b < N; ++b)
+#pragma unroll
+            for (int av = 0; av < N; ++av)
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (kT<N>.D[j][b] != 0.0) y[b][av] += T(kT<N>.D[j][b]) * w[j][av];
+    } else {
+        // y_y[b][a] += sum_i D[i][a] sum_j D[b][j] u_x[j][i]
+#pragma unroll
+        for (int b = 0; b < N; ++b)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T s = T(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (kT<N>.D[b][j] != 0.0) s += T(kT<N>.D[b][j]) * u[0][j][i];
+                w[b][i] = s;
+            }
+#pragma unroll
+        for (int b = 0; b < N; ++b)
+#pragma unroll
+            for (int av = 0; av < N; ++av)
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+                    if (kT<N>.D[i][av] != 0.0) y[b][av] += T(kT<N>.D[i][av]) * w[b][i];
+    }
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int av = 0; av < N; ++av) y[b][av] *= etaK;
+}
+
+// Phase B of component C: face vectors from own and neighbour traces, spread
+// into y_C, written out.
+template <int N, typename T, int C, bool VEC>
+__device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int ey, int ex0, int ey0,
+                                              int tx, int ty, T etaK, T (*s_tr)[4][4 * N],
+                                              T (*s_halo)[4 * N], int el, T (&y)[N][N]) {
+    constexpr int NB = 2 * N * N;
+    const int nx = a.nx, ny = a.ny;
+    T Dm[N * N];
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+        for (int q = 0; q < N; ++q) Dm[p * N + q] = T(kT<N>.D[p][q]);
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        T PQ[2][2][N];   // [face lo/hi][P/Q][m]
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int F = 2 * dir + side;
+            const T* own = s_tr[el][F];
+            const T* nbr = own;
+            T etaN = T(0);
+            int kind;
+            const bool has_nbr = dir == 0 ? (side == 0 ? ex > 0 : ex < nx - 1)
+                                          : (side == 0 ? ey > 0 : ey < ny - 1);
+            if (has_nbr) {
+                kind = 0;
+                const int nxi = ex + (dir == 0 ? (side == 0 ? -1 : 1) : 0);
+                const int nyi = ey + (dir == 1 ? (side == 0 ? -1 : 1) : 0);
+                etaN = a.eta[size_t(nyi) * nx + nxi];
+                const int ltx = nxi - ex0, lty = nyi - ey0;
+                if (ltx >= 0 && ltx < TX && lty >= 0 && lty < TY2)
+                    nbr = s_tr[lty * TX + ltx][F ^ 1];
+                else if (dir == 1)
+                    nbr = s_halo[(side == 0 ? 0 : TX) + tx];
+                else
+                    nbr = s_halo[2 * TX + (side == 0 ? 0 : TY2) + ty];
+            } else {
+                kind = 1 + a.bc[F];
+            }
+            const T eta_e = kind == 0 ? (etaK > etaN ? etaK : etaN) : etaK;
+            const T pen = dir == 0 ? a.pen_x : a.pen_y;
+            const T sigma = pen * eta_e * (kind == 0 ? T(1) : T(2));
+            const T s = side == 0 ? T(-1) : T(1);
+            const FaceGeo<T>& fg = dir == 0 ? a.fgx : a.fgy;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                T P, Q;
+                face_pq<N, T>(kind, C, m, dir, s, fg, etaK, etaN, sigma, own, own + 2 * N, nbr,
+                              nbr + 2 * N, Dm, P, Q);
+                PQ[side][0][m] = P;
+                PQ[side][1][m] = Q;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const T pp = PQ[1][0][m] + PQ[0][0][m];
+            const T pm = PQ[1][0][m] - PQ[0][0][m];
+            const T qp = PQ[1][1][m] + PQ[0][1][m];
+            const T qm = PQ[1][1][m] - PQ[0][1][m];
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                T add = q % 2 == 0 ? T(kT<N>.lp[q]) * pp : T(kT<N>.lp[q]) * pm;
+                if (q > 0) add += q % 2 == 0 ? T(kT<N>.dp[q]) * qm : T(kT<N>.dp[q]) * qp;
+                if (dir == 0)
+                    y[m][q] += add;
+                else
+                    y[q][m] += add;
+            }
+        }
+    }
+    T* dst = a.y + (size_t(ey) * nx + ex) * NB + C * N * N;
+    const T* zz = a.z ? a.z + (size_t(ey) * nx + ex) * NB + C * N * N : nullptr;
+    store_comp<N, T, VEC>(dst, zz, a.alpha, a.beta, y);
+}
+
+template <int N, typename T, bool VEC>
+__global__ void __launch_bounds__(T2THREADS) k_apply_elem2(const ElemArgs<T> a) {
+    constexpr int TR = 4 * N;
+    constexpr int NB = 2 * N * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);   // [TX*TY2][4][TR]
+    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ty = warp / 2, c = warp % 2;    // tile row, velocity component (warp-uniform)
+    const int tx = lane;
+    const int el = ty * TX + tx;
+    const int ex0 = blockIdx.x * TX, ey0 = blockIdx.y * TY2;
+    const int ex = ex0 + tx, ey = ey0 + ty;
+    const int nx = a.nx, ny = a.ny;
+    const bool active = ex < nx && ey < ny;
+
+    // ---- phase A: halo traces (both components of the face touching the tile)
+    for (int h = threadIdx.x; h < NHALO2; h += T2THREADS) {
+        int hx, hy, F;
+        if (h < TX) { hx = ex0 + h; hy = ey0 - 1; F = 3; }
+        else if (h < 2 * TX) { hx = ex0 + h - TX; hy = ey0 + TY2; F = 2; }
+        else if (h < 2 * TX + TY2) { hx = ex0 - 1; hy = ey0 + h - 2 * TX; F = 1; }
+        else { hx = ex0 + TX; hy = ey0 + h - 2 * TX - TY2; F = 0; }
+        if (hx >= 0 && hx < nx && hy >= 0 && hy < ny) {
+            T uh[2][N][N];
+            load_elem<N, T, VEC>(a.x + (size_t(hy) * nx + hx) * NB, uh);
+            face_traces<N, T>(uh, F, F < 2 ? a.two_over_hx : a.two_over_hy, s_halo[h]);
+        }
+    }
+    // ---- phase A: own traces and volume terms of this thread's component
+    T y[N][N];
+    T etaK = T(0);
+    if (active) {
+        T u[2][N][N];
+        load_elem<N, T, VEC>(a.x + (size_t(ey) * nx + ex) * NB, u);
+        etaK = a.eta[size_t(ey) * nx + ex];
+        if (c == 0)
+            elem2_phase_a<N, T, 0>(a, u, etaK, s_tr[el], y);
+        else
+            elem2_phase_a<N, T, 1>(a, u, etaK, s_tr[el], y);
+    }
+    __syncthreads();
+    if (!active) return;
+    if (c == 0)
+        elem2_phase_b<N, T, 0, VEC>(a, ex, ey, ex0, ey0, tx, ty, etaK, s_tr, s_halo, el, y);
+    else
+        elem2_phase_b<N, T, 1, VEC>(a, ex, ey, ex0, ey0, tx, ty, etaK, s_tr, s_halo, el, y);
+}
+
 template <int N, typename T>
 void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z, T beta,
                   cudaStream_t s) {
@@ -330,6 +647,30 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
     for (int i = 0; i < 4; ++i) a.bc[i] = g.bc[i];
     a.pen_x = T(g.pen_x);
     a.pen_y = T(g.pen_y);
+    // two threads per element (component split) unless SIP_APPLY_KERNEL=elem1
+    static const bool split = [] {
+        const char* v = std::getenv("SIP_APPLY_KERNEL");
+        return !(v && std::string(v) == "elem1");
+    }();
+    if (split) {
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
+        const size_t smem = sizeof(T) * (size_t(TX) * TY2 * 4 + NHALO2) * 4 * N;
+        static const bool attr2 = [smem] {   // once per process, thread-safe
+            SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            return true;
+        }();
+        (void)attr2;
+        const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+        if (vec_ok<N, T>() && al16(x) && al16(y) && (z == nullptr || al16(z)))
+            k_apply_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a);
+        else
+            k_apply_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a);
+        SIP_CHECK_LAUNCH();
+        return;
+    }
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
     const size_t smem = sizeof(T) * (size_t(TXY) * 4 + NHALO) * 4 * N;
     static const bool attr_set = [smem] {   // once per process, thread-safe

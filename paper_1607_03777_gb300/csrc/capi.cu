@@ -454,6 +454,7 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->restart = 100;
     o->inner_rtol = 1e-3;
     o->max_inner = 200;
+    o->inner_loop = 0;
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -467,7 +468,8 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
         if (opts) o = *opts;
         sip::require(std::isfinite(o.rtol) && o.rtol > 0 && o.max_outer >= 1 && o.restart >= 1 &&
                          o.restart <= 250 &&
-                         std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1,
+                         std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1 &&
+                         (o.inner_loop == 0 || o.inner_loop == 1),
                      "bad solve options");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));

@@ -1,0 +1,348 @@
+// Inner PCG of the block preconditioner (Sec. 5: the viscous block solved
+// to a relative tolerance by CG preconditioned with one hp-multigrid V-cycle)
+// as ONE CUDA graph launch per solve: the iteration is a device-side `while`
+// conditional node, the stopping test (||r|| < rtol ||t|| or the iteration
+// cap) is taken by a one-block kernel at the end of every pass, and alpha,
+// beta, the norms and the counter stay in device memory.  No host round trip
+// happens inside the loop.
+//
+// The arithmetic is that of the host-driven loop step for step (same
+// kernels' blocking, same reduction order), so the iterates are identical.
+// The loop ends by construction: the control kernel runs once per pass,
+// increments the counter unconditionally and clears the condition once the
+// counter reaches the cap, which the host clamps to [1, 100000].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "sip_solver.h"
+
+namespace sip {
+
+namespace {
+
+constexpr int kRB = 304;   // reduction blocks (2 x 152 SMs), fixed: deterministic sums
+constexpr int kRT = 256;
+
+struct PcgState {
+    const double* t;   // right-hand side (set before each launch)
+    double* y;         // iterate (set before each launch)
+    double nt, rz, alpha, beta, rr;
+    int it, status;    // status 0 ok, 1 non-finite
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    v = warp_sum(v);
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    v = threadIdx.x < blockDim.x / 32 ? ws[lane] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ double final_sum(const double* partial) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kRB; i += blockDim.x) acc += partial[i];
+    return block_sum(acc);
+}
+
+__global__ void k_set(PcgState* st, const double* t, double* y) {
+    st->t = t;
+    st->y = y;
+}
+
+// r = t, y = 0, d = 0; partial sums of t.t
+__global__ void __launch_bounds__(kRT) k_init(size_t n, PcgState* st, double* r, double* d,
+                                              double* partial) {
+    const double* t = st->t;
+    double* y = st->y;
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        const double v = t[g];
+        acc += v * v;
+        r[g] = v;
+        y[g] = 0.0;
+        d[g] = 0.0;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRT) k_init_final(PcgState* st, const double* partial,
+                                                    cudaGraphConditionalHandle h) {
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) {
+        const double nt = sqrt(s);
+        st->nt = nt;
+        st->rr = nt;
+        st->rz = 0.0;
+        st->it = 0;
+        st->status = isfinite(nt) ? 0 : 1;
+        cudaGraphSetConditional(h, (isfinite(nt) && nt > 0.0) ? 1u : 0u);
+    }
+}
+
+// partial sums of r.z, with z = widen(zs) stored into zd when zd != nullptr
+template <typename Tz>
+__global__ void __launch_bounds__(kRT) k_dot_rz(size_t n, const double* __restrict__ r,
+                                                const Tz* __restrict__ zs, double* zd,
+                                                double* partial) {
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        const double z = double(zs[g]);
+        if (zd) zd[g] = z;
+        acc += r[g] * z;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// beta = rz_new / rz (0 on the first pass); rz = rz_new
+__global__ void __launch_bounds__(kRT) k_beta_final(PcgState* st, const double* partial) {
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) {
+        st->beta = st->it == 0 ? 0.0 : s / st->rz;
+        st->rz = s;
+    }
+}
+
+// d = z + beta d
+__global__ void k_dir(size_t n, const double* __restrict__ z, double* d, const PcgState* st) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    d[g] = z[g] + st->beta * d[g];
+}
+
+__global__ void __launch_bounds__(kRT) k_dot(size_t n, const double* __restrict__ a,
+                                             const double* __restrict__ b, double* partial) {
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x)
+        acc += a[g] * b[g];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// alpha = rz / (d.q)
+__global__ void __launch_bounds__(kRT) k_alpha_final(PcgState* st, const double* partial) {
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) st->alpha = st->rz / s;
+}
+
+// y += alpha d; r -= alpha q; partial sums of r.r
+__global__ void __launch_bounds__(kRT) k_update_rr(size_t n, const double* __restrict__ d,
+                                                   const double* __restrict__ q, double* r,
+                                                   const PcgState* st, double* partial) {
+    const double a = st->alpha;
+    double* y = st->y;
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        y[g] += a * d[g];
+        const double rv = r[g] - a * q[g];
+        r[g] = rv;
+        acc += rv * rv;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// End of one pass: counter, stopping test, loop condition.
+__global__ void __launch_bounds__(kRT) k_ctl_final(PcgState* st, const double* partial,
+                                                   double rtol, int maxit,
+                                                   cudaGraphConditionalHandle h) {
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) {
+        const double rr = sqrt(s);
+        const int it = st->it + 1;
+        st->it = it;
+        st->rr = rr;
+        if (!isfinite(rr)) st->status = 1;
+        const bool more = isfinite(rr) && !(rr < rtol * st->nt) && it < maxit;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+inline unsigned nblk(size_t n) { return unsigned((n + 255) / 256); }
+
+}  // namespace
+
+struct InnerLoop {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    DeviceBuffer state, partial;
+    HostScalars hs;             // pinned read-back of the state
+    bool mixed = false;
+    double rtol = -1.0;
+    int maxit = -1;
+    int gen = -1;
+    const void* mg = nullptr;
+    int64_t top_kernels = 0, body_kernels = 0;
+
+    ~InnerLoop() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+void InnerLoopDeleter::operator()(InnerLoop* p) const { delete p; }
+
+namespace {
+
+// One pass of the loop body, captured into the conditional node's graph.
+void capture_body(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphConditionalHandle h,
+                  cudaStream_t cs) {
+    const size_t n_u = size_t(P->n_u);
+    double* r = W.cg_r.as<double>();
+    double* d = W.cg_d.as<double>();
+    double* q = W.cg_q.as<double>();
+    double* z = W.cg_z.as<double>();
+    double* part = L.partial.as<double>();
+    PcgState* st = L.state.as<PcgState>();
+    if (L.mixed) {
+        Multigrid<float>& mg = *P->mg32;
+        float* vin = mg.vin.as<float>();
+        float* vout = mg.vout.as<float>();
+        launch_cast<double, float>(n_u, r, vin, cs);
+        mg.vcycle_on(vin, vout, cs);
+        k_dot_rz<float><<<kRB, kRT, 0, cs>>>(n_u, r, vout, z, part);
+        SIP_CHECK_LAUNCH();
+    } else {
+        Multigrid<double>& mg = *P->mg64;
+        mg.vcycle_on(r, z, cs);
+        k_dot_rz<double><<<kRB, kRT, 0, cs>>>(n_u, r, z, nullptr, part);
+        SIP_CHECK_LAUNCH();
+    }
+    k_beta_final<<<1, kRT, 0, cs>>>(st, part);
+    SIP_CHECK_LAUNCH();
+    k_dir<<<nblk(n_u), 256, 0, cs>>>(n_u, z, d, st);
+    SIP_CHECK_LAUNCH();
+    launch_apply_sip<double>(P->n, P->geom, d, q, P->eta_d.as<double>(), 1.0, nullptr, 0.0, cs);
+    k_dot<<<kRB, kRT, 0, cs>>>(n_u, d, q, part);
+    SIP_CHECK_LAUNCH();
+    k_alpha_final<<<1, kRT, 0, cs>>>(st, part);
+    SIP_CHECK_LAUNCH();
+    k_update_rr<<<kRB, kRT, 0, cs>>>(n_u, d, q, r, st, part);
+    SIP_CHECK_LAUNCH();
+    k_ctl_final<<<1, kRT, 0, cs>>>(st, part, L.rtol, L.maxit, h);
+    SIP_CHECK_LAUNCH();
+}
+
+void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
+    if (L.exec) {
+        SIP_CUDA(cudaGraphExecDestroy(L.exec));
+        L.exec = nullptr;
+    }
+    if (L.graph) {
+        SIP_CUDA(cudaGraphDestroy(L.graph));
+        L.graph = nullptr;
+    }
+    if (!L.cs) SIP_CUDA(cudaStreamCreateWithFlags(&L.cs, cudaStreamNonBlocking));
+    SIP_CUDA(cudaStreamSynchronize(s));   // buffers allocated on s are ready
+    const size_t n_u = size_t(P->n_u);
+    const int64_t before = launch_counter();
+    cudaGraph_t g = nullptr;
+    SIP_CUDA(cudaGraphCreate(&g, 0));
+    L.graph = g;
+    cudaGraphConditionalHandle h;
+    SIP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    // pre-loop part (r = t, y = 0, d = 0, ||t||, first condition), then the
+    // while node after it
+    SIP_CUDA(cudaStreamBeginCaptureToGraph(L.cs, g, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    k_init<<<kRB, kRT, 0, L.cs>>>(n_u, L.state.as<PcgState>(), W.cg_r.as<double>(),
+                                  W.cg_d.as<double>(), L.partial.as<double>());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_init_final<<<1, kRT, 0, L.cs>>>(L.state.as<PcgState>(), L.partial.as<double>(), h);
+        e = cudaGetLastError();
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nloop = nullptr;
+    if (e == cudaSuccess) {
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(L.cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (e == cudaSuccess) e = cudaGraphAddNode(&nloop, g, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(L.cs, &nloop, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies);
+    }
+    cudaGraph_t gout = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(L.cs, &gout);
+    SIP_CUDA(e);
+    SIP_CUDA(ee);
+    L.top_kernels = 2;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    SIP_CUDA(cudaStreamBeginCaptureToGraph(L.cs, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    const int64_t b0 = launch_counter();
+    try {
+        capture_body(P, W, L, h, L.cs);
+    } catch (...) {
+        cudaGraph_t tmp;
+        cudaStreamEndCapture(L.cs, &tmp);
+        launch_counter() = before;
+        throw;
+    }
+    L.body_kernels = launch_counter() - b0;
+    cudaGraph_t body_out;
+    SIP_CUDA(cudaStreamEndCapture(L.cs, &body_out));
+    launch_counter() = before;
+    SIP_CUDA(cudaGraphInstantiate(&L.exec, g, 0));
+}
+
+}  // namespace
+
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, const double* t, double* y,
+                    double rtol, int maxit, cudaStream_t s) {
+    maxit = std::max(1, std::min(maxit, 100000));
+    const size_t n_u = size_t(P->n_u);
+    for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
+    if (!W.loop) W.loop.reset(new InnerLoop());
+    InnerLoop& L = *W.loop;
+    static_assert(sizeof(PcgState) <= 256 * sizeof(double), "state fits the pinned block");
+    L.state.alloc(sizeof(PcgState));
+    L.partial.alloc(kRB * sizeof(double));
+    const void* mg = mixed ? static_cast<const void*>(P->mg32.get())
+                           : static_cast<const void*>(P->mg64.get());
+    const int gen = mixed ? P->mg32->setup_gen : P->mg64->setup_gen;
+    if (!L.exec || L.mixed != mixed || L.rtol != rtol || L.maxit != maxit || L.gen != gen ||
+        L.mg != mg) {
+        L.mixed = mixed;
+        L.rtol = rtol;
+        L.maxit = maxit;
+        L.gen = gen;
+        L.mg = mg;
+        build_loop(P, W, L, s);
+    }
+    k_set<<<1, 1, 0, s>>>(L.state.as<PcgState>(), t, y);
+    SIP_CHECK_LAUNCH();
+    SIP_CUDA(cudaGraphLaunch(L.exec, s));
+    SIP_CUDA(cudaMemcpyAsync(L.hs.p, L.state.ptr, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SIP_CUDA(cudaStreamSynchronize(s));
+    const PcgState& hs = *reinterpret_cast<const PcgState*>(L.hs.p);
+    launch_counter() += L.top_kernels + L.body_kernels * hs.it;
+    if (hs.status != 0) throw Error(SIP_ERR_BREAKDOWN, "non-finite inner residual");
+    return hs.it;
+}
+
+}  // namespace sip

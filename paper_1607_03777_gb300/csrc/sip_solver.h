@@ -31,6 +31,12 @@ template <typename T>
 void launch_jacobi_cheb(size_t n, const T* r, const T* dinv, T* d, T* x, T c1, T c2, bool x_zero,
                         cudaStream_t s);
 template <typename T> void launch_ph_add(int nxc, int nyc, const T* xc, T* yf, cudaStream_t s);
+template <typename T>
+void launch_hcheb_first(size_t n, const T* b, const T* dinv, T* r, T* d, T* x, T c2,
+                        cudaStream_t s);
+template <typename T>
+void launch_hcheb_step(int nvx, int nvy, const T* S, const T* dinv, T* r, const T* d_old,
+                       T* d_new, T* x, T c1, T c2, cudaStream_t s);
 template <typename T> void launch_rh(int nxc, int nyc, const T* rf, T* rc, cudaStream_t s);
 template <typename T>
 void launch_probe_vertices(int nvx, int nvy, int col, int cp, T* x, cudaStream_t s);
@@ -82,7 +88,7 @@ struct HLevel {
     int nx = 0, ny = 0;       // elements of this level's grid
     int nvx = 0, nvy = 0;     // vertices
     size_t n = 0;             // dofs = 2 nvx nvy
-    DeviceBuffer S, dinv, b, x, r, d;
+    DeviceBuffer S, dinv, b, x, r, d, d2;
     double lmax = 0.0;
 };
 
@@ -112,6 +118,7 @@ struct Multigrid {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
     int64_t graph_kernels = 0;
+    int setup_gen = 0;   // incremented by every set-up (graphs holding its kernels go stale)
     bool ready = false;
 
     ~Multigrid();
@@ -119,6 +126,7 @@ struct Multigrid {
     // z = V(r): one V-cycle of Algorithm 1 with y0 = 0 (r, z of length n_u)
     void vcycle(const T* r, T* z, cudaStream_t s);
     void vcycle_direct(cudaStream_t s);   // vin -> vout, kernels only
+    void vcycle_on(const T* b, T* y, cudaStream_t s);   // b -> y, kernels only
     // z = V(r) for FP64 vectors: r rounded to T, the cycle in T, z widened
     void vcycle_widen(const double* r, double* z, cudaStream_t s);
     void bj(const T* r, T* z, cudaStream_t s);
@@ -137,6 +145,12 @@ struct Multigrid {
     void build_coarse_from_band(const std::vector<double>& band, int n, int bw, cudaStream_t s);
 };
 
+// Graph-resident inner PCG (inner_graph.cu).
+struct InnerLoop;
+struct InnerLoopDeleter {
+    void operator()(InnerLoop* p) const;
+};
+
 // FGMRES storage of one problem (FP64): Krylov basis V, flexible basis Z.
 struct Workspace {
     int restart = 0;
@@ -145,12 +159,17 @@ struct Workspace {
     DeviceBuffer cg_r, cg_d, cg_q, cg_z, sc_in;   // FP64 inner PCG of the mixed form
     DeviceBuffer t32, y32;                        // FP32 inner PCG (SIP_PREC_MIXED_F32_INNER)
     HostScalars hs, hs_in;
+    std::unique_ptr<InnerLoop, InnerLoopDeleter> loop;
     bool sinv_ready = false;
     int64_t bytes() const;
 };
 
 int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, double rtol,
                     int maxit, cudaStream_t s);
+// The same inner solve (FP64 iterate; V-cycle in FP32 when mixed, else FP64)
+// as one graph launch with a device-side loop; returns the iteration count.
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, const double* t, double* y,
+                    double rtol, int maxit, cudaStream_t s);
 
 sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 
 #include "sip_solver.h"
@@ -227,7 +228,8 @@ int64_t Multigrid<T>::bytes() const {
                         vin.bytes + vout.bytes + cinv.bytes + ws.bytes + sc.bytes + cg_r.bytes +
                         cg_d.bytes + cg_q.bytes);
     for (const auto& l : h)
-        b += int64_t(l.S.bytes + l.dinv.bytes + l.b.bytes + l.x.bytes + l.r.bytes + l.d.bytes);
+        b += int64_t(l.S.bytes + l.dinv.bytes + l.b.bytes + l.x.bytes + l.r.bytes + l.d.bytes +
+                     l.d2.bytes);
     return b;
 }
 
@@ -488,7 +490,7 @@ void Multigrid<T>::setup(cudaStream_t s) {
             launch_convert<T>(nv * 36, S64[l].as<double>(), Lv.S.template as<T>(), s);
             Lv.dinv.alloc(Lv.n * sizeof(T));
             launch_stencil_dinv<T>(nv, Lv.S.template as<T>(), Lv.dinv.template as<T>(), s);
-            for (DeviceBuffer* b : {&Lv.b, &Lv.x, &Lv.r, &Lv.d}) b->alloc(Lv.n * sizeof(T));
+            for (DeviceBuffer* b : {&Lv.b, &Lv.x, &Lv.r, &Lv.d, &Lv.d2}) b->alloc(Lv.n * sizeof(T));
             SIP_CUDA(cudaStreamSynchronize(s));
         }
         for (int l = 0; l < L; ++l) h[l].lmax = estimate_h(l, s);
@@ -520,6 +522,7 @@ void Multigrid<T>::setup(cudaStream_t s) {
         build_coarse_from_band(band, n, bw, s);
     }
 
+    ++setup_gen;
     // capture the V-cycle (vin -> vout) once
     if (graph) {
         SIP_CUDA(cudaGraphExecDestroy(graph));
@@ -574,20 +577,24 @@ void Multigrid<T>::smooth_h(int l, bool zero, cudaStream_t s) {
     HLevel<T>& L = h[l];
     const Cheb ch(P->desc.cheb_lo * L.lmax, P->desc.cheb_hi * L.lmax);
     T* r = L.r.template as<T>();
-    T* dd = L.d.template as<T>();
+    T* dA = L.d.template as<T>();    // Chebyshev directions, ping-pong
+    T* dB = L.d2.template as<T>();
     T* x = L.x.template as<T>();
     const T* b = L.b.template as<T>();
-    if (zero)
-        launch_axpby<T>(L.n, T(1), b, T(0), r, s);
-    else
-        launch_stencil_apply<T>(L.nvx, L.nvy, L.S.template as<T>(), x, r, T(-1), b, T(1), s);
+    const T* S = L.S.template as<T>();
+    const T* dinv = L.dinv.template as<T>();
+    if (zero) {
+        launch_hcheb_first<T>(L.n, b, dinv, r, dA, x, T(1.0 / ch.theta), s);
+    } else {
+        launch_stencil_apply<T>(L.nvx, L.nvy, S, x, r, T(-1), b, T(1), s);   // r = b - A x
+        launch_jacobi_cheb<T>(L.n, r, dinv, dA, x, T(0), T(1.0 / ch.theta), false, s);
+    }
     double rho = 1.0 / ch.sigma;
-    launch_jacobi_cheb<T>(L.n, r, L.dinv.template as<T>(), dd, x, T(0), T(1.0 / ch.theta), zero, s);
     for (int st = 1; st < P->desc.cheb_steps_h; ++st) {
-        launch_stencil_apply<T>(L.nvx, L.nvy, L.S.template as<T>(), dd, r, T(-1), r, T(1), s);
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
-        launch_jacobi_cheb<T>(L.n, r, L.dinv.template as<T>(), dd, x, T(rn * rho), T(2.0 * rn / ch.delta),
-                              false, s);
+        launch_hcheb_step<T>(L.nvx, L.nvy, S, dinv, r, dA, dB, x, T(rn * rho),
+                             T(2.0 * rn / ch.delta), s);
+        std::swap(dA, dB);
         rho = rn;
     }
 }
@@ -624,8 +631,11 @@ void Multigrid<T>::coarse_solve(const T* b1, T* x1, cudaStream_t s) {
 
 template <typename T>
 void Multigrid<T>::vcycle_direct(cudaStream_t s) {
-    const T* b = vin.template as<T>();
-    T* y = vout.template as<T>();
+    vcycle_on(vin.template as<T>(), vout.template as<T>(), s);
+}
+
+template <typename T>
+void Multigrid<T>::vcycle_on(const T* b, T* y, cudaStream_t s) {
     smooth_p(b, y, true, s);
     launch_apply_sip<T>(N, P->geom, y, pr.template as<T>(), eta_of<T>(P), T(-1), b, T(1), s);  // r = b - A y
     launch_p_restrict<T>(ne, N, pr.template as<T>(), r1.template as<T>(), s);
@@ -837,6 +847,9 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         launch_apply_Bt<double>(P->k, P->geom, v, y + n_u, s);
     };
     int inner_total = 0, inner_max = 0, inner_calls = 0;
+    // the inner PCG runs as one graph launch with a device-side loop unless
+    // the options ask for the host-driven loop (same arithmetic)
+    const bool host_loop = o.inner_loop == 1;
     // z = P^{-1} v
     auto precond = [&](const double* v, double* z) {
         launch_vmul<double>(n_p, v + n_u, W.sinv.as<double>(), z + n_u, s);   // y_p = -S*^{-1} v_p
@@ -849,10 +862,12 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
             its = P->mg32->inner_pcg(W.t32.as<float>(), W.y32.as<float>(), o.inner_rtol,
                                      o.max_inner, s, nullptr);
             launch_cast<float, double>(n_u, W.y32.as<float>(), z, s);
-        } else if (mixed) {
-            its = inner_pcg_mixed(P, W, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s);
+        } else if (host_loop) {
+            its = mixed ? inner_pcg_mixed(P, W, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s)
+                        : P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s,
+                                             nullptr);
         } else {
-            its = P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s, nullptr);
+            its = inner_pcg_graph(P, W, mixed, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s);
         }
         inner_total += its;
         inner_max = std::max(inner_max, its);

@@ -128,6 +128,52 @@ __global__ void k_jacobi_cheb(size_t n, const T* __restrict__ r, const T* __rest
     if (x) x[g] = x_zero ? v : x[g] + v;
 }
 
+// First Chebyshev step from a zero iterate: r = b, d = c2 D^{-1} b, x = d.
+template <typename T>
+__global__ void k_hcheb_first(size_t n, const T* __restrict__ b, const T* __restrict__ dinv,
+                              T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T c2) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const T bv = b[g];
+    const T v = c2 * dinv[g] * bv;
+    r[g] = bv;
+    d[g] = v;
+    x[g] = v;
+}
+
+// One fused Chebyshev / point-Jacobi step on a continuous level:
+// r -= S d_old;  d_new = c1 d_old + c2 D^{-1} r;  x += d_new.
+// d_old is only read (neighbours too), d_new only written: no races.
+template <typename T>
+__global__ void k_hcheb_step(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
+                             T* __restrict__ r, const T* __restrict__ d_old, T* __restrict__ d_new,
+                             T* __restrict__ x, T c1, T c2) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nv = size_t(nvx) * nvy;
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    const T* sv = S + v * 36;
+    T acc = T(0);
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int wy = vy + dy;
+        if (wy < 0 || wy >= nvy) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int wx = vx + dx;
+            if (wx < 0 || wx >= nvx) continue;
+            const int t = (dy + 1) * 3 + (dx + 1);
+            const T* dw = d_old + 2 * (size_t(wy) * nvx + wx);
+            acc += sv[t * 4 + c * 2 + 0] * dw[0] + sv[t * 4 + c * 2 + 1] * dw[1];
+        }
+    }
+    const T rn = r[g] - acc;
+    r[g] = rn;
+    const T dn = c1 * d_old[g] + c2 * dinv[g] * rn;
+    d_new[g] = dn;
+    x[g] += dn;
+}
+
 // fine (2 nxc + 1)^2 <- coarse (nxc + 1)^2 vertex grid, bilinear (add to y)
 template <typename T>
 __global__ void k_ph_add(int nxc, int nyc, const T* __restrict__ xc, T* __restrict__ yf) {
@@ -297,6 +343,19 @@ void launch_jacobi_cheb(size_t n, const T* r, const T* dinv, T* d, T* x, T c1, T
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
+void launch_hcheb_first(size_t n, const T* b, const T* dinv, T* r, T* d, T* x, T c2,
+                        cudaStream_t s) {
+    k_hcheb_first<T><<<nblk(n), 256, 0, s>>>(n, b, dinv, r, d, x, c2);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
+void launch_hcheb_step(int nvx, int nvy, const T* S, const T* dinv, T* r, const T* d_old,
+                       T* d_new, T* x, T c1, T c2, cudaStream_t s) {
+    k_hcheb_step<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new,
+                                                                x, c1, c2);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
 void launch_ph_add(int nxc, int nyc, const T* xc, T* yf, cudaStream_t s) {
     k_ph_add<T><<<nblk(size_t(2 * nxc + 1) * (2 * nyc + 1) * 2), 256, 0, s>>>(nxc, nyc, xc, yf);
     SIP_CHECK_LAUNCH();
@@ -347,6 +406,9 @@ void launch_convert(size_t n, const double* a, T* b, cudaStream_t s) {
     template void launch_jacobi_cheb<T>(size_t, const T*, const T*, T*, T*, T, T, bool,         \
                                         cudaStream_t);                                           \
     template void launch_ph_add<T>(int, int, const T*, T*, cudaStream_t);                       \
+    template void launch_hcheb_first<T>(size_t, const T*, const T*, T*, T*, T*, T, cudaStream_t); \
+    template void launch_hcheb_step<T>(int, int, const T*, const T*, T*, const T*, T*, T*, T, T,  \
+                                       cudaStream_t);                                            \
     template void launch_rh<T>(int, int, const T*, T*, cudaStream_t);                           \
     template void launch_probe_vertices<T>(int, int, int, int, T*, cudaStream_t);               \
     template void launch_extract_stencil<T>(int, int, const T*, T*, cudaStream_t);              \

@@ -1,0 +1,44 @@
+"""Multi-rank bench logic on CPU (gloo, world size 2): each rank solves its
+own instances (replicas, weak scaling); the job time is the slowest rank's
+and the rate counts every rank's solves."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        per_rank_ms = [1000.0, 2500.0][rank]
+        total = bench.max_over_ranks(per_rank_ms, world)
+        out[rank] = (total, bench.whole_job_rate(5, world, total))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_rate_gloo():
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    for rank in range(2):
+        total, rate = out[rank]
+        assert total == 2500.0
+        assert rate == pytest.approx(2 * 5 / 2.5)
+
+
+def test_single_rank_identity():
+    assert bench.max_over_ranks(123.0, 1) == 123.0
+    assert bench.whole_job_rate(4, 1, 2000.0) == pytest.approx(2.0)

@@ -231,3 +231,29 @@ def test_solve_box_inclusion(ctx, precision):
     assert abs(rep["rel_residual"] - res) < 1e-9
     u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
     assert rel(host(u), u_ref) < 1e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,k,nh", [(16, 3, 1), (40, 2, 2)])
+def test_inner_loop_device_equals_host(ctx, precision, nx, k, nh):
+    """The graph-resident inner PCG (device-side loop and stopping test)
+    performs the host-driven loop's arithmetic in the same order: identical
+    iteration counts and bit-identical solutions."""
+    wl = synth.single_box_inclusion(nx, k, 1e4, n_hlevels=nh)
+    eta, rho = materials.rasterise_inclusions(nx, nx, wl.shapes)
+    prob, ref = pair(ctx, nx, nx, k, wl.bc, eta, nh=nh, seed=1, precision=precision)
+    f = dev(sip.rhs_body_force(ref, rho))
+    out = {}
+    for mode in ["host", "device", "host"]:
+        u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+        rep = prob.solve(f, u, p, rtol=1e-8, inner_loop=mode)
+        out.setdefault(mode, []).append((rep, u, p))
+    (rh, uh, ph), (rh2, uh2, ph2) = out["host"]
+    rd, ud, pd_ = out["device"][0]
+    assert torch.equal(uh, uh2) and torch.equal(ph, ph2)   # the solve is deterministic
+    assert (rd["outer_its"], rd["inner_total"], rd["inner_max"]) == \
+        (rh["outer_its"], rh["inner_total"], rh["inner_max"])
+    assert torch.equal(ud, uh) and torch.equal(pd_, ph)
+    assert rd["rel_residual"] == rh["rel_residual"] <= 1e-8
