@@ -75,17 +75,50 @@ def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
     return y, maxit
 
 
+def fcg(apply_A, precond, x, rtol, maxit=200):
+    """Flexible conjugate gradients, FCG(1) (Notay, SIAM J. Sci. Comput. 22,
+    2000), for A y = x from y = 0; stops when ||A y - x|| < rtol ||x||.
+
+    Each new direction is made A-orthogonal to the previous one explicitly,
+    beta = <z, q_prev> / <d_prev, q_prev>, and the step is the exact line
+    minimum along it, alpha = <d, r> / <d, q>.  With a fixed SPD
+    preconditioner this is PCG; it stays convergent when the preconditioner
+    varies a little between applications (a V-cycle in FP32).
+
+    Returns (y, iterations)."""
+    y = np.zeros_like(x)
+    r = x.copy()
+    nx = np.linalg.norm(x)
+    if nx == 0.0:
+        return y, 0
+    d = q = None
+    for it in range(1, maxit + 1):
+        z = precond(r)
+        if d is None:
+            d = z.copy()
+        else:
+            d = z - (z @ q) / (d @ q) * d
+        q = apply_A(d)
+        alpha = (d @ r) / (d @ q)
+        y += alpha * d
+        r -= alpha * q
+        if np.linalg.norm(r) < rtol * nx:
+            return y, it
+    return y, maxit
+
+
 class BlockPreconditioner:
     """Action of the upper block-triangular preconditioner inverse
     (eq. discretestokespc) with the Schur block -S* and A^{-1} -> inner PCG:
         y_p = -S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
 
     def __init__(self, A, B, s_diag, inner_precond, inner_rtol=1e-3,
-                 inner_maxit=200, null_p=None):
+                 inner_maxit=200, null_p=None, inner="pcg"):
         self.A, self.B, self.s = A, B, s_diag
         self.inner_precond = inner_precond
         self.inner_rtol, self.inner_maxit = inner_rtol, inner_maxit
         self.null_p = null_p
+        self.inner = {"pcg": pcg, "fcg": fcg}[inner]
         self.inner_its = []
 
     def __call__(self, x):
@@ -95,8 +128,8 @@ class BlockPreconditioner:
         if self.null_p is not None:
             yp = project_out(yp, self.null_p)
         t = xu - self.B @ yp
-        yu, its = pcg(lambda v: self.A @ v, self.inner_precond, t,
-                      self.inner_rtol, self.inner_maxit)
+        yu, its = self.inner(lambda v: self.A @ v, self.inner_precond, t,
+                             self.inner_rtol, self.inner_maxit)
         self.inner_its.append(its)
         return np.concatenate([yu, yp])
 

@@ -421,3 +421,52 @@ def test_block_preconditioner_uses_negative_schur_block():
     b = np.concatenate([sip.rhs_force(pr, sol.f), np.zeros(B.shape[1])])
     _, its, _ = krylov.fgmres(lambda v: K @ v, Pc, b, 1e-6, null_p=null, n_u=A.shape[0])
     assert its <= 12
+
+
+def _spd(n, seed, cond=1e4):
+    g = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(g.standard_normal((n, n)))
+    ev = np.logspace(0, np.log10(cond), n)
+    return (Q * ev) @ Q.T
+
+
+def test_fcg_equals_pcg_with_fixed_preconditioner():
+    """FCG(1) and PCG coincide in exact arithmetic for a fixed SPD
+    preconditioner (the explicit A-orthogonalisation reproduces PCG's beta):
+    same iteration count, iterates equal to rounding."""
+    A = _spd(40, 1, cond=1e2)
+    dinv = 1.0 / np.diag(A)
+    x = np.random.default_rng(2).standard_normal(40)
+    for m in (1, 3, 8):   # iterates after m steps (before rounding drift)
+        y1, i1 = krylov.pcg(lambda v: A @ v, lambda r: dinv * r, x, 1e-14, maxit=m)
+        y2, i2 = krylov.fcg(lambda v: A @ v, lambda r: dinv * r, x, 1e-14, maxit=m)
+        assert i1 == i2 == m
+        assert np.linalg.norm(y1 - y2) <= 1e-10 * np.linalg.norm(y1)
+    y1, i1 = krylov.pcg(lambda v: A @ v, lambda r: dinv * r, x, 1e-10, maxit=400)
+    y2, i2 = krylov.fcg(lambda v: A @ v, lambda r: dinv * r, x, 1e-10, maxit=400)
+    assert abs(i1 - i2) <= 1
+    assert np.linalg.norm(A @ y2 - x) < 1e-10 * np.linalg.norm(x)
+
+
+def test_fcg_exact_preconditioner_one_step():
+    """With B = A^{-1} the first direction is the exact error: one iteration."""
+    A = _spd(25, 3, cond=1e3)
+    Ainv = np.linalg.inv(A)
+    x = np.random.default_rng(4).standard_normal(25)
+    y, its = krylov.fcg(lambda v: A @ v, lambda r: Ainv @ r, x, 1e-9)
+    assert its == 1
+    assert np.linalg.norm(A @ y - x) < 1e-9 * np.linalg.norm(x)
+
+
+def test_fcg_tolerates_varying_preconditioner():
+    """A preconditioner perturbed by a fresh 5% random diagonal at every
+    application (not a fixed linear operator): FCG(1) still converges to
+    1e-8 within a modest iteration count."""
+    A = _spd(60, 5, cond=1e3)
+    dinv = 1.0 / np.diag(A)
+    g = np.random.default_rng(6)
+    x = g.standard_normal(60)
+    prec = lambda r: dinv * r * (1.0 + 0.05 * g.standard_normal(60))
+    y, its = krylov.fcg(lambda v: A @ v, prec, x, 1e-8, maxit=500)
+    assert np.linalg.norm(A @ y - x) < 1e-8 * np.linalg.norm(x)
+    assert its < 300
