@@ -44,6 +44,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"],
+                    help="form timed by --profile-only")
+    ap.add_argument("--profile-n", type=int, default=128,
+                    help="mesh side of the --profile-only run (same physics)")
+    ap.add_argument("--inner-loop", default="device", choices=["device", "host"],
+                    help="inner PCG loop on the device (one graph launch per inner solve) or "
+                         "driven from the host (for profilers that cannot see kernels inside "
+                         "graphs with conditional nodes)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
@@ -149,7 +157,9 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
     torch.cuda.set_device(dev)
     ctx = api.Context(dev.index)
-    wl = synth.single_box_inclusion()
+    wl = synth.single_box_inclusion(
+        n=args.profile_n, n_hlevels=synth.levels_to_17(args.profile_n)) if args.profile_only \
+        else synth.single_box_inclusion()
     n, k = wl.nx, wl.k
     eta_d, rho_d = ctx.rasterise_inclusions(n, n, wl.shapes)
     eta_h = eta_d.cpu().numpy()
@@ -167,7 +177,8 @@ def run_ours(args, rank, world):
     def step(prob, f, u, p):
         prob.update_eta(eta_d)
         prob.rhs_body_force(rho_d, synth.GRAVITY, f)
-        return prob.solve(f, u, p, rtol=wl.rtol, inner_rtol=args.inner_rtol, max_outer=1000)
+        return prob.solve(f, u, p, rtol=wl.rtol, inner_rtol=args.inner_rtol, max_outer=1000,
+                          inner_loop=args.inner_loop, check=not args.profile_only)
 
     def timed(precision, steps, warmup, clocks=None):
         prob, f, u, p = make(precision)
@@ -193,12 +204,14 @@ def run_ours(args, rank, world):
         return prob, f, u, p, times, reps, clocks_out
 
     clocks = ClockSampler(dev.index)
+    if args.profile_only:   # one form only, for profiler launch lists
+        _, _, _, _, tp, rp, _ = timed(args.profile_precision, args.steps, args.warmup)
+        return {"metric": METRIC, "value": whole_job_rate(args.steps, 1, sum(tp)), "unit": UNIT,
+                "profile_only": True, "precision": args.profile_precision,
+                "solve_report": rp[-1]}
     prob64, f64, u64, p64, t64, r64, clk = timed("fp64", args.steps, args.warmup, clocks)
     total_ms = max_over_ranks(sum(t64), world, dev)
     value = whole_job_rate(args.steps, world, total_ms)
-    if args.profile_only:
-        return {"metric": METRIC, "value": value, "unit": UNIT, "profile_only": True,
-                "solve_report": r64[-1]}
 
     # mixed-precision form on the same workload
     prob32, f32, u32, p32, t32, r32, _ = timed("mixed", args.steps, max(1, args.warmup - 1))
@@ -374,60 +387,81 @@ def cpu_baseline():
                       "SciPy sparse kernels, single-threaded"}
 
 
+def _instance(ctx, wl, precision, seed):
+    """A problem with its load vector and output buffers on the device."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    eta, rho = ctx.rasterise_inclusions(wl.nx, wl.ny, wl.shapes)
+    pr = api.Problem(ctx, wl.nx, wl.ny, wl.k, eta.cpu().numpy(), bc=wl.bc,
+                     n_hlevels=wl.n_hlevels, seed=seed, precision=precision)
+    f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
+    pr.rhs_body_force(rho, synth.GRAVITY, f)
+    u = torch.empty_like(f)
+    p = torch.empty(pr.n_p, dtype=torch.float64, device="cuda")
+    return pr, f, u, p
+
+
 def run_batch(args):
-    """Batched form: independent instances (side in {32, 64, 128, 256}, k in
-    {2..5}, 16 discs, contrast 10^U[2,6]) solved concurrently, mixed precision;
-    the first ``--count`` instances of the seeded list."""
+    """Batched form: the first ``--count`` instances of the seeded list
+    (side in {32, 64, 128, 256}, k in {2..5}, the six inclusions of Sec. 7.3
+    jittered, contrast 10^U[2,5]), mixed precision (FP32 V-cycle, FP64
+    Krylov), solved concurrently on 8 streams; against the plain FP64 form
+    solved one at a time.  Set-up is inside both timed regions."""
     import torch
     from paper_1607_03777_gb300 import api, synth
     ctx = api.Context(0)
     insts = synth.batch_instances(128)[:args.count]
-    probs, fs, us, ps = [], [], [], []
-    for wl in insts:
-        eta, rho = ctx.rasterise_inclusions(wl.nx, wl.ny, wl.shapes)
-        pr = api.Problem(ctx, wl.nx, wl.ny, wl.k, eta.cpu().numpy(), bc=wl.bc,
-                         n_hlevels=wl.n_hlevels, seed=4, precision=wl.precision)
-        f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
-        pr.rhs_body_force(rho, synth.GRAVITY, f)
-        probs.append(pr)
-        fs.append(f)
-        us.append(torch.empty_like(f))
-        ps.append(torch.empty(pr.n_p, dtype=torch.float64, device="cuda"))
-    for pr in probs:
-        pr.setup()
+    mixed = [_instance(ctx, wl, "mixed", 4) for wl in insts]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, reps = api.solve_batch(ctx, probs, fs, us, ps, n_streams=8, rtol=1e-8)
+    for pr, _, _, _ in mixed:
+        pr.setup()
+    st, reps = api.solve_batch(ctx, [m[0] for m in mixed], [m[1] for m in mixed],
+                               [m[2] for m in mixed], [m[3] for m in mixed], n_streams=8,
+                               rtol=1e-8)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     t1 = time.perf_counter()
-    for pr, f, u, p in zip(probs, fs, us, ps):
-        pr.solve(f, u, p, rtol=1e-8)
+    plain = []
+    for wl in insts:
+        pr, f, u, p = _instance(ctx, wl, "fp64", 4)
+        rep = pr.solve(f, u, p, rtol=1e-8, check=False)
+        plain.append((rep, u))
+        del pr
     torch.cuda.synchronize()
     dt1 = time.perf_counter() - t1
+    err = [float(torch.linalg.norm(m[2] - u) / torch.linalg.norm(u)) for m, (_, u) in zip(mixed, plain)]
     return {"metric": "batched_stokes_solves_per_s", "value": len(insts) / dt, "unit": UNIT,
-            "one_at_a_time": len(insts) / dt1, "instances": len(insts), "status": st,
+            "fp64_one_at_a_time": len(insts) / dt1, "instances": len(insts), "status": st,
+            "converged": sum(1 for r in reps if r["status"] == 0),
+            "fp64_converged": sum(1 for r, _ in plain if r["status"] == 0),
             "max_rel_residual": max(r["rel_residual"] for r in reps),
-            "config": {"workload": "batch_instances(seed 4)", "count": len(insts),
-                       "precision": "mixed", "streams": 8}}
+            "u_rel_diff_vs_fp64": {"max": max(err), "median": float(sorted(err)[len(err) // 2])},
+            "config": {"workload": "batch_instances(seed 4): sides 32-256, k 2-5, "
+                                   "jittered six inclusions, contrast 1e2-1e5",
+                       "count": len(insts), "precision": "mixed", "streams": 8, "rtol": 1e-8}}
 
 
 def run_serve(args):
-    """Served form: Poisson arrivals at 200 requests/s (side log-uniform in
-    [32, 512], k in {2..6}, 16 discs, contrast 10^U[0,6]); the first
-    ``--count`` requests of the seeded stream, replayed in real time."""
+    """Served form: the first ``--count`` requests of the seeded Poisson
+    stream (200 requests/s, side log-uniform in [32, 512], k in {2..6}, the
+    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,5]) replayed in real
+    time into the server (mixed precision, 8 slots, HBM admission budget =
+    free HBM - 10%); latency = submit to result on the host.  Against the
+    same requests solved one at a time in plain FP64."""
     import numpy as np
+    import torch
     from paper_1607_03777_gb300 import api, synth
     ctx = api.Context(0)
     arrivals, wls = synth.request_stream()
     arrivals, wls = arrivals[:args.count], wls[:args.count]
-    free = 200 << 30
-    srv = api.Server(ctx, budget_bytes=free, max_slots=8)
-    keep = []
+    free, _ = torch.cuda.mem_get_info()
+    srv = api.Server(ctx, budget_bytes=int(free * 0.9), max_slots=8)
     eta_rho = []
     for wl in wls:   # element materials on the device, copied to the host once
         eta, rho = ctx.rasterise_inclusions(wl.nx, wl.ny, wl.shapes)
         eta_rho.append((eta.cpu().numpy(), rho.cpu().numpy()))
+    keep = []
     t0 = time.perf_counter()
     for i, (ta, wl) in enumerate(zip(arrivals, wls)):
         wait = t0 + ta - time.perf_counter()
@@ -435,18 +469,41 @@ def run_serve(args):
             time.sleep(wait)
         eta, rho = eta_rho[i]
         keep.append(srv.submit(i, wl.nx, wl.ny, wl.k, eta, rho, g=synth.GRAVITY, bc=wl.bc,
-                               n_hlevels=wl.n_hlevels, seed=5, precision=wl.precision))
+                               n_hlevels=wl.n_hlevels, seed=5, precision="mixed"))
     srv.drain()
     dt = time.perf_counter() - t0
     done = srv.poll(cap=max(256, len(wls)))
+    srv.close()
     lat = np.array([r["solve_ms"] for _, r in done])
     ok = sum(1 for _, r in done if r["status"] == 0)
-    srv.close()
+    # baseline: the same requests, one at a time, plain FP64, arrival times ignored
+    t1 = time.perf_counter()
+    base_lat, base_ok, base_u = [], 0, []
+    for wl in wls:
+        ts = time.perf_counter()
+        pr, f, u, p = _instance(ctx, wl, "fp64", 5)
+        rep = pr.solve(f, u, p, rtol=1e-8, check=False)
+        torch.cuda.synchronize()
+        base_lat.append((time.perf_counter() - ts) * 1e3)
+        base_ok += rep["status"] == 0
+        base_u.append(u)
+        del pr
+    dt1 = time.perf_counter() - t1
+    err = []
+    for (st_i, u_srv, _), u64 in zip(keep, base_u):
+        ref = u64.cpu().numpy()
+        err.append(float(np.linalg.norm(u_srv - ref) / np.linalg.norm(ref)))
     return {"metric": "served_stokes_solves_per_s", "value": len(done) / dt, "unit": UNIT,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "requests": len(done), "converged": ok,
-            "config": {"workload": "request_stream(seed 5, 200 req/s)", "count": len(wls),
-                       "slots": 8, "precision": "mixed"}}
+            "u_rel_diff_vs_fp64": {"max": max(err), "median": float(np.median(err))},
+            "fp64_one_at_a_time": {"value": len(wls) / dt1, "unit": UNIT,
+                                   "solve_ms_p50": float(np.percentile(base_lat, 50)),
+                                   "solve_ms_p99": float(np.percentile(base_lat, 99)),
+                                   "converged": int(base_ok)},
+            "config": {"workload": "request_stream(seed 5): 200 req/s, sides 32-512, k 2-6, "
+                                   "jittered six inclusions, contrast 1-1e5",
+                       "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8}}
 
 
 def main():

@@ -117,6 +117,16 @@ sip_status sip_problem_update_eta(sip_problem* prob, const double* eta, void* st
 /* Number of velocity and pressure dofs and the device bytes held. */
 sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p,
                              int64_t* device_bytes);
+/* Kernel schedule in force (no counterpart in the paper).  The first set-up
+ * of a problem of a new (degree, precision, mesh) times the candidate kernels
+ * on the device and keeps the fastest; later problems of the same shape reuse
+ * the choice.  apply[0] / apply[1]: SIP apply kernel of the FP64 / FP32
+ * operator (1 component-split thread pair per element, 2 one thread per
+ * element, 3 shared-memory tile); fused[0] / fused[1]: 1 if a p-level
+ * smoother step is one launch (apply, block-Jacobi and Chebyshev update
+ * together), 0 if it is the apply and block-Jacobi launches.  Either array
+ * may be NULL; the values are those of the last set-up (defaults before). */
+sip_status sip_problem_schedule(const sip_problem* prob, int apply[2], int fused[2]);
 
 /* ---- operators (paper Sec. 4) ------------------------------------------- */
 /* y_u = A x_u: the SIP viscous operator, eq. stiffness_form -- volume term
@@ -197,6 +207,10 @@ typedef struct {
                          *    loop runs on the device (default); 1: host-driven     *
                          *    loop, one read-back per iteration.  Same arithmetic:  *
                          *    both give bit-identical iterates.                     */
+    int inner_krylov;   /* 0: automatic (PCG for SIP_PREC_FP64, flexible CG for the *
+                         *    mixed forms, whose FP32 V-cycle is not exactly the    *
+                         *    same linear operator at every application);          *
+                         *    1: PCG; 2: flexible CG, FCG(1) (device loop only)     */
 } sip_solve_opts;
 
 typedef struct {
@@ -213,7 +227,7 @@ typedef struct {
 } sip_solve_report;
 
 /* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
- * inner_loop 0. */
+ * inner_loop 0, inner_krylov 0. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES with the upper block-triangular preconditioner

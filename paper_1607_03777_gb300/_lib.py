@@ -48,6 +48,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_rtol", ctypes.c_double),
         ("max_inner", ctypes.c_int),
         ("inner_loop", ctypes.c_int),
+        ("inner_krylov", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ SIGNATURES = {
     "sip_problem_create": (ctypes.c_int, [_VP, ctypes.POINTER(ProblemDesc), ctypes.POINTER(_VP)]),
     "sip_problem_destroy": (None, [_VP]),
     "sip_problem_sizes": (ctypes.c_int, [_VP, _I64P, _I64P, _I64P]),
+    "sip_problem_schedule": (ctypes.c_int, [_VP, ctypes.c_void_p, ctypes.c_void_p]),
     "sip_apply_A": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_A_f32": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_B": (ctypes.c_int, [_VP, _VP, _VP, _VP]),

@@ -113,6 +113,14 @@ class Problem:
         except Exception:
             pass
 
+    def schedule(self):
+        """sip_problem_schedule: {"apply": [fp64, fp32], "fused": [fp64, fp32]}
+        (apply: 1 component split, 2 one thread per element, 3 tile)."""
+        apply = (ctypes.c_int * 2)()
+        fused = (ctypes.c_int * 2)()
+        self.ctx.check(self.ctx.lib.sip_problem_schedule(self.handle, apply, fused))
+        return {"apply": list(apply), "fused": list(fused)}
+
     def device_bytes(self):
         n_u, n_p, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self.ctx.check(self.ctx.lib.sip_problem_sizes(self.handle, ctypes.byref(n_u),
@@ -213,11 +221,13 @@ class Problem:
 
     # -- Stokes solve --------------------------------------------------------
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
-              max_inner=200, inner_loop="device", stream=None, check=True):
+              max_inner=200, inner_loop="device", inner_krylov="auto", stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
         ``check``).  ``inner_loop`` = "device" (one graph launch per inner
-        solve) or "host" (host-driven loop)."""
-        o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop)
+        solve) or "host" (host-driven loop); ``inner_krylov`` = "auto",
+        "pcg" or "fcg"."""
+        o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
+                  inner_krylov)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -251,15 +261,18 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
 
 
 INNER_LOOP = {"device": 0, "host": 1}
+INNER_KRYLOV = {"auto": 0, "pcg": 1, "fcg": 2}
 
 
 def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
-          inner_loop="device"):
+          inner_loop="device", inner_krylov="auto"):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
     o.inner_rtol, o.max_inner = inner_rtol, max_inner
     o.inner_loop = INNER_LOOP[inner_loop] if isinstance(inner_loop, str) else int(inner_loop)
+    o.inner_krylov = (INNER_KRYLOV[inner_krylov] if isinstance(inner_krylov, str)
+                      else int(inner_krylov))
     return o
 
 

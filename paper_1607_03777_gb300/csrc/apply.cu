@@ -456,15 +456,29 @@ __global__ void k_rasterise(int nx, int ny, double hx, double hy, const double* 
 }  // namespace
 
 template <typename T>
+int apply_variant(const OpGeom& g) {
+    static const int forced = [] {
+        const char* v = std::getenv("SIP_APPLY_KERNEL");
+        if (!v) return int(APPLY_AUTO);
+        const std::string e(v);
+        return e == "elem2" ? int(APPLY_ELEM2)
+                            : (e == "elem1" ? int(APPLY_ELEM1)
+                                            : (e == "tile" ? int(APPLY_TILE) : int(APPLY_AUTO)));
+    }();
+    return forced != APPLY_AUTO ? forced : g.variant[sizeof(T) == 4 ? 1 : 0];
+}
+template int apply_variant<double>(const OpGeom&);
+template int apply_variant<float>(const OpGeom&);
+
+template <typename T>
 void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                       const T* z, T beta, cudaStream_t s) {
-    // low degrees: one thread per element with compile-time tables
-    // (SIP_APPLY_KERNEL=tile selects the shared-memory tile kernel for all N)
-    static const bool use_elem = [] {
-        const char* v = std::getenv("SIP_APPLY_KERNEL");
-        return !(v && std::string(v) == "tile");
-    }();
-    if (use_elem && launch_apply_sip_elem<T>(N, g, x, y, eta, alpha, z, beta, s)) return;
+    // low degrees: thread-per-element kernels with compile-time tables,
+    // unless the schedule picks the shared-memory tile kernel
+    const int v = apply_variant<T>(g);
+    if (v != APPLY_TILE &&
+        launch_apply_sip_elem<T>(N, g, x, y, eta, alpha, z, beta, v != APPLY_ELEM1, s))
+        return;
     switch (N) {
         case 2: apply_sip_n<2, T>(g, x, y, eta, alpha, z, beta, s); break;
         case 3: apply_sip_n<3, T>(g, x, y, eta, alpha, z, beta, s); break;

@@ -16,6 +16,7 @@
 // from own and neighbour traces, spread to the outputs, one write per mode.
 #include "sip_face.cuh"
 #include "sip_internal.h"
+#include "sip_parity.cuh"
 
 namespace sip {
 
@@ -74,6 +75,7 @@ struct ElemArgs {
     FaceGeo<T> fgx, fgy;
     int bc[4];
     T pen_x, pen_y;
+    T* r1;   // component-split kernel: write only the Q^2_1 modes (i, j < 2) here
 };
 
 // Traces of one element on face F (0 left, 1 right, 2 bottom, 3 top):
@@ -393,10 +395,11 @@ __device__ __forceinline__ void load_elem(const T* __restrict__ src, T (&u)[2][N
     }
 }
 
-// dst[j][i] = alpha y[j][i] (+ beta zz[j][i]) over one component block
+// dst[j][i] = alpha y[j][i] (+ beta zz[j][i]) over one component block;
+// the same values also go to sres (shared memory) when it is not null
 template <int N, typename T, bool VEC>
 __device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
-                                           const T (&y)[N][N]) {
+                                           const T (&y)[N][N], T* sres) {
     if constexpr (VEC && vec_ok<N, T>()) {
         using V = Vec16<T>;
         typename V::type* d = reinterpret_cast<typename V::type*>(dst);
@@ -418,6 +421,10 @@ __device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
                 }
             }
             d[k] = V::make(v);
+            if (sres) {
+#pragma unroll
+                for (int t = 0; t < V::n; ++t) sres[k * V::n + t] = v[t];
+            }
         }
     } else {
 #pragma unroll
@@ -427,6 +434,7 @@ __device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
                 T v = alpha * y[j][i];
                 if (zz) v += beta * zz[j * N + i];
                 dst[j * N + i] = v;
+                if (sres) sres[j * N + i] = v;
             }
     }
 }
@@ -504,7 +512,8 @@ __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)
 template <int N, typename T, int C, bool VEC>
 __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int ey, int ex0, int ey0,
                                               int tx, int ty, T etaK, T (*s_tr)[4][4 * N],
-                                              T (*s_halo)[4 * N], int el, T (&y)[N][N]) {
+                                              T (*s_halo)[4 * N], int el, T (&y)[N][N],
+                                              T* sres = nullptr) {
     constexpr int NB = 2 * N * N;
     const int nx = a.nx, ny = a.ny;
     T Dm[N * N];
@@ -570,63 +579,196 @@ __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int 
             }
         }
     }
-    T* dst = a.y + (size_t(ey) * nx + ex) * NB + C * N * N;
     const T* zz = a.z ? a.z + (size_t(ey) * nx + ex) * NB + C * N * N : nullptr;
-    store_comp<N, T, VEC>(dst, zz, a.alpha, a.beta, y);
+    if (a.r1) {   // residual restricted to the Q^2_1 modes (p-transfer R = P^T)
+        T* d1 = a.r1 + (size_t(ey) * nx + ex) * 8 + C * 4;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                T v = a.alpha * y[j][i];
+                if (zz) v += a.beta * zz[j * N + i];
+                d1[j * 2 + i] = v;
+            }
+        return;
+    }
+    T* dst = a.y + (size_t(ey) * nx + ex) * NB + C * N * N;
+    store_comp<N, T, VEC>(dst, zz, a.alpha, a.beta, y, sres);
 }
 
-template <int N, typename T, bool VEC>
-__global__ void __launch_bounds__(T2THREADS) k_apply_elem2(const ElemArgs<T> a) {
-    constexpr int TR = 4 * N;
-    constexpr int NB = 2 * N * N;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);   // [TX*TY2][4][TR]
-    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ty = warp / 2, c = warp % 2;    // tile row, velocity component (warp-uniform)
-    const int tx = lane;
-    const int el = ty * TX + tx;
-    const int ex0 = blockIdx.x * TX, ey0 = blockIdx.y * TY2;
-    const int ex = ex0 + tx, ey = ey0 + ty;
-    const int nx = a.nx, ny = a.ny;
-    const bool active = ex < nx && ey < ny;
+// Thread roles of the component-split tile: warps 2r and 2r+1 serve
+// velocity components 0 and 1 of the 32 elements of tile row r.
+struct Elem2Ids {
+    int warp, lane, ty, c, tx, el, ex0, ey0, ex, ey;
+    bool active;
+    __device__ Elem2Ids(int nx, int ny) {
+        warp = threadIdx.x / 32;
+        lane = threadIdx.x % 32;
+        ty = warp / 2;
+        c = warp % 2;
+        tx = lane;
+        el = ty * TX + tx;
+        ex0 = blockIdx.x * TX;
+        ey0 = blockIdx.y * TY2;
+        ex = ex0 + tx;
+        ey = ey0 + ty;
+        active = ex < nx && ey < ny;
+    }
+};
 
-    // ---- phase A: halo traces (both components of the face touching the tile)
+// Phase A of the component-split tile: halo traces (both components of the
+// face touching the tile) and, for an active thread, its component's own
+// traces and volume terms (into y).  Ends with the CTA barrier.
+template <int N, typename T, bool VEC>
+__device__ __forceinline__ void elem2_phase_a_all(const ElemArgs<T>& a, const Elem2Ids& id,
+                                                  T (*s_tr)[4][4 * N], T (*s_halo)[4 * N],
+                                                  T (&y)[N][N], T& etaK) {
+    constexpr int NB = 2 * N * N;
+    const int nx = a.nx, ny = a.ny;
     for (int h = threadIdx.x; h < NHALO2; h += T2THREADS) {
         int hx, hy, F;
-        if (h < TX) { hx = ex0 + h; hy = ey0 - 1; F = 3; }
-        else if (h < 2 * TX) { hx = ex0 + h - TX; hy = ey0 + TY2; F = 2; }
-        else if (h < 2 * TX + TY2) { hx = ex0 - 1; hy = ey0 + h - 2 * TX; F = 1; }
-        else { hx = ex0 + TX; hy = ey0 + h - 2 * TX - TY2; F = 0; }
+        if (h < TX) { hx = id.ex0 + h; hy = id.ey0 - 1; F = 3; }
+        else if (h < 2 * TX) { hx = id.ex0 + h - TX; hy = id.ey0 + TY2; F = 2; }
+        else if (h < 2 * TX + TY2) { hx = id.ex0 - 1; hy = id.ey0 + h - 2 * TX; F = 1; }
+        else { hx = id.ex0 + TX; hy = id.ey0 + h - 2 * TX - TY2; F = 0; }
         if (hx >= 0 && hx < nx && hy >= 0 && hy < ny) {
             T uh[2][N][N];
             load_elem<N, T, VEC>(a.x + (size_t(hy) * nx + hx) * NB, uh);
             face_traces<N, T>(uh, F, F < 2 ? a.two_over_hx : a.two_over_hy, s_halo[h]);
         }
     }
-    // ---- phase A: own traces and volume terms of this thread's component
-    T y[N][N];
-    T etaK = T(0);
-    if (active) {
+    etaK = T(0);
+    if (id.active) {
         T u[2][N][N];
-        load_elem<N, T, VEC>(a.x + (size_t(ey) * nx + ex) * NB, u);
-        etaK = a.eta[size_t(ey) * nx + ex];
-        if (c == 0)
-            elem2_phase_a<N, T, 0>(a, u, etaK, s_tr[el], y);
+        load_elem<N, T, VEC>(a.x + (size_t(id.ey) * nx + id.ex) * NB, u);
+        etaK = a.eta[size_t(id.ey) * nx + id.ex];
+        if (id.c == 0)
+            elem2_phase_a<N, T, 0>(a, u, etaK, s_tr[id.el], y);
         else
-            elem2_phase_a<N, T, 1>(a, u, etaK, s_tr[el], y);
+            elem2_phase_a<N, T, 1>(a, u, etaK, s_tr[id.el], y);
     }
     __syncthreads();
-    if (!active) return;
-    if (c == 0)
-        elem2_phase_b<N, T, 0, VEC>(a, ex, ey, ex0, ey0, tx, ty, etaK, s_tr, s_halo, el, y);
-    else
-        elem2_phase_b<N, T, 1, VEC>(a, ex, ey, ex0, ey0, tx, ty, etaK, s_tr, s_halo, el, y);
 }
 
-template <int N, typename T>
-void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z, T beta,
-                  cudaStream_t s) {
+template <int N, typename T, bool VEC>
+__global__ void __launch_bounds__(T2THREADS) k_apply_elem2(const ElemArgs<T> a) {
+    constexpr int TR = 4 * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);   // [TX*TY2][4][TR]
+    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
+    const Elem2Ids id(a.nx, a.ny);
+    T y[N][N];
+    T etaK;
+    elem2_phase_a_all<N, T, VEC>(a, id, s_tr, s_halo, y, etaK);
+    if (!id.active) return;
+    if (id.c == 0)
+        elem2_phase_b<N, T, 0, VEC>(a, id.ex, id.ey, id.ex0, id.ey0, id.tx, id.ty, etaK, s_tr,
+                                    s_halo, id.el, y);
+    else
+        elem2_phase_b<N, T, 1, VEC>(a, id.ex, id.ey, id.ex0, id.ey0, id.tx, id.ty, etaK, s_tr,
+                                    s_halo, id.el, y);
+}
+
+// Element-block Jacobi / Chebyshev update of the fused smoother step.
+template <typename T>
+struct BJArgs {
+    const int* emap;        // class (< 0: -(mask+1)) or unique slot of each element
+    const T* cls_inv;       // reference inverses by boundary mask, scaled by 1/eta_K
+    const int* cls_sym;     // their reflection-symmetry types (null: dense)
+    const T* uniq_inv;      // inverses of the unique blocks
+    const T* eta_inv;       // 1/eta_K
+    const T* d_old;         // previous direction (null when c1 == 0 and !pend)
+    T* d_new;               // new direction
+    T* yv;                  // iterate to update (null: no update)
+    T c1, c2;
+    int pend;               // add d_old to the iterate too (its update was deferred)
+};
+
+// One p-level Chebyshev step of the element-block Jacobi smoother (Sec. 6)
+// in one launch:
+//   r = z - A x,  d_new = c1 d_old + c2 M^{-1} r,  yv += [pend] d_old + d_new.
+// The operator part is k_apply_elem2's (alpha = -1, beta = 1, output r; z
+// may alias r); the residual blocks of the tile are also kept in shared
+// memory, where each warp then applies the block inverses of its elements
+// (lane = row, columns of the symmetric inverse read coalesced).  x must not
+// alias d_new or yv: other tiles read x while this one writes.
+template <int N, typename T, bool VEC>
+__global__ void __launch_bounds__(T2THREADS) k_cheb_elem2(const ElemArgs<T> a, const BJArgs<T> b) {
+    constexpr int TR = 4 * N;
+    constexpr int NB = 2 * N * N;
+    static_assert(NB <= 32, "one warp lane per block row");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);
+    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
+    T* s_res = reinterpret_cast<T*>(smem_raw + sizeof(T) * (TX * TY2 * 4 + NHALO2) * TR);
+    const Elem2Ids id(a.nx, a.ny);
+    T y[N][N];
+    T etaK;
+    elem2_phase_a_all<N, T, VEC>(a, id, s_tr, s_halo, y, etaK);
+    if (id.active) {
+        T* sres = s_res + id.el * NB + id.c * N * N;
+        if (id.c == 0)
+            elem2_phase_b<N, T, 0, VEC>(a, id.ex, id.ey, id.ex0, id.ey0, id.tx, id.ty, etaK, s_tr,
+                                        s_halo, id.el, y, sres);
+        else
+            elem2_phase_b<N, T, 1, VEC>(a, id.ex, id.ey, id.ex0, id.ey0, id.tx, id.ty, etaK, s_tr,
+                                        s_halo, id.el, y, sres);
+    }
+    __syncthreads();
+    // block inverses: warp w takes elements w, w + NW, ...; ILP of them at a
+    // time so that their independent column loads overlap
+    constexpr int NW = T2THREADS / 32;
+    constexpr int PER = TX * TY2 / NW;
+    constexpr int ILP = 4;
+    static_assert(PER % ILP == 0, "whole rounds of ILP elements per warp");
+    const int row = id.lane;
+#pragma unroll 1
+    for (int base = 0; base < PER; base += ILP) {
+        const T* Mk[ILP];
+        T sc[ILP];
+        size_t ek[ILP];
+        int e2k[ILP];
+        int symk[ILP];
+        bool ok[ILP];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            const int e2 = id.warp + NW * (base + k);
+            const int gx = id.ex0 + e2 % TX, gy = id.ey0 + e2 / TX;
+            e2k[k] = e2;
+            ok[k] = gx < a.nx && gy < a.ny;
+            ek[k] = ok[k] ? size_t(gy) * a.nx + gx : 0;
+            const int m = ok[k] ? b.emap[ek[k]] : -1;   // outside: any valid matrix, unused
+            if (m < 0) {
+                Mk[k] = b.cls_inv + size_t(-m - 1) * NB * NB;
+                sc[k] = ok[k] ? b.eta_inv[ek[k]] : T(0);
+                symk[k] = b.cls_sym ? b.cls_sym[-m - 1] : 0;
+            } else {
+                Mk[k] = b.uniq_inv + size_t(m) * NB * NB;
+                sc[k] = T(1);
+                symk[k] = 0;
+            }
+        }
+        if (row < NB) {
+            T acc[ILP];
+#pragma unroll
+            for (int k = 0; k < ILP; ++k)
+                acc[k] = block_row_apply<N, T>(Mk[k], s_res + e2k[k] * NB, row, symk[k]);
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) {
+                if (!ok[k]) continue;
+                const size_t o = ek[k] * NB + row;
+                T v = b.c2 * sc[k] * acc[k];
+                if (b.c1 != T(0)) v += b.c1 * b.d_old[o];
+                b.d_new[o] = v;
+                if (b.yv) b.yv[o] += b.pend ? b.d_old[o] + v : v;
+            }
+        }
+    }
+}
+
+template <typename T>
+ElemArgs<T> make_elem_args(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z,
+                           T beta) {
     ElemArgs<T> a;
     a.x = x;
     a.y = y;
@@ -647,11 +789,16 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
     for (int i = 0; i < 4; ++i) a.bc[i] = g.bc[i];
     a.pen_x = T(g.pen_x);
     a.pen_y = T(g.pen_y);
-    // two threads per element (component split) unless SIP_APPLY_KERNEL=elem1
-    static const bool split = [] {
-        const char* v = std::getenv("SIP_APPLY_KERNEL");
-        return !(v && std::string(v) == "elem1");
-    }();
+    a.r1 = nullptr;
+    return a;
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <int N, typename T>
+void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z, T beta,
+                  bool split, cudaStream_t s) {
+    const ElemArgs<T> a = make_elem_args<T>(g, x, y, eta, alpha, z, beta);
     if (split) {
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
         const size_t smem = sizeof(T) * (size_t(TX) * TY2 * 4 + NHALO2) * 4 * N;
@@ -663,8 +810,7 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
             return true;
         }();
         (void)attr2;
-        const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-        if (vec_ok<N, T>() && al16(x) && al16(y) && (z == nullptr || al16(z)))
+        if (vec_ok<N, T>() && aligned16(x) && aligned16(y) && (z == nullptr || aligned16(z)))
             k_apply_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a);
         else
             k_apply_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a);
@@ -683,22 +829,119 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
     SIP_CHECK_LAUNCH();
 }
 
+template <int N, typename T>
+void residual_restrict_n(const OpGeom& g, const T* y, const T* b, const T* eta, T* r1,
+                         cudaStream_t s) {
+    ElemArgs<T> a = make_elem_args<T>(g, y, nullptr, eta, T(-1), b, T(1));
+    a.r1 = r1;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
+    const size_t smem = sizeof(T) * (size_t(TX) * TY2 * 4 + NHALO2) * 4 * N;
+    static const bool attr = [smem] {   // once per process, thread-safe
+        SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        return true;
+    }();
+    (void)attr;
+    if (vec_ok<N, T>() && aligned16(y) && aligned16(b))
+        k_apply_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a);
+    else
+        k_apply_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a);
+    SIP_CHECK_LAUNCH();
+}
+
+template <int N, typename T>
+void cheb_elem_n(const OpGeom& g, const T* x, const T* z, T* r, const T* eta, const BJArgs<T>& b,
+                 cudaStream_t s) {
+    const ElemArgs<T> a = make_elem_args<T>(g, x, r, eta, T(-1), z, T(1));
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
+    const size_t smem = sizeof(T) * ((size_t(TX) * TY2 * 4 + NHALO2) * 4 * N +
+                                     size_t(TX) * TY2 * 2 * N * N);
+    static const bool attr = [smem] {   // once per process, thread-safe
+        SIP_CUDA(cudaFuncSetAttribute(k_cheb_elem2<N, T, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        SIP_CUDA(cudaFuncSetAttribute(k_cheb_elem2<N, T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        return true;
+    }();
+    (void)attr;
+    if (vec_ok<N, T>() && aligned16(x) && aligned16(r) && aligned16(z))
+        k_cheb_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a, b);
+    else
+        k_cheb_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a, b);
+    SIP_CHECK_LAUNCH();
+}
+
 }  // namespace
+
+bool cheb_elem_available(int N) { return N >= 2 && N <= 4; }
+
+template <typename T>
+bool launch_residual_restrict_elem(int N, const OpGeom& g, const T* y, const T* b, const T* eta,
+                                   T* r1, cudaStream_t s) {
+    if (!cheb_elem_available(N)) return false;
+    switch (N) {
+        case 2: residual_restrict_n<2, T>(g, y, b, eta, r1, s); break;
+        case 3: residual_restrict_n<3, T>(g, y, b, eta, r1, s); break;
+        default: residual_restrict_n<4, T>(g, y, b, eta, r1, s); break;
+    }
+    return true;
+}
+template bool launch_residual_restrict_elem<double>(int, const OpGeom&, const double*,
+                                                    const double*, const double*, double*,
+                                                    cudaStream_t);
+template bool launch_residual_restrict_elem<float>(int, const OpGeom&, const float*, const float*,
+                                                   const float*, float*, cudaStream_t);
+
+template <typename T>
+bool launch_cheb_elem(int N, const OpGeom& g, const T* x, const T* z, T* r, const T* eta,
+                      const int* emap, const T* cls_inv, const int* cls_sym, const T* uniq_inv,
+                      const T* eta_inv, const T* d_old, T* d_new, T* yv, T c1, T c2, bool pend,
+                      cudaStream_t s) {
+    if (!cheb_elem_available(N)) return false;
+    BJArgs<T> b;
+    b.emap = emap;
+    b.cls_inv = cls_inv;
+    b.cls_sym = cls_sym;
+    b.uniq_inv = uniq_inv;
+    b.eta_inv = eta_inv;
+    b.d_old = d_old;
+    b.d_new = d_new;
+    b.yv = yv;
+    b.c1 = c1;
+    b.c2 = c2;
+    b.pend = pend ? 1 : 0;
+    switch (N) {
+        case 2: cheb_elem_n<2, T>(g, x, z, r, eta, b, s); break;
+        case 3: cheb_elem_n<3, T>(g, x, z, r, eta, b, s); break;
+        default: cheb_elem_n<4, T>(g, x, z, r, eta, b, s); break;
+    }
+    return true;
+}
+template bool launch_cheb_elem<double>(int, const OpGeom&, const double*, const double*, double*,
+                                       const double*, const int*, const double*, const int*,
+                                       const double*, const double*, const double*, double*,
+                                       double*, double, double, bool, cudaStream_t);
+template bool launch_cheb_elem<float>(int, const OpGeom&, const float*, const float*, float*,
+                                      const float*, const int*, const float*, const int*,
+                                      const float*, const float*, const float*, float*, float*,
+                                      float, float, bool, cudaStream_t);
 
 template <typename T>
 bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
-                           const T* z, T beta, cudaStream_t s) {
+                           const T* z, T beta, bool split, cudaStream_t s) {
     switch (N) {
-        case 2: apply_elem_n<2, T>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 3: apply_elem_n<3, T>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 4: apply_elem_n<4, T>(g, x, y, eta, alpha, z, beta, s); return true;
+        case 2: apply_elem_n<2, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
+        case 3: apply_elem_n<3, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
+        case 4: apply_elem_n<4, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
         default: return false;
     }
 }
 template bool launch_apply_sip_elem<double>(int, const OpGeom&, const double*, double*,
-                                            const double*, double, const double*, double,
+                                            const double*, double, const double*, double, bool,
                                             cudaStream_t);
 template bool launch_apply_sip_elem<float>(int, const OpGeom&, const float*, float*, const float*,
-                                           float, const float*, float, cudaStream_t);
+                                           float, const float*, float, bool, cudaStream_t);
 
 }  // namespace sip

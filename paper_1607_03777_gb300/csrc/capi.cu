@@ -161,6 +161,7 @@ void sip_problem_destroy(sip_problem* p) {
     // used: wait for the device before returning them to the pool
     cudaSetDevice(p->ctx->device);
     cudaDeviceSynchronize();
+    sip::ReleaseOnLegacyScope legacy;   // its allocation streams may be destroyed by now
     delete p;
 }
 
@@ -170,6 +171,19 @@ sip_status sip_problem_sizes(const sip_problem* p, int64_t* n_u, int64_t* n_p,
     if (n_u) *n_u = p->n_u;
     if (n_p) *n_p = p->n_p;
     if (device_bytes) *device_bytes = p->device_bytes();
+    return SIP_OK;
+}
+
+sip_status sip_problem_schedule(const sip_problem* p, int apply[2], int fused[2]) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    for (int t = 0; t < 2; ++t) {
+        if (apply) {
+            const int v = p->geom.variant[t];
+            apply[t] = v != sip::APPLY_AUTO ? v : (p->n <= 4 ? int(sip::APPLY_ELEM2)
+                                                             : int(sip::APPLY_TILE));
+        }
+        if (fused) fused[t] = (p->n <= 4 && p->geom.fused[t]) ? 1 : 0;
+    }
     return SIP_OK;
 }
 
@@ -455,6 +469,7 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->inner_rtol = 1e-3;
     o->max_inner = 200;
     o->inner_loop = 0;
+    o->inner_krylov = 0;
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -469,7 +484,8 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
         sip::require(std::isfinite(o.rtol) && o.rtol > 0 && o.max_outer >= 1 && o.restart >= 1 &&
                          o.restart <= 250 &&
                          std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1 &&
-                         (o.inner_loop == 0 || o.inner_loop == 1),
+                         (o.inner_loop == 0 || o.inner_loop == 1) && o.inner_krylov >= 0 &&
+                         o.inner_krylov <= 2 && !(o.inner_loop == 1 && o.inner_krylov == 2),
                      "bad solve options");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));

@@ -28,7 +28,7 @@ constexpr int kRT = 256;
 struct PcgState {
     const double* t;   // right-hand side (set before each launch)
     double* y;         // iterate (set before each launch)
-    double nt, rz, alpha, beta, rr;
+    double nt, rz, alpha, beta, rr, dq;
     int it, status;    // status 0 ok, 1 non-finite
 };
 
@@ -158,6 +158,65 @@ __global__ void __launch_bounds__(kRT) k_update_rr(size_t n, const double* __res
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// ---- flexible CG, FCG(1) (Notay, SIAM J. Sci. Comput. 22, 2000): the
+// direction is A-orthogonalised against the previous one explicitly,
+//   beta = <z_{k+1}, q_k> / <d_k, q_k>,  d_{k+1} = z_{k+1} - beta d_k,
+//   alpha = <d_k, r_k> / <d_k, q_k>,
+// which equals PCG in exact arithmetic with a fixed SPD preconditioner and
+// tolerates a preconditioner that varies slightly between applications
+// (the FP32 V-cycle of the mixed form).
+
+// partial sums of z.q, with z = widen(zs) stored into zd when zd != nullptr
+template <typename Tz>
+__global__ void __launch_bounds__(kRT) k_dot_zq(size_t n, const double* __restrict__ q,
+                                                const Tz* __restrict__ zs, double* zd,
+                                                double* partial) {
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        const double z = double(zs[g]);
+        if (zd) zd[g] = z;
+        acc += z * q[g];
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// stored as -beta so that k_dir (d = z + beta d) forms z - beta d
+__global__ void __launch_bounds__(kRT) k_beta_fcg_final(PcgState* st, const double* partial) {
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) st->beta = st->it == 0 ? 0.0 : -(s / st->dq);
+}
+
+// partial sums of d.q (partial[0..kRB)) and d.r (partial[kRB..2kRB))
+__global__ void __launch_bounds__(kRT) k_dot_dq_dr(size_t n, const double* __restrict__ d,
+                                                   const double* __restrict__ q,
+                                                   const double* __restrict__ r,
+                                                   double* partial) {
+    double a1 = 0.0, a2 = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        const double dv = d[g];
+        a1 += dv * q[g];
+        a2 += dv * r[g];
+    }
+    a1 = block_sum(a1);
+    a2 = block_sum(a2);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = a1;
+        partial[kRB + blockIdx.x] = a2;
+    }
+}
+
+__global__ void __launch_bounds__(kRT) k_alpha_fcg_final(PcgState* st, const double* partial) {
+    const double dq = final_sum(partial);
+    const double dr = final_sum(partial + kRB);
+    if (threadIdx.x == 0) {
+        st->dq = dq;
+        st->alpha = dr / dq;
+    }
+}
+
 // End of one pass: counter, stopping test, loop condition.
 __global__ void __launch_bounds__(kRT) k_ctl_final(PcgState* st, const double* partial,
                                                    double rtol, int maxit,
@@ -185,6 +244,7 @@ struct InnerLoop {
     DeviceBuffer state, partial;
     HostScalars hs;             // pinned read-back of the state
     bool mixed = false;
+    bool flexible = false;
     double rtol = -1.0;
     int maxit = -1;
     int gen = -1;
@@ -212,29 +272,46 @@ void capture_body(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphCondition
     double* z = W.cg_z.as<double>();
     double* part = L.partial.as<double>();
     PcgState* st = L.state.as<PcgState>();
+    // z = V(r) with the scalar of the direction update: r.z (PCG) or z.q (FCG)
     if (L.mixed) {
         Multigrid<float>& mg = *P->mg32;
         float* vin = mg.vin.as<float>();
         float* vout = mg.vout.as<float>();
         launch_cast<double, float>(n_u, r, vin, cs);
         mg.vcycle_on(vin, vout, cs);
-        k_dot_rz<float><<<kRB, kRT, 0, cs>>>(n_u, r, vout, z, part);
+        if (L.flexible)
+            k_dot_zq<float><<<kRB, kRT, 0, cs>>>(n_u, q, vout, z, part);
+        else
+            k_dot_rz<float><<<kRB, kRT, 0, cs>>>(n_u, r, vout, z, part);
         SIP_CHECK_LAUNCH();
     } else {
         Multigrid<double>& mg = *P->mg64;
         mg.vcycle_on(r, z, cs);
-        k_dot_rz<double><<<kRB, kRT, 0, cs>>>(n_u, r, z, nullptr, part);
+        if (L.flexible)
+            k_dot_zq<double><<<kRB, kRT, 0, cs>>>(n_u, q, z, nullptr, part);
+        else
+            k_dot_rz<double><<<kRB, kRT, 0, cs>>>(n_u, r, z, nullptr, part);
         SIP_CHECK_LAUNCH();
     }
-    k_beta_final<<<1, kRT, 0, cs>>>(st, part);
+    if (L.flexible)
+        k_beta_fcg_final<<<1, kRT, 0, cs>>>(st, part);
+    else
+        k_beta_final<<<1, kRT, 0, cs>>>(st, part);
     SIP_CHECK_LAUNCH();
     k_dir<<<nblk(n_u), 256, 0, cs>>>(n_u, z, d, st);
     SIP_CHECK_LAUNCH();
     launch_apply_sip<double>(P->n, P->geom, d, q, P->eta_d.as<double>(), 1.0, nullptr, 0.0, cs);
-    k_dot<<<kRB, kRT, 0, cs>>>(n_u, d, q, part);
-    SIP_CHECK_LAUNCH();
-    k_alpha_final<<<1, kRT, 0, cs>>>(st, part);
-    SIP_CHECK_LAUNCH();
+    if (L.flexible) {
+        k_dot_dq_dr<<<kRB, kRT, 0, cs>>>(n_u, d, q, r, part);
+        SIP_CHECK_LAUNCH();
+        k_alpha_fcg_final<<<1, kRT, 0, cs>>>(st, part);
+        SIP_CHECK_LAUNCH();
+    } else {
+        k_dot<<<kRB, kRT, 0, cs>>>(n_u, d, q, part);
+        SIP_CHECK_LAUNCH();
+        k_alpha_final<<<1, kRT, 0, cs>>>(st, part);
+        SIP_CHECK_LAUNCH();
+    }
     k_update_rr<<<kRB, kRT, 0, cs>>>(n_u, d, q, r, st, part);
     SIP_CHECK_LAUNCH();
     k_ctl_final<<<1, kRT, 0, cs>>>(st, part, L.rtol, L.maxit, h);
@@ -312,8 +389,8 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
 
 }  // namespace
 
-int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, const double* t, double* y,
-                    double rtol, int maxit, cudaStream_t s) {
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, const double* t,
+                    double* y, double rtol, int maxit, cudaStream_t s) {
     maxit = std::max(1, std::min(maxit, 100000));
     const size_t n_u = size_t(P->n_u);
     for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
@@ -321,13 +398,14 @@ int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, const double* t, d
     InnerLoop& L = *W.loop;
     static_assert(sizeof(PcgState) <= 256 * sizeof(double), "state fits the pinned block");
     L.state.alloc(sizeof(PcgState));
-    L.partial.alloc(kRB * sizeof(double));
+    L.partial.alloc(2 * kRB * sizeof(double));
     const void* mg = mixed ? static_cast<const void*>(P->mg32.get())
                            : static_cast<const void*>(P->mg64.get());
     const int gen = mixed ? P->mg32->setup_gen : P->mg64->setup_gen;
-    if (!L.exec || L.mixed != mixed || L.rtol != rtol || L.maxit != maxit || L.gen != gen ||
-        L.mg != mg) {
+    if (!L.exec || L.mixed != mixed || L.flexible != flexible || L.rtol != rtol ||
+        L.maxit != maxit || L.gen != gen || L.mg != mg) {
         L.mixed = mixed;
+        L.flexible = flexible;
         L.rtol = rtol;
         L.maxit = maxit;
         L.gen = gen;

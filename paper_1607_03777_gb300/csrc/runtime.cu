@@ -12,6 +12,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 
@@ -42,7 +43,7 @@ int64_t estimate_problem_bytes(const sip_problem_desc& d, int restart) {
     // multigrid: block inverses (class + unique worst case is bounded by the
     // elements with a stiffer neighbour; count them all), work vectors
     b += 16 * nb * nb * w + ne * nb * nb * w / 4;
-    b += 10 * n_u * w + 16 * ne * w + ne * 8;
+    b += 11 * n_u * w + 16 * ne * w + ne * 8;
     int64_t nv = int64_t(d.nx + 1) * (d.ny + 1);
     for (int l = 0; l <= d.n_hlevels; ++l) {
         b += nv * (36 + 8) * w + nv * 36 * 8;             // stencils (+ FP64 set-up copy)
@@ -50,6 +51,7 @@ int64_t estimate_problem_bytes(const sip_problem_desc& d, int restart) {
     }
     b += int64_t(d.eig_iters + 1) * n_u * 8;               // Arnoldi basis of the set-up
     b += int64_t(2 * restart + 1) * nk * 8 + 8 * nk * 8;  // FGMRES V, Z and work vectors
+    b += 4 * n_u * 8;                                      // FP64 inner Krylov vectors
     return b;
 }
 
@@ -68,14 +70,38 @@ struct Job {
     std::string err;
 };
 
+// Worker streams of batched solves, per device and worker slot, created once
+// and never destroyed: buffers a batched solve allocates belong to the
+// caller's problem and are ordered on these streams for the problem's life.
+cudaStream_t batch_stream(int device, int slot) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, cudaStream_t> streams;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find({device, slot});
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(SIP_ERR_CUDA, "batch worker stream creation failed");
+    }
+    streams[{device, slot}] = s;
+    return s;
+}
+
 void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n_streams) {
     std::atomic<size_t> next{0};
-    auto worker = [&]() {
+    auto worker = [&](int slot) {
         cudaSetDevice(device);
         cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            s = nullptr;
+        try {
+            s = batch_stream(device, slot);
+        } catch (const Error& e) {
+            for (size_t i = next++; i < jobs.size(); i = next++) {
+                jobs[i].st = e.status;
+                jobs[i].err = e.what();
+                if (jobs[i].rep) jobs[i].rep->status = e.status;
+            }
+            return;
         }
         sip::AllocStreamScope scope(s);
         for (size_t i = next++; i < jobs.size(); i = next++) {
@@ -93,11 +119,11 @@ void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n
                 if (j.rep) j.rep->status = SIP_ERR_CUDA;
             }
         }
-        if (s) cudaStreamDestroy(s);
+        cudaStreamSynchronize(s);
     };
     std::vector<std::thread> pool;
     const int nt = std::max(1, std::min<int>(n_streams, int(jobs.size())));
-    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker, t);
     for (auto& t : pool) t.join();
 }
 

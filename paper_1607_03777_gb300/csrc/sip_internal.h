@@ -85,11 +85,17 @@ Tab1D<N, T> make_tab() {
 // sigma_e / eta_e for an interior face with x- / y-normal:
 // penalty_scale * n_f (1+tau) (k_pen+1)^2 |e|/|K| with n_f = 4, tau = 0 and
 // |e|/|K| = 1/h_normal; boundary faces double it (eq. sipg_penalty).
+// Kernel schedule of one operator, per precision ([0] FP64, [1] FP32):
+// which apply kernel runs and whether the p-level smoother step is fused.
+enum ApplyVariant { APPLY_AUTO = 0, APPLY_ELEM2 = 1, APPLY_ELEM1 = 2, APPLY_TILE = 3 };
+
 struct OpGeom {
     int nx, ny;
     double hx, hy;
     int bc[4];
     double pen_x, pen_y;
+    int variant[2];   // ApplyVariant (APPLY_AUTO: component-split for N <= 4, else tile)
+    int fused[2];     // p-level smoother step fused into one launch (1) or not (0)
 };
 
 inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], int k_pen,
@@ -101,6 +107,8 @@ inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], i
     g.hy = ly / ny;
     for (int i = 0; i < 4; ++i) g.bc[i] = bc[i];
     double c = penalty_scale * 4.0 * double(k_pen + 1) * double(k_pen + 1);
+    g.variant[0] = g.variant[1] = APPLY_AUTO;
+    g.fused[0] = g.fused[1] = 1;
     g.pen_x = c / g.hx;
     g.pen_y = c / g.hy;
     return g;
@@ -111,10 +119,30 @@ inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], i
 template <typename T>
 void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                       const T* z, T beta, cudaStream_t s);
-// Thread-per-element variant for N <= 4; returns false for other N.
+// Thread-per-element variants for N <= 4 (split: two threads per element,
+// one per velocity component); returns false for other N.
 template <typename T>
 bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
-                           const T* z, T beta, cudaStream_t s);
+                           const T* z, T beta, bool split, cudaStream_t s);
+// The apply variant in force for precision T: SIP_APPLY_KERNEL (elem2, elem1,
+// tile) overrides the operator's schedule.
+template <typename T>
+int apply_variant(const OpGeom& g);
+// Fused p-level smoother step (N <= 4; returns false otherwise, nothing launched):
+//   r = z - A x;  d_new = c1 d_old + c2 M^{-1} r;  yv += (pend ? d_old : 0) + d_new
+// with M^{-1} the element-block Jacobi inverses (class by emap < 0, scaled by
+// eta_inv, else unique).  z may alias r; x must not alias r, d_new or yv.
+bool cheb_elem_available(int N);
+// r1 = R (b - A y): the residual restricted to the Q^2_1 modes in one launch
+// (N <= 4; returns false otherwise, nothing launched).
+template <typename T>
+bool launch_residual_restrict_elem(int N, const OpGeom& g, const T* y, const T* b, const T* eta,
+                                   T* r1, cudaStream_t s);
+template <typename T>
+bool launch_cheb_elem(int N, const OpGeom& g, const T* x, const T* z, T* r, const T* eta,
+                      const int* emap, const T* cls_inv, const int* cls_sym, const T* uniq_inv,
+                      const T* eta_inv, const T* d_old, T* d_new, T* yv, T c1, T c2, bool pend,
+                      cudaStream_t s);
 template <typename T>
 void launch_apply_B(int k, const OpGeom& g, const T* p, T* y, cudaStream_t s);
 template <typename T>
@@ -135,6 +163,18 @@ struct AllocStreamScope {
     cudaStream_t prev;
     explicit AllocStreamScope(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
     ~AllocStreamScope() { alloc_stream() = prev; }
+};
+
+// While set (this thread), buffers are returned on the legacy default stream
+// instead of the stream they were allocated on.  Used where the device has
+// just been synchronised (problem destruction): the allocation stream may be
+// gone by then (a caller's stream, a finished batch worker's stream).
+bool& release_on_legacy();
+
+struct ReleaseOnLegacyScope {
+    bool prev;
+    ReleaseOnLegacyScope() : prev(release_on_legacy()) { release_on_legacy() = true; }
+    ~ReleaseOnLegacyScope() { release_on_legacy() = prev; }
 };
 
 struct DeviceBuffer {
@@ -161,7 +201,7 @@ struct DeviceBuffer {
     }
     ~DeviceBuffer() { release(); }
     void release() {
-        if (ptr) cudaFreeAsync(ptr, st);
+        if (ptr) cudaFreeAsync(ptr, release_on_legacy() ? cudaStreamLegacy : st);
         ptr = nullptr;
         bytes = 0;
     }

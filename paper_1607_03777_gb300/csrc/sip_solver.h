@@ -16,7 +16,8 @@ void launch_build_blocks(int N, const OpGeom& g, const int* spec, int count, con
                          T* out, cudaStream_t s);
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
-                     const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s);
+                     const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
+                     cudaStream_t s);
 
 // ---- transfer.cu
 template <typename T> void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s);
@@ -35,8 +36,11 @@ template <typename T>
 void launch_hcheb_first(size_t n, const T* b, const T* dinv, T* r, T* d, T* x, T c2,
                         cudaStream_t s);
 template <typename T>
+void launch_hcheb_start(int nvx, int nvy, const T* S, const T* dinv, const T* b, const T* x, T* r,
+                        T* d, T c2, cudaStream_t s);
+template <typename T>
 void launch_hcheb_step(int nvx, int nvy, const T* S, const T* dinv, T* r, const T* d_old,
-                       T* d_new, T* x, T c1, T c2, cudaStream_t s);
+                       T* d_new, T* x, T c1, T c2, bool pend, cudaStream_t s);
 template <typename T> void launch_rh(int nxc, int nyc, const T* rf, T* rc, cudaStream_t s);
 template <typename T>
 void launch_probe_vertices(int nvx, int nvy, int col, int cp, T* x, cudaStream_t s);
@@ -99,10 +103,11 @@ struct Multigrid {
     size_t ne = 0, n_u = 0;
     // element-block Jacobi
     DeviceBuffer emap, uniq_list, n_uniq_d, cls_inv, uniq_inv, eta_T;
+    DeviceBuffer cls_sym;   // reflection-symmetry type of each class block (sip_parity.cuh)
     int n_uniq = 0;
     double lmax_p = 0.0;
     // p-level work
-    DeviceBuffer pb, pr, pd, r1, e1, vin, vout;
+    DeviceBuffer pb, pr, pd, pd2, r1, e1, vin, vout;
     // continuous hierarchy (h[0] = finest continuous level)
     std::vector<HLevel<T>> h;
     // coarsest direct solve (dense inverse)
@@ -132,10 +137,15 @@ struct Multigrid {
     void bj(const T* r, T* z, cudaStream_t s);
     void coarse_solve(const T* b1, T* e1, cudaStream_t s);
     void hlevel_apply(int l, const T* x, T* y, cudaStream_t s);
+    // choose fused or split p-level smoother steps by timing (tune.cu)
+    void tune_smoother(cudaStream_t s);
     int inner_pcg(const T* t, T* y, double rtol, int maxit, cudaStream_t s, double* final_rel);
     int64_t bytes() const;
 
    private:
+    // fused p-level smoother steps: available for N <= 4, chosen by the
+    // schedule, and not overridden by SIP_APPLY_KERNEL=elem1 / tile
+    bool use_fused() const;
     void smooth_p(const T* b, T* y, bool zero, cudaStream_t s);
     void hcycle(int l, cudaStream_t s);
     void smooth_h(int l, bool zero, cudaStream_t s);
@@ -164,12 +174,17 @@ struct Workspace {
     int64_t bytes() const;
 };
 
+// Pick the apply kernel of each precision the problem runs in by timing
+// (tune.cu); cached per degree, precision and mesh.
+void tune_apply(sip_problem* P, cudaStream_t s);
+
 int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, double rtol,
                     int maxit, cudaStream_t s);
 // The same inner solve (FP64 iterate; V-cycle in FP32 when mixed, else FP64)
 // as one graph launch with a device-side loop; returns the iteration count.
-int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, const double* t, double* y,
-                    double rtol, int maxit, cudaStream_t s);
+// flexible: FCG(1) directions instead of PCG's.
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, const double* t,
+                    double* y, double rtol, int maxit, cudaStream_t s);
 
 sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,

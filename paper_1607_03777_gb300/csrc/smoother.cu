@@ -9,6 +9,7 @@
 // 1/eta_K; the remaining ("unique") elements get their own inverse.
 #include "sip_face.cuh"
 #include "sip_internal.h"
+#include "sip_parity.cuh"
 
 namespace sip {
 
@@ -173,6 +174,7 @@ template <int N, typename T>
 __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ r, T* out, T* x,
                                                   const int* __restrict__ emap,
                                                   const T* __restrict__ cls_inv,
+                                                  const int* __restrict__ cls_sym,
                                                   const T* __restrict__ uniq_inv,
                                                   const T* __restrict__ eta_inv, T c1, T c2,
                                                   int x_zero) {
@@ -189,17 +191,16 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
         const int m = emap[e];
         const T* Minv;
         T scale;
+        int sym = 0;
         if (m < 0) {
             Minv = cls_inv + size_t(-m - 1) * NB * NB;
             scale = eta_inv[e];
+            if (cls_sym) sym = cls_sym[-m - 1];
         } else {
             Minv = uniq_inv + size_t(m) * NB * NB;
             scale = T(1);
         }
-        const T* rr = sr + el * NB;
-        T acc = T(0);
-#pragma unroll 7
-        for (int s = 0; s < NB; ++s) acc += Minv[s * NB + row] * rr[s];
+        const T acc = block_row_apply<N, T>(Minv, sr + el * NB, row, sym);
         const size_t o = size_t(e) * NB + row;
         T v = c2 * scale * acc;
         if (c1 != T(0)) v += c1 * out[o];
@@ -238,12 +239,13 @@ void build_blocks_n(const OpGeom& g, const int* spec, int count, const double* e
 
 template <int N, typename T>
 void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
-                const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s) {
+                const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
+                cudaStream_t s) {
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     const int blocks = (ne + EB - 1) / EB;
-    k_bj_apply<N, T><<<blocks, 256, 0, s>>>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2,
-                                            x_zero ? 1 : 0);
+    k_bj_apply<N, T><<<blocks, 256, 0, s>>>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta,
+                                            c1, c2, x_zero ? 1 : 0);
     SIP_CHECK_LAUNCH();
 }
 
@@ -276,22 +278,23 @@ template void launch_build_blocks<float>(int, const OpGeom&, const int*, int, co
 
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
-                     const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero, cudaStream_t s) {
+                     const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
+                     cudaStream_t s) {
     switch (N) {
-        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
         default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
     }
 }
 template void launch_bj_apply<double>(int, int, const double*, double*, double*, const int*,
-                                      const double*, const double*, const double*, double, double,
-                                      bool, cudaStream_t);
+                                      const double*, const int*, const double*, const double*,
+                                      double, double, bool, cudaStream_t);
 template void launch_bj_apply<float>(int, int, const float*, float*, float*, const int*,
-                                     const float*, const float*, const float*, float, float, bool,
-                                     cudaStream_t);
+                                     const float*, const int*, const float*, const float*, float,
+                                     float, bool, cudaStream_t);
 
 }  // namespace sip

@@ -22,6 +22,11 @@ cudaStream_t& alloc_stream() {
     return s;
 }
 
+bool& release_on_legacy() {
+    static thread_local bool on = false;
+    return on;
+}
+
 namespace {
 
 __global__ void k_splitmix(size_t n, uint64_t seed, double* out) {
@@ -224,7 +229,7 @@ Multigrid<T>::~Multigrid() {
 template <typename T>
 int64_t Multigrid<T>::bytes() const {
     int64_t b = int64_t(emap.bytes + uniq_list.bytes + n_uniq_d.bytes + cls_inv.bytes +
-                        uniq_inv.bytes + pb.bytes + pr.bytes + pd.bytes + r1.bytes + e1.bytes +
+                        uniq_inv.bytes + cls_sym.bytes + pb.bytes + pr.bytes + pd.bytes + pd2.bytes + r1.bytes + e1.bytes +
                         vin.bytes + vout.bytes + cinv.bytes + ws.bytes + sc.bytes + cg_r.bytes +
                         cg_d.bytes + cg_q.bytes);
     for (const auto& l : h)
@@ -255,12 +260,47 @@ void Multigrid<T>::build_blocks(cudaStream_t s) {
     uniq_inv.alloc(size_t(std::max(n_uniq, 1)) * nb * nb * sizeof(T));
     launch_build_blocks<T>(N, P->geom, uniq_list.as<int>(), n_uniq, P->eta_d.as<double>(),
                            uniq_inv.template as<T>(), s);
+    // Reflection symmetry of each class block: x-faces of one kind (both
+    // interior, or both boundary with the same condition) make the block
+    // commute with x -> -x, likewise in y; confirmed on the computed inverse
+    // (couplings between modes of different parity must vanish), else dense.
+    const int NBl = nb;
+    std::vector<T> ch(size_t(16) * NBl * NBl);
+    SIP_CUDA(cudaMemcpyAsync(ch.data(), cls_inv.ptr, ch.size() * sizeof(T), cudaMemcpyDeviceToHost, s));
     SIP_CUDA(cudaStreamSynchronize(s));   // dspec is released on return
+    std::vector<int> par(NBl), sym(16, 0);
+    for (int q = 0; q < NBl; ++q) {
+        const int c = q / (N * N), j = (q / N) % N, i = q % N;
+        par[q] = ((i + (c == 0)) & 1) | (((j + (c == 1)) & 1) << 1);
+    }
+    const int* bc = P->geom.bc;
+    for (int m = 0; m < 16; ++m) {
+        const bool bl = m & 1, br = m & 2, bb = m & 4, bt = m & 8;
+        const bool sx = bl == br && (!bl || bc[0] == bc[1]);
+        const bool sy = bb == bt && (!bb || bc[2] == bc[3]);
+        int t = (sx ? 1 : 0) | (sy ? 2 : 0);
+        if (t) {
+            const T* M = ch.data() + size_t(m) * NBl * NBl;
+            double mx = 0.0, off = 0.0;
+            for (int a = 0; a < NBl; ++a)
+                for (int b2 = 0; b2 < NBl; ++b2) {
+                    const double v = std::abs(double(M[size_t(a) * NBl + b2]));
+                    mx = std::max(mx, v);
+                    if ((par[a] & t) != (par[b2] & t)) off = std::max(off, v);
+                }
+            if (!(off <= 1e-10 * mx)) t = 0;
+        }
+        sym[m] = t;
+    }
+    cls_sym.alloc(16 * sizeof(int));
+    SIP_CUDA(cudaMemcpyAsync(cls_sym.ptr, sym.data(), 16 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SIP_CUDA(cudaStreamSynchronize(s));   // sym is released on return
 }
 
 template <typename T>
 void Multigrid<T>::bj(const T* r, T* z, cudaStream_t s) {
-    launch_bj_apply<T>(N, int(ne), r, z, nullptr, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(),
+    launch_bj_apply<T>(N, int(ne), r, z, nullptr, emap.as<int>(), cls_inv.template as<T>(),
+                       cls_sym.as<int>(), uniq_inv.template as<T>(),
                        eta_inv_of<T>(P), T(0), T(1), true, s);
 }
 
@@ -388,6 +428,7 @@ void Multigrid<T>::setup(cudaStream_t s) {
     pb.alloc(n_u * sizeof(T));
     pr.alloc(n_u * sizeof(T));
     pd.alloc(n_u * sizeof(T));
+    if (cheb_elem_available(N)) pd2.alloc(n_u * sizeof(T));
     vin.alloc(n_u * sizeof(T));
     vout.alloc(n_u * sizeof(T));
     r1.alloc(ne * 8 * sizeof(T));
@@ -397,6 +438,7 @@ void Multigrid<T>::setup(cudaStream_t s) {
     cg_q.alloc(n_u * sizeof(T));
     build_blocks(s);
     lmax_p = estimate_p(s);
+    tune_smoother(s);
 
     const OpGeom& g1 = P->geom1;
     if (d.n_hlevels == 0) {
@@ -550,23 +592,72 @@ void Multigrid<T>::setup(cudaStream_t s) {
 }
 
 template <typename T>
+bool Multigrid<T>::use_fused() const {
+    static const bool env_off = [] {
+        const char* v = std::getenv("SIP_APPLY_KERNEL");
+        return v && (std::string(v) == "elem1" || std::string(v) == "tile");
+    }();
+    return !env_off && pd2.ptr && cheb_elem_available(N) &&
+           P->geom.fused[sizeof(T) == 4 ? 1 : 0] != 0;
+}
+
+template <typename T>
 void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
     const Cheb ch(P->desc.cheb_lo * lmax_p, P->desc.cheb_hi * lmax_p);
     T* r = pr.template as<T>();
     T* dd = pd.template as<T>();
     const T* eta = eta_of<T>(P);
+    const T* einv0 = eta_inv_of<T>(P);
+    const int steps = P->desc.cheb_steps_p;
+    // fused path (N <= 4): each step after the first is one launch
+    //   r = z - A d, d' = c1 d + c2 M^{-1} r, y += d'   (directions ping-pong);
+    // from a non-zero y the first step only forms r = b - A y and d, and
+    // its y update is deferred into the next launch (x = y cannot be
+    // written while neighbours read it).
+    if (steps >= 2 && use_fused()) {
+        T* dA = dd;
+        T* dB = pd2.template as<T>();
+        bool pend = false;
+        const int* em = emap.as<int>();
+        const T* ci = cls_inv.template as<T>();
+        const T* ui = uniq_inv.template as<T>();
+        const int* cs = cls_sym.as<int>();
+        if (zero) {
+            // d = c2 M^{-1} b, y = d; the next step's residual is b - A d
+            launch_bj_apply<T>(N, int(ne), b, dA, y, em, ci, cs, ui, einv0, T(0), T(1.0 / ch.theta),
+                               true, s);
+        } else {
+            launch_cheb_elem<T>(N, P->geom, y, b, r, eta, em, ci, cs, ui, einv0, nullptr, dA, nullptr,
+                                T(0), T(1.0 / ch.theta), false, s);
+            pend = true;
+        }
+        const T* zsrc = zero ? b : r;
+        double rho = 1.0 / ch.sigma;
+        for (int st = 1; st < steps; ++st) {
+            const double rn = 1.0 / (2.0 * ch.sigma - rho);
+            launch_cheb_elem<T>(N, P->geom, dA, zsrc, r, eta, em, ci, cs, ui, einv0, dA, dB, y,
+                                T(rn * rho), T(2.0 * rn / ch.delta), pend, s);
+            pend = false;
+            std::swap(dA, dB);
+            zsrc = r;
+            rho = rn;
+        }
+        return;
+    }
     if (zero)
         launch_axpby<T>(n_u, T(1), b, T(0), r, s);
     else
         launch_apply_sip<T>(N, P->geom, y, r, eta, T(-1), b, T(1), s);   // r = b - A y
     double rho = 1.0 / ch.sigma;
     const T* einv = eta_inv_of<T>(P);
-    launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(), einv,
+    launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
+                       cls_sym.as<int>(), uniq_inv.template as<T>(), einv,
                        T(0), T(1.0 / ch.theta), zero, s);
     for (int st = 1; st < P->desc.cheb_steps_p; ++st) {
         launch_apply_sip<T>(N, P->geom, dd, r, eta, T(-1), r, T(1), s);  // r -= A d
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
-        launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(), uniq_inv.template as<T>(),
+        launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
+                           cls_sym.as<int>(), uniq_inv.template as<T>(),
                            einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s);
         rho = rn;
     }
@@ -583,17 +674,24 @@ void Multigrid<T>::smooth_h(int l, bool zero, cudaStream_t s) {
     const T* b = L.b.template as<T>();
     const T* S = L.S.template as<T>();
     const T* dinv = L.dinv.template as<T>();
+    const int steps = P->desc.cheb_steps_h;
+    bool pend = false;
     if (zero) {
         launch_hcheb_first<T>(L.n, b, dinv, r, dA, x, T(1.0 / ch.theta), s);
+    } else if (steps >= 2) {
+        // r = b - A x, d = c2 D^{-1} r; x += d deferred to the next step
+        launch_hcheb_start<T>(L.nvx, L.nvy, S, dinv, b, x, r, dA, T(1.0 / ch.theta), s);
+        pend = true;
     } else {
         launch_stencil_apply<T>(L.nvx, L.nvy, S, x, r, T(-1), b, T(1), s);   // r = b - A x
         launch_jacobi_cheb<T>(L.n, r, dinv, dA, x, T(0), T(1.0 / ch.theta), false, s);
     }
     double rho = 1.0 / ch.sigma;
-    for (int st = 1; st < P->desc.cheb_steps_h; ++st) {
+    for (int st = 1; st < steps; ++st) {
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
         launch_hcheb_step<T>(L.nvx, L.nvy, S, dinv, r, dA, dB, x, T(rn * rho),
-                             T(2.0 * rn / ch.delta), s);
+                             T(2.0 * rn / ch.delta), pend, s);
+        pend = false;
         std::swap(dA, dB);
         rho = rn;
     }
@@ -637,8 +735,12 @@ void Multigrid<T>::vcycle_direct(cudaStream_t s) {
 template <typename T>
 void Multigrid<T>::vcycle_on(const T* b, T* y, cudaStream_t s) {
     smooth_p(b, y, true, s);
-    launch_apply_sip<T>(N, P->geom, y, pr.template as<T>(), eta_of<T>(P), T(-1), b, T(1), s);  // r = b - A y
-    launch_p_restrict<T>(ne, N, pr.template as<T>(), r1.template as<T>(), s);
+    // r1 = R (b - A y)
+    if (!use_fused() ||
+        !launch_residual_restrict_elem<T>(N, P->geom, y, b, eta_of<T>(P), r1.template as<T>(), s)) {
+        launch_apply_sip<T>(N, P->geom, y, pr.template as<T>(), eta_of<T>(P), T(-1), b, T(1), s);
+        launch_p_restrict<T>(ne, N, pr.template as<T>(), r1.template as<T>(), s);
+    }
     coarse_solve(r1.template as<T>(), e1.template as<T>(), s);
     launch_p_prolong_add<T>(ne, N, e1.template as<T>(), y, s);
     smooth_p(b, y, false, s);
@@ -850,6 +952,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
     // the inner PCG runs as one graph launch with a device-side loop unless
     // the options ask for the host-driven loop (same arithmetic)
     const bool host_loop = o.inner_loop == 1;
+    // flexible CG where the V-cycle is FP32 (automatic choice), else PCG
+    const bool flexible = o.inner_krylov == 2 || (o.inner_krylov == 0 && mixed && !host_loop);
     // z = P^{-1} v
     auto precond = [&](const double* v, double* z) {
         launch_vmul<double>(n_p, v + n_u, W.sinv.as<double>(), z + n_u, s);   // y_p = -S*^{-1} v_p
@@ -867,7 +971,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                         : P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s,
                                              nullptr);
         } else {
-            its = inner_pcg_graph(P, W, mixed, W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s);
+            its = inner_pcg_graph(P, W, mixed, flexible, W.tu.as<double>(), z, o.inner_rtol,
+                                  o.max_inner, s);
         }
         inner_total += its;
         inner_max = std::max(inner_max, its);
@@ -1030,6 +1135,8 @@ void sip_problem::derive_eta(cudaStream_t s) {
 void sip_problem::ensure_setup(cudaStream_t s) {
     const double t0 = sip::now_ms();
     bool did = false;
+    const bool fresh = (mg32 == nullptr || !mg32->ready) && (mg64 == nullptr || !mg64->ready);
+    if (fresh) sip::tune_apply(this, s);
     if (desc.precision == SIP_PREC_MIXED || desc.precision == SIP_PREC_MIXED_F32_INNER) {
         if (!mg32) {
             mg32 = std::make_unique<sip::Multigrid<float>>();

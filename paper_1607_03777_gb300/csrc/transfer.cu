@@ -79,18 +79,28 @@ __global__ void k_rdc(int nx, int ny, const T* __restrict__ r, T* __restrict__ o
     out[g] = T(acc);
 }
 
-// y = alpha * S x + beta * z for the 9-point 2x2-block stencil on an
-// (nvx x nvy) vertex grid; S[v][t][c][c'], t = (dy+1)*3 + (dx+1).
-template <typename T>
-__global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ x,
-                                T* __restrict__ y, T alpha, const T* __restrict__ z, T beta) {
-    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t nv = size_t(nvx) * nvy;
-    if (g >= nv * 2) return;
-    const int c = int(g % 2);
-    const size_t v = g / 2;
-    const int vx = int(v % nvx), vy = int(v / nvx);
-    const T* sv = S + v * 36;
+// Two consecutive values; one 2-word vector load when VEC (the launcher has
+// checked that every such pair is 2-word aligned).
+template <typename T, bool VEC>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
+    if constexpr (VEC && sizeof(T) == 8) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    } else if constexpr (VEC) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    } else {
+        a = p[0];
+        b = p[1];
+    }
+}
+
+// Row c of vertex (vx, vy) of the 9-point 2x2-block stencil times x.
+template <typename T, bool VEC>
+__device__ __forceinline__ T stencil_row(int nvx, int nvy, int vx, int vy, int c, const T* sv,
+                                         const T* __restrict__ x) {
     T acc = T(0);
     for (int dy = -1; dy <= 1; ++dy) {
         const int wy = vy + dy;
@@ -99,10 +109,32 @@ __global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const
             const int wx = vx + dx;
             if (wx < 0 || wx >= nvx) continue;
             const int t = (dy + 1) * 3 + (dx + 1);
-            const T* xw = x + 2 * (size_t(wy) * nvx + wx);
-            acc += sv[t * 4 + c * 2 + 0] * xw[0] + sv[t * 4 + c * 2 + 1] * xw[1];
+            T s0, s1, x0, x1;
+            ld2<T, VEC>(sv + t * 4 + c * 2, s0, s1);
+            ld2<T, VEC>(x + 2 * (size_t(wy) * nvx + wx), x0, x1);
+            acc += s0 * x0 + s1 * x1;
         }
     }
+    return acc;
+}
+
+template <typename T>
+bool pair_aligned(const T* p) {
+    return (reinterpret_cast<uintptr_t>(p) % (2 * sizeof(T))) == 0;
+}
+
+// y = alpha * S x + beta * z for the 9-point 2x2-block stencil on an
+// (nvx x nvy) vertex grid; S[v][t][c][c'], t = (dy+1)*3 + (dx+1).
+template <typename T, bool VEC>
+__global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ x,
+                                T* __restrict__ y, T alpha, const T* __restrict__ z, T beta) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nv = size_t(nvx) * nvy;
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    const T acc = stencil_row<T, VEC>(nvx, nvy, vx, vy, c, S + v * 36, x);
     T out = alpha * acc;
     if (z) out += beta * z[g];
     y[g] = out;
@@ -141,37 +173,45 @@ __global__ void k_hcheb_first(size_t n, const T* __restrict__ b, const T* __rest
     x[g] = v;
 }
 
-// One fused Chebyshev / point-Jacobi step on a continuous level:
-// r -= S d_old;  d_new = c1 d_old + c2 D^{-1} r;  x += d_new.
-// d_old is only read (neighbours too), d_new only written: no races.
-template <typename T>
-__global__ void k_hcheb_step(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
-                             T* __restrict__ r, const T* __restrict__ d_old, T* __restrict__ d_new,
-                             T* __restrict__ x, T c1, T c2) {
+// First Chebyshev step from a non-zero iterate, without its x update (x
+// is read by neighbours here): r = b - S x, d = c2 D^{-1} r.  The next
+// step adds d to x together with its own direction.
+template <typename T, bool VEC>
+__global__ void k_hcheb_start(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
+                              const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
+                              T* __restrict__ d, T c2) {
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t nv = size_t(nvx) * nvy;
     if (g >= nv * 2) return;
     const int c = int(g % 2);
     const size_t v = g / 2;
     const int vx = int(v % nvx), vy = int(v / nvx);
-    const T* sv = S + v * 36;
-    T acc = T(0);
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int wy = vy + dy;
-        if (wy < 0 || wy >= nvy) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int wx = vx + dx;
-            if (wx < 0 || wx >= nvx) continue;
-            const int t = (dy + 1) * 3 + (dx + 1);
-            const T* dw = d_old + 2 * (size_t(wy) * nvx + wx);
-            acc += sv[t * 4 + c * 2 + 0] * dw[0] + sv[t * 4 + c * 2 + 1] * dw[1];
-        }
-    }
+    const T acc = stencil_row<T, VEC>(nvx, nvy, vx, vy, c, S + v * 36, x);
+    const T rn = b[g] - acc;
+    r[g] = rn;
+    d[g] = c2 * dinv[g] * rn;
+}
+
+// One fused Chebyshev / point-Jacobi step on a continuous level:
+// r -= S d_old;  d_new = c1 d_old + c2 D^{-1} r;  x += d_new (+ d_old when
+// pend: the start step's deferred update).  d_old is only read (neighbours
+// too), d_new only written: no races.
+template <typename T, bool VEC>
+__global__ void k_hcheb_step(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
+                             T* __restrict__ r, const T* __restrict__ d_old, T* __restrict__ d_new,
+                             T* __restrict__ x, T c1, T c2, int pend) {
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nv = size_t(nvx) * nvy;
+    if (g >= nv * 2) return;
+    const int c = int(g % 2);
+    const size_t v = g / 2;
+    const int vx = int(v % nvx), vy = int(v / nvx);
+    const T acc = stencil_row<T, VEC>(nvx, nvy, vx, vy, c, S + v * 36, d_old);
     const T rn = r[g] - acc;
     r[g] = rn;
     const T dn = c1 * d_old[g] + c2 * dinv[g] * rn;
     d_new[g] = dn;
-    x[g] += dn;
+    x[g] += pend ? d_old[g] + dn : dn;
 }
 
 // fine (2 nxc + 1)^2 <- coarse (nxc + 1)^2 vertex grid, bilinear (add to y)
@@ -328,7 +368,11 @@ void launch_rdc(int nx, int ny, const T* r, T* out, cudaStream_t s) {
 template <typename T>
 void launch_stencil_apply(int nvx, int nvy, const T* S, const T* x, T* y, T alpha, const T* z,
                           T beta, cudaStream_t s) {
-    k_stencil_apply<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
+    const unsigned nb = nblk(size_t(nvx) * nvy * 2);
+    if (pair_aligned(S) && pair_aligned(x))
+        k_stencil_apply<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
+    else
+        k_stencil_apply<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -349,10 +393,25 @@ void launch_hcheb_first(size_t n, const T* b, const T* dinv, T* r, T* d, T* x, T
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
+void launch_hcheb_start(int nvx, int nvy, const T* S, const T* dinv, const T* b, const T* x, T* r,
+                        T* d, T c2, cudaStream_t s) {
+    const unsigned nb = nblk(size_t(nvx) * nvy * 2);
+    if (pair_aligned(S) && pair_aligned(x))
+        k_hcheb_start<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, b, x, r, d, c2);
+    else
+        k_hcheb_start<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, b, x, r, d, c2);
+    SIP_CHECK_LAUNCH();
+}
+template <typename T>
 void launch_hcheb_step(int nvx, int nvy, const T* S, const T* dinv, T* r, const T* d_old,
-                       T* d_new, T* x, T c1, T c2, cudaStream_t s) {
-    k_hcheb_step<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new,
-                                                                x, c1, c2);
+                       T* d_new, T* x, T c1, T c2, bool pend, cudaStream_t s) {
+    const unsigned nb = nblk(size_t(nvx) * nvy * 2);
+    if (pair_aligned(S) && pair_aligned(d_old))
+        k_hcheb_step<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
+                                                 pend ? 1 : 0);
+    else
+        k_hcheb_step<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
+                                                  pend ? 1 : 0);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -408,7 +467,9 @@ void launch_convert(size_t n, const double* a, T* b, cudaStream_t s) {
     template void launch_ph_add<T>(int, int, const T*, T*, cudaStream_t);                       \
     template void launch_hcheb_first<T>(size_t, const T*, const T*, T*, T*, T*, T, cudaStream_t); \
     template void launch_hcheb_step<T>(int, int, const T*, const T*, T*, const T*, T*, T*, T, T,  \
-                                       cudaStream_t);                                            \
+                                       bool, cudaStream_t);                                      \
+    template void launch_hcheb_start<T>(int, int, const T*, const T*, const T*, const T*, T*, T*, \
+                                        T, cudaStream_t);                                        \
     template void launch_rh<T>(int, int, const T*, T*, cudaStream_t);                           \
     template void launch_probe_vertices<T>(int, int, int, int, T*, cudaStream_t);               \
     template void launch_extract_stencil<T>(int, int, const T*, T*, cudaStream_t);              \

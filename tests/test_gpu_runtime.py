@@ -96,3 +96,52 @@ def test_server_queues_beyond_slots(ctx):
     assert sorted(i for i, _ in done) == [0, 1, 2, 3]
     assert all(r["status"] == 0 for _, r in done)
     srv.close()
+
+
+@pytest.mark.parametrize("k,precision", [(2, "fp64"), (3, "mixed"), (5, "fp64")])
+def test_autotuned_schedule(ctx, k, precision):
+    """The first set-up of a shape picks its kernels by timing; a second
+    problem of the same shape reuses the choice; the schedule holds only
+    kernels that exist for the degree (degree > 3: the tile kernel, no fused
+    smoother)."""
+    n = 48
+    shapes = synth.jittered_sinkers(3, (2.0, 2.0))
+    a = _alone(ctx, n, k, shapes, precision)
+    b = _alone(ctx, n, k, shapes, precision)
+    sa, sb = a[0].schedule(), b[0].schedule()
+    assert sa == sb
+    if k <= 3:
+        assert all(v in (1, 2, 3) for v in sa["apply"])
+        assert all(v in (0, 1) for v in sa["fused"])
+    else:
+        assert sa["apply"] == [3, 3] and sa["fused"] == [0, 0]
+    # same shape, same kernels: bit-identical solves
+    assert torch.equal(a[2], b[2]) and torch.equal(a[3], b[3])
+
+
+def test_batch_allocates_then_problems_destroyed(ctx):
+    """Problems whose solver workspace is first allocated inside a batched
+    solve (on the batch's worker streams) are solved again alone and then
+    destroyed after the batch has returned."""
+    inst = _instances(4, 7)
+    probs, fs, us, ps = [], [], [], []
+    for n, k, shapes, precision in inst:
+        eta, rho = ctx.rasterise_inclusions(n, n, shapes)
+        prob = api.Problem(ctx, n, n, k, eta.cpu().numpy(), bc=synth.SINKER_BC,
+                           n_hlevels=synth.levels_to_17(n) if n > 16 else 1, seed=2,
+                           precision=precision)
+        f = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        prob.rhs_body_force(rho, synth.GRAVITY, f)
+        probs.append(prob)
+        fs.append(f)
+        us.append(torch.empty_like(f))
+        ps.append(torch.empty(prob.n_p, dtype=torch.float64, device="cuda"))
+    st, reps = api.solve_batch(ctx, probs, fs, us, ps, n_streams=4, rtol=1e-8)
+    assert st == 0 and all(r["status"] == 0 for r in reps)
+    u2 = torch.empty_like(us[0])
+    p2 = torch.empty_like(ps[0])
+    probs[0].solve(fs[0], u2, p2, rtol=1e-8)
+    assert torch.equal(u2, us[0])
+    for pr in probs:
+        pr.close()
+    torch.cuda.synchronize()

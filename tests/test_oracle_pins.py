@@ -470,3 +470,42 @@ def test_fcg_tolerates_varying_preconditioner():
     y, its = krylov.fcg(lambda v: A @ v, prec, x, 1e-8, maxit=500)
     assert np.linalg.norm(A @ y - x) < 1e-8 * np.linalg.norm(x)
     assert its < 300
+
+
+def _parity_classes(k):
+    n = k + 1
+    out = []
+    for c in range(2):
+        for j in range(n):
+            for i in range(n):
+                out.append(((i + (c == 0)) & 1) | (((j + (c == 1)) & 1) << 1))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_element_block_reflection_parity(k):
+    """The diagonal block of an element whose opposite faces are alike
+    (interior with equal penalties, or boundary of one kind) couples only
+    velocity modes of equal reflection parity, (-1)^(i + [c = x]) in x and
+    (-1)^(j + [c = y]) in y; an element with one boundary x-face and one
+    interior x-face couples the x-parities."""
+    nx = ny = 3
+    prob = sip.Problem(nx, ny, k, np.ones(nx * ny), bc=("navier",) * 4)
+    A = sip.assemble_A(prob).tocsr()
+    nb = prob.num.nb
+    blocks = multigrid.block_jacobi_blocks(A, nb)
+    par = _parity_classes(k)
+    same_x = (par[:, None] & 1) == (par[None, :] & 1)
+    same_y = (par[:, None] & 2) == (par[None, :] & 2)
+    centre = blocks[4]                       # all four faces interior
+    scale = np.abs(centre).max()
+    assert np.abs(centre[~(same_x & same_y)]).max() <= 1e-13 * scale
+    corner = blocks[0]                       # Navier left and bottom, interior right and top
+    assert np.abs(corner[~same_x]).max() > 1e-3 * np.abs(corner).max()
+    strip = sip.Problem(1, 3, k, np.ones(3), bc=("navier",) * 4)   # both x-faces Navier
+    Bs = multigrid.block_jacobi_blocks(sip.assemble_A(strip).tocsr(), nb)
+    mid = Bs[1]                              # x: Navier both sides; y: interior both sides
+    assert np.abs(mid[~(same_x & same_y)]).max() <= 1e-13 * np.abs(mid).max()
+    # the inverse keeps the structure
+    inv = np.linalg.inv(centre)
+    assert np.abs(inv[~(same_x & same_y)]).max() <= 1e-12 * np.abs(inv).max()
