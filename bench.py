@@ -283,6 +283,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(eta_h.nbytes + rho_pin.numel() * 8),
                 "d2h_bytes_per_step": int((prob64.n_u + prob64.n_p) * 8)},
         "gpu_launches": int(launches),
+        "schedule": {"fp64": prob64.schedule(), "mixed": prob32.schedule()},
         "clocks": clk,
         "sip_apply": {"kernel": DOMINANT, "ms": apply_ms,
                       "GB_per_s": ab / apply_ms / 1e6, "GFLOP_per_s": af / apply_ms / 1e6,

@@ -597,8 +597,15 @@ bool Multigrid<T>::use_fused() const {
         const char* v = std::getenv("SIP_APPLY_KERNEL");
         return v && (std::string(v) == "elem1" || std::string(v) == "tile");
     }();
-    return !env_off && pd2.ptr && cheb_elem_available(N) &&
-           P->geom.fused[sizeof(T) == 4 ? 1 : 0] != 0;
+    // SIP_FUSED_SMOOTHER=0 / 1 pins the choice (profiling runs, where timings
+    // taken under the profiler would mislead the autotuner)
+    static const int forced = [] {
+        const char* v = std::getenv("SIP_FUSED_SMOOTHER");
+        return v ? (std::string(v) == "1" ? 1 : 0) : -1;
+    }();
+    if (env_off || !pd2.ptr || !cheb_elem_available(N)) return false;
+    if (forced >= 0) return forced == 1;
+    return P->geom.fused[sizeof(T) == 4 ? 1 : 0] != 0;
 }
 
 template <typename T>
