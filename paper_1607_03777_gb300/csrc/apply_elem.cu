@@ -134,9 +134,11 @@ template <int N, typename T>
 __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
     constexpr int TR = 4 * N;                 // [2 val/der][2 comp][N] per face
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // own element, all four faces: s_tr[TXY][4][TR]; halo: s_halo[NHALO][TR]
-    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);
-    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TXY * 4 * TR);
+    // own element, all four faces: s_tr[TXY][4 TR + 1]; halo: s_halo[NHALO][TR + 1]
+    // (odd row strides: lanes of a warp hit distinct banks)
+    T (*s_tr)[4 * TR + 1] = reinterpret_cast<T (*)[4 * TR + 1]>(smem_raw);
+    T (*s_halo)[TR + 1] =
+        reinterpret_cast<T (*)[TR + 1]>(smem_raw + sizeof(T) * TXY * (4 * TR + 1));
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int ex0 = blockIdx.x * TX, ey0 = blockIdx.y * TY;
     const int ex = ex0 + tx, ey = ey0 + ty;
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
         etaK = a.eta[size_t(ey) * nx + ex];
 #pragma unroll
         for (int F = 0; F < 4; ++F)
-            face_traces<N, T>(u, F, F < 2 ? a.two_over_hx : a.two_over_hy, s_tr[threadIdx.x][F]);
+            face_traces<N, T>(u, F, F < 2 ? a.two_over_hx : a.two_over_hy,
+                              s_tr[threadIdx.x] + F * TR);
         // volume: eta_K [ 2(hy/hx) G_x + (hx/hy) G_y + cross ] on u_x, and
         //         eta_K [ 2(hx/hy) G_y + (hy/hx) G_x + cross ] on u_y
 #pragma unroll
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int F = 2 * dir + side;
-            const T* own = s_tr[threadIdx.x][F];
+            const T* own = s_tr[threadIdx.x] + F * TR;
             const T* nbr = nullptr;
             T etaN = T(0);
             int kind;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
                 etaN = a.eta[size_t(nyi) * nx + nxi];
                 const int ltx = nxi - ex0, lty = nyi - ey0;
                 if (ltx >= 0 && ltx < TX && lty >= 0 && lty < TY) {
-                    nbr = s_tr[lty * TX + ltx][F ^ 1];
+                    nbr = s_tr[lty * TX + ltx] + (F ^ 1) * TR;
                 } else if (dir == 1) {
                     nbr = s_halo[(side == 0 ? 0 : TX) + tx];
                 } else {
@@ -443,10 +446,10 @@ __device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
 // registers) in phase A: own traces of component C and the volume terms of y_C.
 template <int N, typename T, int C>
 __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)[2][N][N], T etaK,
-                                              T (*tr)[4 * N], T (&y)[N][N]) {
+                                              T* tr, T (&y)[N][N]) {
 #pragma unroll
     for (int F = 0; F < 4; ++F)
-        face_traces_comp<N, T>(u, F, C, F < 2 ? a.two_over_hx : a.two_over_hy, tr[F]);
+        face_traces_comp<N, T>(u, F, C, F < 2 ? a.two_over_hx : a.two_over_hy, tr + F * 4 * N);
     const T sx = C == 0 ? a.c2hy_hx : a.chy_hx;   // weight of G along x on u_C
     const T sy = C == 0 ? a.chx_hy : a.c2hx_hy;   // weight of G along y on u_C
 #pragma unroll
@@ -511,8 +514,8 @@ __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)
 // into y_C, written out.
 template <int N, typename T, int C, bool VEC>
 __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int ey, int ex0, int ey0,
-                                              int tx, int ty, T etaK, T (*s_tr)[4][4 * N],
-                                              T (*s_halo)[4 * N], int el, T (&y)[N][N],
+                                              int tx, int ty, T etaK, T (*s_tr)[16 * N + 1],
+                                              T (*s_halo)[4 * N + 1], int el, T (&y)[N][N],
                                               T* sres = nullptr) {
     constexpr int NB = 2 * N * N;
     const int nx = a.nx, ny = a.ny;
@@ -527,7 +530,7 @@ __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int 
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int F = 2 * dir + side;
-            const T* own = s_tr[el][F];
+            const T* own = s_tr[el] + F * 4 * N;
             const T* nbr = own;
             T etaN = T(0);
             int kind;
@@ -540,7 +543,7 @@ __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int 
                 etaN = a.eta[size_t(nyi) * nx + nxi];
                 const int ltx = nxi - ex0, lty = nyi - ey0;
                 if (ltx >= 0 && ltx < TX && lty >= 0 && lty < TY2)
-                    nbr = s_tr[lty * TX + ltx][F ^ 1];
+                    nbr = s_tr[lty * TX + ltx] + (F ^ 1) * 4 * N;
                 else if (dir == 1)
                     nbr = s_halo[(side == 0 ? 0 : TX) + tx];
                 else
@@ -621,7 +624,7 @@ struct Elem2Ids {
 // traces and volume terms (into y).  Ends with the CTA barrier.
 template <int N, typename T, bool VEC>
 __device__ __forceinline__ void elem2_phase_a_all(const ElemArgs<T>& a, const Elem2Ids& id,
-                                                  T (*s_tr)[4][4 * N], T (*s_halo)[4 * N],
+                                                  T (*s_tr)[16 * N + 1], T (*s_halo)[4 * N + 1],
                                                   T (&y)[N][N], T& etaK) {
     constexpr int NB = 2 * N * N;
     const int nx = a.nx, ny = a.ny;
@@ -654,8 +657,10 @@ template <int N, typename T, bool VEC>
 __global__ void __launch_bounds__(T2THREADS) k_apply_elem2(const ElemArgs<T> a) {
     constexpr int TR = 4 * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);   // [TX*TY2][4][TR]
-    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
+    // [TX*TY2][4 TR + 1] and [NHALO2][TR + 1]: odd row strides, conflict-free banks
+    T (*s_tr)[4 * TR + 1] = reinterpret_cast<T (*)[4 * TR + 1]>(smem_raw);
+    T (*s_halo)[TR + 1] =
+        reinterpret_cast<T (*)[TR + 1]>(smem_raw + sizeof(T) * TX * TY2 * (4 * TR + 1));
     const Elem2Ids id(a.nx, a.ny);
     T y[N][N];
     T etaK;
@@ -698,15 +703,18 @@ __global__ void __launch_bounds__(T2THREADS) k_cheb_elem2(const ElemArgs<T> a, c
     constexpr int NB = 2 * N * N;
     static_assert(NB <= 32, "one warp lane per block row");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*s_tr)[4][TR] = reinterpret_cast<T (*)[4][TR]>(smem_raw);
-    T (*s_halo)[TR] = reinterpret_cast<T (*)[TR]>(smem_raw + sizeof(T) * TX * TY2 * 4 * TR);
-    T* s_res = reinterpret_cast<T*>(smem_raw + sizeof(T) * (TX * TY2 * 4 + NHALO2) * TR);
+    T (*s_tr)[4 * TR + 1] = reinterpret_cast<T (*)[4 * TR + 1]>(smem_raw);
+    T (*s_halo)[TR + 1] =
+        reinterpret_cast<T (*)[TR + 1]>(smem_raw + sizeof(T) * TX * TY2 * (4 * TR + 1));
+    // residual blocks, row stride NB + 1
+    T* s_res = reinterpret_cast<T*>(smem_raw + sizeof(T) * (TX * TY2 * (4 * TR + 1) +
+                                                            NHALO2 * (TR + 1)));
     const Elem2Ids id(a.nx, a.ny);
     T y[N][N];
     T etaK;
     elem2_phase_a_all<N, T, VEC>(a, id, s_tr, s_halo, y, etaK);
     if (id.active) {
-        T* sres = s_res + id.el * NB + id.c * N * N;
+        T* sres = s_res + id.el * (NB + 1) + id.c * N * N;
         if (id.c == 0)
             elem2_phase_b<N, T, 0, VEC>(a, id.ex, id.ey, id.ex0, id.ey0, id.tx, id.ty, etaK, s_tr,
                                         s_halo, id.el, y, sres);
@@ -752,7 +760,7 @@ __global__ void __launch_bounds__(T2THREADS) k_cheb_elem2(const ElemArgs<T> a, c
             T acc[ILP];
 #pragma unroll
             for (int k = 0; k < ILP; ++k)
-                acc[k] = block_row_apply<N, T>(Mk[k], s_res + e2k[k] * NB, row, symk[k]);
+                acc[k] = block_row_apply<N, T>(Mk[k], s_res + e2k[k] * (NB + 1), row, symk[k]);
 #pragma unroll
             for (int k = 0; k < ILP; ++k) {
                 if (!ok[k]) continue;
@@ -764,6 +772,15 @@ __global__ void __launch_bounds__(T2THREADS) k_cheb_elem2(const ElemArgs<T> a, c
             }
         }
     }
+}
+
+// dynamic shared memory of the component-split kernels (padded rows)
+template <int N, typename T>
+size_t elem2_smem(bool with_residual) {
+    const size_t tile = size_t(TX) * TY2;
+    size_t words = tile * (16 * N + 1) + size_t(NHALO2) * (4 * N + 1);
+    if (with_residual) words += tile * (2 * N * N + 1);
+    return sizeof(T) * words;
 }
 
 template <typename T>
@@ -801,7 +818,7 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
     const ElemArgs<T> a = make_elem_args<T>(g, x, y, eta, alpha, z, beta);
     if (split) {
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
-        const size_t smem = sizeof(T) * (size_t(TX) * TY2 * 4 + NHALO2) * 4 * N;
+        const size_t smem = elem2_smem<N, T>(false);
         static const bool attr2 = [smem] {   // once per process, thread-safe
             SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, false>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -818,7 +835,7 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
         return;
     }
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    const size_t smem = sizeof(T) * (size_t(TXY) * 4 + NHALO) * 4 * N;
+    const size_t smem = sizeof(T) * (size_t(TXY) * (16 * N + 1) + size_t(NHALO) * (4 * N + 1));
     static const bool attr_set = [smem] {   // once per process, thread-safe
         SIP_CUDA(cudaFuncSetAttribute(k_apply_elem<N, T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -835,7 +852,7 @@ void residual_restrict_n(const OpGeom& g, const T* y, const T* b, const T* eta, 
     ElemArgs<T> a = make_elem_args<T>(g, y, nullptr, eta, T(-1), b, T(1));
     a.r1 = r1;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
-    const size_t smem = sizeof(T) * (size_t(TX) * TY2 * 4 + NHALO2) * 4 * N;
+    const size_t smem = elem2_smem<N, T>(false);
     static const bool attr = [smem] {   // once per process, thread-safe
         SIP_CUDA(cudaFuncSetAttribute(k_apply_elem2<N, T, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -856,8 +873,7 @@ void cheb_elem_n(const OpGeom& g, const T* x, const T* z, T* r, const T* eta, co
                  cudaStream_t s) {
     const ElemArgs<T> a = make_elem_args<T>(g, x, r, eta, T(-1), z, T(1));
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY2 - 1) / TY2);
-    const size_t smem = sizeof(T) * ((size_t(TX) * TY2 * 4 + NHALO2) * 4 * N +
-                                     size_t(TX) * TY2 * 2 * N * N);
+    const size_t smem = elem2_smem<N, T>(true);
     static const bool attr = [smem] {   // once per process, thread-safe
         SIP_CUDA(cudaFuncSetAttribute(k_cheb_elem2<N, T, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
