@@ -61,6 +61,7 @@ constexpr size_t apply_smem_elems() {
 // both sides).
 template <int N, typename T>
 __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
+    grid_dep_wait();
     constexpr int NN = N * N, NB = 2 * NN, EX = TileCfg<N>::EX, EXH = EX + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* su = reinterpret_cast<T*>(smem_raw);
@@ -281,7 +282,7 @@ void apply_sip_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const
     }();
     (void)attr_set;
     dim3 grid((g.nx + EX - 1) / EX, g.ny);
-    k_apply_sip<N, T><<<grid, 256, smem, s>>>(a);
+    launch_k(k_apply_sip<N, T>, grid, 256, smem, s, a);
     SIP_CHECK_LAUNCH();
 }
 
@@ -300,6 +301,7 @@ struct BArgs {
 // degree k - 1 (indices < K = N - 1).
 template <int N, typename T>
 __global__ void k_apply_B(const BArgs<N, T> a) {
+    grid_dep_wait();
     constexpr int NN = N * N, NB = 2 * NN, K = N - 1, MP = K * K;
     const size_t gid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t ne = size_t(a.nx) * a.ny;
@@ -354,6 +356,7 @@ __global__ void k_apply_B(const BArgs<N, T> a) {
 // B^T u: one thread per pressure output (e, jb, ia).
 template <int N, typename T>
 __global__ void k_apply_Bt(const BArgs<N, T> a) {
+    grid_dep_wait();
     constexpr int NN = N * N, NB = 2 * NN, K = N - 1, MP = K * K;
     const size_t gid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t ne = size_t(a.nx) * a.ny;
@@ -413,6 +416,7 @@ BArgs<N, T> make_bargs(const OpGeom& g, const T* in, T* out) {
 
 __global__ void k_rhs_body(const double* rho, double grav, double area_half, int nb, size_t ne,
                            double* f) {
+    grid_dep_wait();
     const size_t gid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (gid >= ne * nb) return;
     const size_t e = gid / nb;
@@ -423,6 +427,7 @@ __global__ void k_rhs_body(const double* rho, double grav, double area_half, int
 
 __global__ void k_rasterise(int nx, int ny, double hx, double hy, const double* shp, int ns,
                             double eta_bg, double rho_bg, double* eta, double* rho) {
+    grid_dep_wait();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nx * ny) return;
     const int ex = e % nx, ey = e / nx;
@@ -500,7 +505,7 @@ void launch_apply_B(int k, const OpGeom& g, const T* p, T* y, cudaStream_t s) {
     const unsigned blocks = unsigned((total + 255) / 256);
     switch (k + 1) {
 #define SIP_B_CASE(NN_)                                                                    \
-    case NN_: k_apply_B<NN_, T><<<blocks, 256, 0, s>>>(make_bargs<NN_, T>(g, p, y)); break;
+    case NN_: launch_k(k_apply_B<NN_, T>, blocks, 256, 0, s, make_bargs<NN_, T>(g, p, y)); break;
         SIP_B_CASE(2) SIP_B_CASE(3) SIP_B_CASE(4) SIP_B_CASE(5) SIP_B_CASE(6) SIP_B_CASE(7)
 #undef SIP_B_CASE
         default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
@@ -515,7 +520,7 @@ void launch_apply_Bt(int k, const OpGeom& g, const T* u, T* y, cudaStream_t s) {
     const unsigned blocks = unsigned((total + 255) / 256);
     switch (k + 1) {
 #define SIP_BT_CASE(NN_)                                                                   \
-    case NN_: k_apply_Bt<NN_, T><<<blocks, 256, 0, s>>>(make_bargs<NN_, T>(g, u, y)); break;
+    case NN_: launch_k(k_apply_Bt<NN_, T>, blocks, 256, 0, s, make_bargs<NN_, T>(g, u, y)); break;
         SIP_BT_CASE(2) SIP_BT_CASE(3) SIP_BT_CASE(4) SIP_BT_CASE(5) SIP_BT_CASE(6) SIP_BT_CASE(7)
 #undef SIP_BT_CASE
         default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
@@ -529,7 +534,7 @@ void launch_rhs_body_force(int k, const OpGeom& g, const double* rho, double gra
     const int nb = 2 * (k + 1) * (k + 1);
     const size_t ne = size_t(g.nx) * g.ny;
     const size_t total = ne * nb;
-    k_rhs_body<<<unsigned((total + 255) / 256), 256, 0, s>>>(rho, grav, 0.5 * g.hx * g.hy, nb, ne,
+    launch_k(k_rhs_body, unsigned((total + 255) / 256), 256, 0, s, rho, grav, 0.5 * g.hx * g.hy, nb, ne,
                                                              f);
     SIP_CHECK_LAUNCH();
 }
@@ -537,7 +542,7 @@ void launch_rhs_body_force(int k, const OpGeom& g, const double* rho, double gra
 void launch_rasterise(int nx, int ny, double lx, double ly, const double* shapes, int ns,
                       double eta_bg, double rho_bg, double* eta, double* rho, cudaStream_t s) {
     const int ne = nx * ny;
-    k_rasterise<<<(ne + 255) / 256, 256, 0, s>>>(nx, ny, lx / nx, ly / ny, shapes, ns, eta_bg,
+    launch_k(k_rasterise, (ne + 255) / 256, 256, 0, s, nx, ny, lx / nx, ly / ny, shapes, ns, eta_bg,
                                                  rho_bg, eta, rho);
     SIP_CHECK_LAUNCH();
 }

@@ -132,6 +132,7 @@ __device__ __forceinline__ void face_traces_comp(const T (&u)[2][N][N], int F, i
 
 template <int N, typename T>
 __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
+    grid_dep_wait();
     constexpr int TR = 4 * N;                 // [2 val/der][2 comp][N] per face
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // own element, all four faces: s_tr[TXY][4 TR + 1]; halo: s_halo[NHALO][TR + 1]
@@ -655,6 +656,7 @@ __device__ __forceinline__ void elem2_phase_a_all(const ElemArgs<T>& a, const El
 
 template <int N, typename T, bool VEC>
 __global__ void __launch_bounds__(T2THREADS) k_apply_elem2(const ElemArgs<T> a) {
+    grid_dep_wait();
     constexpr int TR = 4 * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // [TX*TY2][4 TR + 1] and [NHALO2][TR + 1]: odd row strides, conflict-free banks
@@ -699,6 +701,7 @@ struct BJArgs {
 // alias d_new or yv: other tiles read x while this one writes.
 template <int N, typename T, bool VEC>
 __global__ void __launch_bounds__(T2THREADS) k_cheb_elem2(const ElemArgs<T> a, const BJArgs<T> b) {
+    grid_dep_wait();
     constexpr int TR = 4 * N;
     constexpr int NB = 2 * N * N;
     static_assert(NB <= 32, "one warp lane per block row");
@@ -828,9 +831,9 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
         }();
         (void)attr2;
         if (vec_ok<N, T>() && aligned16(x) && aligned16(y) && (z == nullptr || aligned16(z)))
-            k_apply_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a);
+            launch_k(k_apply_elem2<N, T, true>, grid, T2THREADS, smem, s, a);
         else
-            k_apply_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a);
+            launch_k(k_apply_elem2<N, T, false>, grid, T2THREADS, smem, s, a);
         SIP_CHECK_LAUNCH();
         return;
     }
@@ -842,7 +845,7 @@ void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, cons
         return true;
     }();
     (void)attr_set;
-    k_apply_elem<N, T><<<grid, TXY, smem, s>>>(a);
+    launch_k(k_apply_elem<N, T>, grid, TXY, smem, s, a);
     SIP_CHECK_LAUNCH();
 }
 
@@ -862,9 +865,9 @@ void residual_restrict_n(const OpGeom& g, const T* y, const T* b, const T* eta, 
     }();
     (void)attr;
     if (vec_ok<N, T>() && aligned16(y) && aligned16(b))
-        k_apply_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a);
+        launch_k(k_apply_elem2<N, T, true>, grid, T2THREADS, smem, s, a);
     else
-        k_apply_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a);
+        launch_k(k_apply_elem2<N, T, false>, grid, T2THREADS, smem, s, a);
     SIP_CHECK_LAUNCH();
 }
 
@@ -883,9 +886,9 @@ void cheb_elem_n(const OpGeom& g, const T* x, const T* z, T* r, const T* eta, co
     }();
     (void)attr;
     if (vec_ok<N, T>() && aligned16(x) && aligned16(r) && aligned16(z))
-        k_cheb_elem2<N, T, true><<<grid, T2THREADS, smem, s>>>(a, b);
+        launch_k(k_cheb_elem2<N, T, true>, grid, T2THREADS, smem, s, a, b);
     else
-        k_cheb_elem2<N, T, false><<<grid, T2THREADS, smem, s>>>(a, b);
+        launch_k(k_cheb_elem2<N, T, false>, grid, T2THREADS, smem, s, a, b);
     SIP_CHECK_LAUNCH();
 }
 

@@ -56,6 +56,7 @@ __device__ __forceinline__ double final_sum(const double* partial) {
 }
 
 __global__ void k_set(PcgState* st, const double* t, double* y) {
+    grid_dep_wait();
     st->t = t;
     st->y = y;
 }
@@ -63,6 +64,7 @@ __global__ void k_set(PcgState* st, const double* t, double* y) {
 // r = t, y = 0, d = 0; partial sums of t.t
 __global__ void __launch_bounds__(kRT) k_init(size_t n, PcgState* st, double* r, double* d,
                                               double* partial) {
+    grid_dep_wait();
     const double* t = st->t;
     double* y = st->y;
     double acc = 0.0;
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(kRT) k_init(size_t n, PcgState* st, double* r,
 
 __global__ void __launch_bounds__(kRT) k_init_final(PcgState* st, const double* partial,
                                                     cudaGraphConditionalHandle h) {
+    grid_dep_wait();
     const double s = final_sum(partial);
     if (threadIdx.x == 0) {
         const double nt = sqrt(s);
@@ -97,6 +100,7 @@ template <typename Tz>
 __global__ void __launch_bounds__(kRT) k_dot_rz(size_t n, const double* __restrict__ r,
                                                 const Tz* __restrict__ zs, double* zd,
                                                 double* partial) {
+    grid_dep_wait();
     double acc = 0.0;
     for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
          g += size_t(gridDim.x) * blockDim.x) {
@@ -110,6 +114,7 @@ __global__ void __launch_bounds__(kRT) k_dot_rz(size_t n, const double* __restri
 
 // beta = rz_new / rz (0 on the first pass); rz = rz_new
 __global__ void __launch_bounds__(kRT) k_beta_final(PcgState* st, const double* partial) {
+    grid_dep_wait();
     const double s = final_sum(partial);
     if (threadIdx.x == 0) {
         st->beta = st->it == 0 ? 0.0 : s / st->rz;
@@ -119,6 +124,7 @@ __global__ void __launch_bounds__(kRT) k_beta_final(PcgState* st, const double* 
 
 // d = z + beta d
 __global__ void k_dir(size_t n, const double* __restrict__ z, double* d, const PcgState* st) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     d[g] = z[g] + st->beta * d[g];
@@ -126,6 +132,7 @@ __global__ void k_dir(size_t n, const double* __restrict__ z, double* d, const P
 
 __global__ void __launch_bounds__(kRT) k_dot(size_t n, const double* __restrict__ a,
                                              const double* __restrict__ b, double* partial) {
+    grid_dep_wait();
     double acc = 0.0;
     for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
          g += size_t(gridDim.x) * blockDim.x)
@@ -136,6 +143,7 @@ __global__ void __launch_bounds__(kRT) k_dot(size_t n, const double* __restrict_
 
 // alpha = rz / (d.q)
 __global__ void __launch_bounds__(kRT) k_alpha_final(PcgState* st, const double* partial) {
+    grid_dep_wait();
     const double s = final_sum(partial);
     if (threadIdx.x == 0) st->alpha = st->rz / s;
 }
@@ -144,6 +152,7 @@ __global__ void __launch_bounds__(kRT) k_alpha_final(PcgState* st, const double*
 __global__ void __launch_bounds__(kRT) k_update_rr(size_t n, const double* __restrict__ d,
                                                    const double* __restrict__ q, double* r,
                                                    const PcgState* st, double* partial) {
+    grid_dep_wait();
     const double a = st->alpha;
     double* y = st->y;
     double acc = 0.0;
@@ -171,6 +180,7 @@ template <typename Tz>
 __global__ void __launch_bounds__(kRT) k_dot_zq(size_t n, const double* __restrict__ q,
                                                 const Tz* __restrict__ zs, double* zd,
                                                 double* partial) {
+    grid_dep_wait();
     double acc = 0.0;
     for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
          g += size_t(gridDim.x) * blockDim.x) {
@@ -184,6 +194,7 @@ __global__ void __launch_bounds__(kRT) k_dot_zq(size_t n, const double* __restri
 
 // stored as -beta so that k_dir (d = z + beta d) forms z - beta d
 __global__ void __launch_bounds__(kRT) k_beta_fcg_final(PcgState* st, const double* partial) {
+    grid_dep_wait();
     const double s = final_sum(partial);
     if (threadIdx.x == 0) st->beta = st->it == 0 ? 0.0 : -(s / st->dq);
 }
@@ -193,6 +204,7 @@ __global__ void __launch_bounds__(kRT) k_dot_dq_dr(size_t n, const double* __res
                                                    const double* __restrict__ q,
                                                    const double* __restrict__ r,
                                                    double* partial) {
+    grid_dep_wait();
     double a1 = 0.0, a2 = 0.0;
     for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
          g += size_t(gridDim.x) * blockDim.x) {
@@ -209,6 +221,7 @@ __global__ void __launch_bounds__(kRT) k_dot_dq_dr(size_t n, const double* __res
 }
 
 __global__ void __launch_bounds__(kRT) k_alpha_fcg_final(PcgState* st, const double* partial) {
+    grid_dep_wait();
     const double dq = final_sum(partial);
     const double dr = final_sum(partial + kRB);
     if (threadIdx.x == 0) {
@@ -221,6 +234,7 @@ __global__ void __launch_bounds__(kRT) k_alpha_fcg_final(PcgState* st, const dou
 __global__ void __launch_bounds__(kRT) k_ctl_final(PcgState* st, const double* partial,
                                                    double rtol, int maxit,
                                                    cudaGraphConditionalHandle h) {
+    grid_dep_wait();
     const double s = final_sum(partial);
     if (threadIdx.x == 0) {
         const double rr = sqrt(s);
@@ -280,45 +294,47 @@ void capture_body(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphCondition
         launch_cast<double, float>(n_u, r, vin, cs);
         mg.vcycle_on(vin, vout, cs);
         if (L.flexible)
-            k_dot_zq<float><<<kRB, kRT, 0, cs>>>(n_u, q, vout, z, part);
+            launch_k(k_dot_zq<float>, kRB, kRT, 0, cs, n_u, q, vout, z, part);
         else
-            k_dot_rz<float><<<kRB, kRT, 0, cs>>>(n_u, r, vout, z, part);
+            launch_k(k_dot_rz<float>, kRB, kRT, 0, cs, n_u, r, vout, z, part);
         SIP_CHECK_LAUNCH();
     } else {
         Multigrid<double>& mg = *P->mg64;
         mg.vcycle_on(r, z, cs);
         if (L.flexible)
-            k_dot_zq<double><<<kRB, kRT, 0, cs>>>(n_u, q, z, nullptr, part);
+            launch_k(k_dot_zq<double>, kRB, kRT, 0, cs, n_u, q, z, nullptr, part);
         else
-            k_dot_rz<double><<<kRB, kRT, 0, cs>>>(n_u, r, z, nullptr, part);
+            launch_k(k_dot_rz<double>, kRB, kRT, 0, cs, n_u, r, z, nullptr, part);
         SIP_CHECK_LAUNCH();
     }
     if (L.flexible)
-        k_beta_fcg_final<<<1, kRT, 0, cs>>>(st, part);
+        launch_k(k_beta_fcg_final, 1, kRT, 0, cs, st, part);
     else
-        k_beta_final<<<1, kRT, 0, cs>>>(st, part);
+        launch_k(k_beta_final, 1, kRT, 0, cs, st, part);
     SIP_CHECK_LAUNCH();
-    k_dir<<<nblk(n_u), 256, 0, cs>>>(n_u, z, d, st);
+    launch_k(k_dir, nblk(n_u), 256, 0, cs, n_u, z, d, st);
     SIP_CHECK_LAUNCH();
     launch_apply_sip<double>(P->n, P->geom, d, q, P->eta_d.as<double>(), 1.0, nullptr, 0.0, cs);
     if (L.flexible) {
-        k_dot_dq_dr<<<kRB, kRT, 0, cs>>>(n_u, d, q, r, part);
+        launch_k(k_dot_dq_dr, kRB, kRT, 0, cs, n_u, d, q, r, part);
         SIP_CHECK_LAUNCH();
-        k_alpha_fcg_final<<<1, kRT, 0, cs>>>(st, part);
+        launch_k(k_alpha_fcg_final, 1, kRT, 0, cs, st, part);
         SIP_CHECK_LAUNCH();
     } else {
-        k_dot<<<kRB, kRT, 0, cs>>>(n_u, d, q, part);
+        launch_k(k_dot, kRB, kRT, 0, cs, n_u, d, q, part);
         SIP_CHECK_LAUNCH();
-        k_alpha_final<<<1, kRT, 0, cs>>>(st, part);
+        launch_k(k_alpha_final, 1, kRT, 0, cs, st, part);
         SIP_CHECK_LAUNCH();
     }
-    k_update_rr<<<kRB, kRT, 0, cs>>>(n_u, d, q, r, st, part);
+    launch_k(k_update_rr, kRB, kRT, 0, cs, n_u, d, q, r, st, part);
     SIP_CHECK_LAUNCH();
-    k_ctl_final<<<1, kRT, 0, cs>>>(st, part, L.rtol, L.maxit, h);
+    launch_k(k_ctl_final, 1, kRT, 0, cs, st, part, L.rtol, L.maxit, h);
     SIP_CHECK_LAUNCH();
 }
 
 void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
+    // plain launches inside the graph that holds the conditional node
+    PdlOffScope pdl_off;
     if (L.exec) {
         SIP_CUDA(cudaGraphExecDestroy(L.exec));
         L.exec = nullptr;
@@ -340,11 +356,11 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
     // while node after it
     SIP_CUDA(cudaStreamBeginCaptureToGraph(L.cs, g, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal));
-    k_init<<<kRB, kRT, 0, L.cs>>>(n_u, L.state.as<PcgState>(), W.cg_r.as<double>(),
+    launch_k(k_init, kRB, kRT, 0, L.cs, n_u, L.state.as<PcgState>(), W.cg_r.as<double>(),
                                   W.cg_d.as<double>(), L.partial.as<double>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        k_init_final<<<1, kRT, 0, L.cs>>>(L.state.as<PcgState>(), L.partial.as<double>(), h);
+        launch_k(k_init_final, 1, kRT, 0, L.cs, L.state.as<PcgState>(), L.partial.as<double>(), h);
         e = cudaGetLastError();
     }
     cudaGraphNodeParams cp = {};
@@ -412,7 +428,7 @@ int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, con
         L.mg = mg;
         build_loop(P, W, L, s);
     }
-    k_set<<<1, 1, 0, s>>>(L.state.as<PcgState>(), t, y);
+    launch_k(k_set, 1, 1, 0, s, L.state.as<PcgState>(), t, y);
     SIP_CHECK_LAUNCH();
     SIP_CUDA(cudaGraphLaunch(L.exec, s));
     SIP_CUDA(cudaMemcpyAsync(L.hs.p, L.state.ptr, sizeof(PcgState), cudaMemcpyDeviceToHost, s));

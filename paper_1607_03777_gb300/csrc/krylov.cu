@@ -32,6 +32,7 @@ __device__ __forceinline__ double block_sum(double v) {
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(size_t n, const T* __restrict__ V, size_t ldv,
                                                     const T* __restrict__ w, double* partial) {
+    grid_dep_wait();
     const T* x = V + blockIdx.y * ldv;
     double acc = 0.0;
     for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n; g += size_t(gridDim.x) * blockDim.x)
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(size_t n, const T*
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_final_sum(int parts, const double* partial, double* out) {
+    grid_dep_wait();
     double acc = 0.0;
     for (int i = threadIdx.x; i < parts; i += blockDim.x) acc += partial[blockIdx.x * parts + i];
     acc = block_sum(acc);
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(kRedThreads) k_final_sum(int parts, const doub
 template <typename T>
 __global__ void k_maxpy(int m, size_t n, const T* __restrict__ V, size_t ldv, const double* __restrict__ h,
                         double sign, T* w) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     double acc = 0.0;
@@ -62,6 +65,7 @@ __global__ void k_maxpy(int m, size_t n, const T* __restrict__ V, size_t ldv, co
 template <typename T>
 __global__ void k_pcg_update(size_t n, const T* __restrict__ d, const T* __restrict__ q, T* y, T* r,
                              const double* num, const double* den) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const T a = T(*num / *den);
@@ -72,6 +76,7 @@ __global__ void k_pcg_update(size_t n, const T* __restrict__ d, const T* __restr
 // d = z + (num / den) d
 template <typename T>
 __global__ void k_pcg_dir(size_t n, const T* __restrict__ z, T* d, const double* num, const double* den) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     d[g] = z[g] + T(*num / *den) * d[g];
@@ -79,6 +84,7 @@ __global__ void k_pcg_dir(size_t n, const T* __restrict__ z, T* d, const double*
 
 template <typename T>
 __global__ void k_axpby(size_t n, T a, const T* __restrict__ x, T b, T* y) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     y[g] = a * x[g] + (b == T(0) ? T(0) : b * y[g]);
@@ -87,24 +93,28 @@ __global__ void k_axpby(size_t n, T a, const T* __restrict__ x, T b, T* y) {
 // y = x * scale[i] (element-wise scale vector)
 template <typename T>
 __global__ void k_vmul(size_t n, const T* __restrict__ x, const T* __restrict__ s, T* y) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g < n) y[g] = x[g] * s[g];
 }
 
 template <typename Ti, typename To>
 __global__ void k_cast(size_t n, const Ti* __restrict__ a, To* __restrict__ b) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g < n) b[g] = To(a[g]);
 }
 
 // zero-mean projection of the constant pressure: subtract mean of p[e][0][0]
 __global__ void k_sub_mode0(size_t ne, int mp, double* p, const double* sum) {
+    grid_dep_wait();
     const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < ne) p[e * mp] -= *sum / double(ne);
 }
 
 template <typename T>
 __global__ void k_sum_mode0_partial(size_t ne, int mp, const T* __restrict__ p, double* partial) {
+    grid_dep_wait();
     double acc = 0.0;
     for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < ne; e += size_t(gridDim.x) * blockDim.x)
         acc += double(p[e * mp]);
@@ -123,9 +133,9 @@ void launch_mdot(int m, size_t n, const T* V, size_t ldv, const T* w, double* ou
                  cudaStream_t s) {
     if (m <= 0) return;
     dim3 grid(kRedBlocks, m);
-    k_mdot_partial<T><<<grid, kRedThreads, 0, s>>>(n, V, ldv, w, ws);
+    launch_k(k_mdot_partial<T>, grid, kRedThreads, 0, s, n, V, ldv, w, ws);
     SIP_CHECK_LAUNCH();
-    k_final_sum<<<m, kRedThreads, 0, s>>>(kRedBlocks, ws, out);
+    launch_k(k_final_sum, m, kRedThreads, 0, s, kRedBlocks, ws, out);
     SIP_CHECK_LAUNCH();
 }
 
@@ -138,48 +148,48 @@ template <typename T>
 void launch_maxpy(int m, size_t n, const T* V, size_t ldv, const double* h, double sign, T* w,
                   cudaStream_t s) {
     if (m <= 0) return;
-    k_maxpy<T><<<nblk(n), 256, 0, s>>>(m, n, V, ldv, h, sign, w);
+    launch_k(k_maxpy<T>, nblk(n), 256, 0, s, m, n, V, ldv, h, sign, w);
     SIP_CHECK_LAUNCH();
 }
 
 template <typename T>
 void launch_pcg_update(size_t n, const T* d, const T* q, T* y, T* r, const double* num,
                        const double* den, cudaStream_t s) {
-    k_pcg_update<T><<<nblk(n), 256, 0, s>>>(n, d, q, y, r, num, den);
+    launch_k(k_pcg_update<T>, nblk(n), 256, 0, s, n, d, q, y, r, num, den);
     SIP_CHECK_LAUNCH();
 }
 
 template <typename T>
 void launch_pcg_dir(size_t n, const T* z, T* d, const double* num, const double* den,
                     cudaStream_t s) {
-    k_pcg_dir<T><<<nblk(n), 256, 0, s>>>(n, z, d, num, den);
+    launch_k(k_pcg_dir<T>, nblk(n), 256, 0, s, n, z, d, num, den);
     SIP_CHECK_LAUNCH();
 }
 
 template <typename T>
 void launch_axpby(size_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
-    k_axpby<T><<<nblk(n), 256, 0, s>>>(n, a, x, b, y);
+    launch_k(k_axpby<T>, nblk(n), 256, 0, s, n, a, x, b, y);
     SIP_CHECK_LAUNCH();
 }
 
 template <typename T>
 void launch_vmul(size_t n, const T* x, const T* sc, T* y, cudaStream_t s) {
-    k_vmul<T><<<nblk(n), 256, 0, s>>>(n, x, sc, y);
+    launch_k(k_vmul<T>, nblk(n), 256, 0, s, n, x, sc, y);
     SIP_CHECK_LAUNCH();
 }
 
 template <typename Ti, typename To>
 void launch_cast(size_t n, const Ti* a, To* b, cudaStream_t s) {
-    k_cast<Ti, To><<<nblk(n), 256, 0, s>>>(n, a, b);
+    launch_k(k_cast<Ti, To>, nblk(n), 256, 0, s, n, a, b);
     SIP_CHECK_LAUNCH();
 }
 
 void launch_zero_mean_pressure(size_t ne, int mp, double* p, double* ws, cudaStream_t s) {
-    k_sum_mode0_partial<double><<<kRedBlocks, kRedThreads, 0, s>>>(ne, mp, p, ws);
+    launch_k(k_sum_mode0_partial<double>, kRedBlocks, kRedThreads, 0, s, ne, mp, p, ws);
     SIP_CHECK_LAUNCH();
-    k_final_sum<<<1, kRedThreads, 0, s>>>(kRedBlocks, ws, ws + kRedBlocks);
+    launch_k(k_final_sum, 1, kRedThreads, 0, s, kRedBlocks, ws, ws + kRedBlocks);
     SIP_CHECK_LAUNCH();
-    k_sub_mode0<<<nblk(ne), 256, 0, s>>>(ne, mp, p, ws + kRedBlocks);
+    launch_k(k_sub_mode0, nblk(ne), 256, 0, s, ne, mp, p, ws + kRedBlocks);
     SIP_CHECK_LAUNCH();
 }
 

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sipstokes.h"
@@ -31,6 +32,44 @@ struct Error : std::runtime_error {
 // Host-side count of kernel launches issued by the library (each launcher
 // ends with SIP_CHECK_LAUNCH); graph replays add their captured kernel count.
 int64_t& launch_counter();
+
+// Programmatic dependent launch.  Kernels are launched with programmatic
+// stream serialisation (when enabled), so the next kernel of a chain is
+// scheduled while the previous one drains; every kernel starts with
+// grid_dep_wait(), which returns once the preceding grid has completed and
+// its memory is visible, so the stream order of the data is unchanged and
+// only launch latency overlaps.  SIP_PDL=0 launches plainly; the flag is
+// also cleared while capturing graph bodies of conditional nodes.
+__device__ __forceinline__ void grid_dep_wait() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+bool& pdl_enabled();
+
+struct PdlOffScope {
+    bool prev;
+    PdlOffScope() : prev(pdl_enabled()) { pdl_enabled() = false; }
+    ~PdlOffScope() { pdl_enabled() = prev; }
+};
+
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) throw Error(SIP_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
 
 #define SIP_CHECK_LAUNCH()                  \
     do {                                    \

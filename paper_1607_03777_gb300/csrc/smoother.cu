@@ -82,6 +82,7 @@ __device__ double block_entry(int r, int s, double etaK, const int kind[4], cons
 // elimination (SPD: no pivoting needed), store M^{-1} as T.
 template <int N, typename T>
 __global__ void __launch_bounds__(256) k_build_blocks(const BlockArgs<N> a, T* out) {
+    grid_dep_wait();
     constexpr int NB = 2 * N * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* M = reinterpret_cast<double*>(smem_raw);
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(256) k_build_blocks(const BlockArgs<N> a, T* o
 // unique list (order by atomic ticket; results do not depend on it).
 __global__ void k_classify(int nx, int ny, const double* eta, int* emap, int* uniq_list,
                            int* n_uniq) {
+    grid_dep_wait();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nx * ny) return;
     const int ex = e % nx, ey = e / nx;
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
                                                   const T* __restrict__ uniq_inv,
                                                   const T* __restrict__ eta_inv, T c1, T c2,
                                                   int x_zero) {
+    grid_dep_wait();
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     __shared__ T sr[EB * NB];
@@ -233,7 +236,7 @@ void build_blocks_n(const OpGeom& g, const int* spec, int count, const double* e
     const size_t smem = size_t(NB) * NB * sizeof(double);
     SIP_CUDA(cudaFuncSetAttribute(k_build_blocks<N, T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    k_build_blocks<N, T><<<count, 256, smem, s>>>(make_block_args<N>(g, spec, eta), out);
+    launch_k(k_build_blocks<N, T>, count, 256, smem, s, make_block_args<N>(g, spec, eta), out);
     SIP_CHECK_LAUNCH();
 }
 
@@ -244,7 +247,7 @@ void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     const int blocks = (ne + EB - 1) / EB;
-    k_bj_apply<N, T><<<blocks, 256, 0, s>>>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta,
+    launch_k(k_bj_apply<N, T>, blocks, 256, 0, s, ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta,
                                             c1, c2, x_zero ? 1 : 0);
     SIP_CHECK_LAUNCH();
 }
@@ -254,7 +257,7 @@ void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_
 void launch_classify(int nx, int ny, const double* eta, int* emap, int* uniq_list, int* n_uniq,
                      cudaStream_t s) {
     const int ne = nx * ny;
-    k_classify<<<(ne + 255) / 256, 256, 0, s>>>(nx, ny, eta, emap, uniq_list, n_uniq);
+    launch_k(k_classify, (ne + 255) / 256, 256, 0, s, nx, ny, eta, emap, uniq_list, n_uniq);
     SIP_CHECK_LAUNCH();
 }
 

@@ -27,9 +27,18 @@ bool& release_on_legacy() {
     return on;
 }
 
+bool& pdl_enabled() {
+    static thread_local bool on = [] {
+        const char* v = std::getenv("SIP_PDL");
+        return !(v && std::string(v) == "0");
+    }();
+    return on;
+}
+
 namespace {
 
 __global__ void k_splitmix(size_t n, uint64_t seed, double* out) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based hash
@@ -76,12 +85,13 @@ inline double read_scalar(const double* dev, double* host, cudaStream_t s) {
 }  // namespace
 
 void launch_splitmix_uniform(size_t n, uint64_t seed, double* out, cudaStream_t s) {
-    k_splitmix<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, seed, out);
+    launch_k(k_splitmix, unsigned((n + 255) / 256), 256, 0, s, n, seed, out);
     SIP_CHECK_LAUNCH();
 }
 
 namespace {
 __global__ void k_check_positive(size_t n, const double* v, int* bad) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g < n && !(isfinite(v[g]) && v[g] > 0.0)) atomicOr(bad, 1);
 }
@@ -91,7 +101,7 @@ bool eta_valid(size_t n, const double* eta, cudaStream_t s) {
     DeviceBuffer flag;
     flag.alloc(sizeof(int));
     SIP_CUDA(cudaMemsetAsync(flag.ptr, 0, sizeof(int), s));
-    k_check_positive<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, eta, flag.as<int>());
+    launch_k(k_check_positive, unsigned((n + 255) / 256), 256, 0, s, n, eta, flag.as<int>());
     SIP_CHECK_LAUNCH();
     int bad = 0;
     SIP_CUDA(cudaMemcpyAsync(&bad, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -873,6 +883,7 @@ int64_t Workspace::bytes() const {
 namespace {
 
 __global__ void k_sinv(size_t ne, int mp, double area_quarter, const double* eta, double* out) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g < ne * mp) out[g] = -eta[g / mp] / area_quarter;
 }
@@ -914,7 +925,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         // complement -B^T A^{-1} B, approximated by -S*, S* = the pressure mass
         // (h_x h_y / 4 on the orthonormal basis) scaled by 1/eta_K; stored
         // here as the diagonal of its inverse, -eta_K / (h_x h_y / 4)
-        k_sinv<<<unsigned((n_p + 255) / 256), 256, 0, s>>>(
+        launch_k(k_sinv, unsigned((n_p + 255) / 256), 256, 0, s, 
             size_t(P->ne), P->mp, 0.25 * P->geom.hx * P->geom.hy, P->eta_d.as<double>(),
             W.sinv.as<double>());
         SIP_CHECK_LAUNCH();
@@ -1119,6 +1130,7 @@ int64_t sip_problem::device_bytes() const {
 
 namespace {
 __global__ void k_derive_eta(size_t n, const double* eta, float* ef, double* inv, float* invf) {
+    sip::grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const double e = eta[g];
@@ -1133,9 +1145,8 @@ void sip_problem::derive_eta(cudaStream_t s) {
     eta_f.alloc(n * sizeof(float));
     eta_inv_d.alloc(n * sizeof(double));
     eta_inv_f.alloc(n * sizeof(float));
-    k_derive_eta<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, eta_d.as<double>(), eta_f.as<float>(),
-                                                         eta_inv_d.as<double>(),
-                                                         eta_inv_f.as<float>());
+    sip::launch_k(k_derive_eta, unsigned((n + 255) / 256), 256, 0, s, n, eta_d.as<double>(),
+                  eta_f.as<float>(), eta_inv_d.as<double>(), eta_inv_f.as<float>());
     SIP_CHECK_LAUNCH();
 }
 

@@ -19,6 +19,7 @@ constexpr double kInvSqrt6 = 0.40824829046386301637;   // |int L_p l_1|
 
 template <typename T>
 __global__ void k_p_restrict(size_t ne, int N, const T* __restrict__ r, T* __restrict__ r1) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= ne * 8) return;
     const size_t e = g / 8;
@@ -28,6 +29,7 @@ __global__ void k_p_restrict(size_t ne, int N, const T* __restrict__ r, T* __res
 
 template <typename T>
 __global__ void k_p_prolong_add(size_t ne, int N, const T* __restrict__ e1, T* __restrict__ y) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= ne * 8) return;
     const size_t e = g / 8;
@@ -43,6 +45,7 @@ __device__ __forceinline__ double hatw(int i, int p) {
 
 template <typename T>
 __global__ void k_pcd(int nx, int ny, const T* __restrict__ v, T* __restrict__ out) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t ne = size_t(nx) * ny;
     if (g >= ne * 8) return;
@@ -58,6 +61,7 @@ __global__ void k_pcd(int nx, int ny, const T* __restrict__ v, T* __restrict__ o
 
 template <typename T>
 __global__ void k_rdc(int nx, int ny, const T* __restrict__ r, T* __restrict__ out) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t nv = size_t(nx + 1) * (ny + 1);
     if (g >= nv * 2) return;
@@ -128,6 +132,7 @@ bool pair_aligned(const T* p) {
 template <typename T, bool VEC>
 __global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ x,
                                 T* __restrict__ y, T alpha, const T* __restrict__ z, T beta) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t nv = size_t(nvx) * nvy;
     if (g >= nv * 2) return;
@@ -142,6 +147,7 @@ __global__ void k_stencil_apply(int nvx, int nvy, const T* __restrict__ S, const
 
 template <typename T>
 __global__ void k_stencil_dinv(size_t nv, const T* __restrict__ S, T* __restrict__ dinv) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= nv * 2) return;
     const int c = int(g % 2);
@@ -152,6 +158,7 @@ __global__ void k_stencil_dinv(size_t nv, const T* __restrict__ S, T* __restrict
 template <typename T>
 __global__ void k_jacobi_cheb(size_t n, const T* __restrict__ r, const T* __restrict__ dinv, T* d,
                               T* x, T c1, T c2, int x_zero) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     T v = c2 * dinv[g] * r[g];
@@ -164,6 +171,7 @@ __global__ void k_jacobi_cheb(size_t n, const T* __restrict__ r, const T* __rest
 template <typename T>
 __global__ void k_hcheb_first(size_t n, const T* __restrict__ b, const T* __restrict__ dinv,
                               T* __restrict__ r, T* __restrict__ d, T* __restrict__ x, T c2) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const T bv = b[g];
@@ -180,6 +188,7 @@ template <typename T, bool VEC>
 __global__ void k_hcheb_start(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
                               const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
                               T* __restrict__ d, T c2) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t nv = size_t(nvx) * nvy;
     if (g >= nv * 2) return;
@@ -200,6 +209,7 @@ template <typename T, bool VEC>
 __global__ void k_hcheb_step(int nvx, int nvy, const T* __restrict__ S, const T* __restrict__ dinv,
                              T* __restrict__ r, const T* __restrict__ d_old, T* __restrict__ d_new,
                              T* __restrict__ x, T c1, T c2, int pend) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t nv = size_t(nvx) * nvy;
     if (g >= nv * 2) return;
@@ -217,6 +227,7 @@ __global__ void k_hcheb_step(int nvx, int nvy, const T* __restrict__ S, const T*
 // fine (2 nxc + 1)^2 <- coarse (nxc + 1)^2 vertex grid, bilinear (add to y)
 template <typename T>
 __global__ void k_ph_add(int nxc, int nyc, const T* __restrict__ xc, T* __restrict__ yf) {
+    grid_dep_wait();
     const int nfx = 2 * nxc + 1, nfy = 2 * nyc + 1;
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= size_t(nfx) * nfy * 2) return;
@@ -242,6 +253,7 @@ __global__ void k_ph_add(int nxc, int nyc, const T* __restrict__ xc, T* __restri
 // R_h = P_h^T: coarse vertex gathers fine vertices 2I-1 .. 2I+1 with weights 1/2, 1, 1/2
 template <typename T>
 __global__ void k_rh(int nxc, int nyc, const T* __restrict__ rf, T* __restrict__ rc) {
+    grid_dep_wait();
     const int nfx = 2 * nxc + 1, nfy = 2 * nyc + 1;
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= size_t(nxc + 1) * (nyc + 1) * 2) return;
@@ -266,6 +278,7 @@ __global__ void k_rh(int nxc, int nyc, const T* __restrict__ rf, T* __restrict__
 // probe vector: 1 on vertices of colour (vx % 3, vy % 3) == (col % 3, col / 3), component cp
 template <typename T>
 __global__ void k_probe_vertices(int nvx, int nvy, int col, int cp, T* x) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= size_t(nvx) * nvy * 2) return;
     const int c = int(g % 2);
@@ -277,6 +290,7 @@ __global__ void k_probe_vertices(int nvx, int nvy, int col, int cp, T* x) {
 // S[v][t][c][cp] from the 18 probe results Y[col*2 + cp][v][c]
 template <typename T>
 __global__ void k_extract_stencil(int nvx, int nvy, const T* __restrict__ Y, T* __restrict__ S) {
+    grid_dep_wait();
     const size_t nv = size_t(nvx) * nvy;
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= nv * 36) return;
@@ -296,6 +310,7 @@ __global__ void k_extract_stencil(int nvx, int nvy, const T* __restrict__ Y, T* 
 // colour (ex % 3, ey % 3) == (col % 3, col / 3)
 template <typename T>
 __global__ void k_probe_elements(int nx, int ny, int col, int l, T* x) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= size_t(nx) * ny * 8) return;
     const size_t e = g / 8;
@@ -306,6 +321,7 @@ __global__ void k_probe_elements(int nx, int ny, int col, int l, T* x) {
 // y = M x for a dense symmetric n x n matrix (row-major); one warp per row
 template <typename T>
 __global__ void k_dense_symv(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
+    grid_dep_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
     if (warp >= n) return;
     const T* row = M + size_t(warp) * n;
@@ -318,6 +334,7 @@ __global__ void k_dense_symv(int n, const T* __restrict__ M, const T* __restrict
 // Dense inverse from a banded Cholesky factor L (lower, band width bw,
 // stored L[i][bw-1-(i-j)] for i-bw < j <= i): thread = column of the inverse.
 __global__ void k_band_chol_inverse(int n, int bw, const double* __restrict__ L, double* X) {
+    grid_dep_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= n) return;
     double* x = X + size_t(col) * n;   // column col of X, stored as a row (X symmetric)
@@ -337,6 +354,7 @@ __global__ void k_band_chol_inverse(int n, int bw, const double* __restrict__ L,
 
 template <typename T>
 __global__ void k_convert(size_t n, const double* __restrict__ a, T* __restrict__ b) {
+    grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g < n) b[g] = T(a[g]);
 }
@@ -347,22 +365,22 @@ inline unsigned nblk(size_t n, int t = 256) { return unsigned((n + t - 1) / t); 
 
 template <typename T>
 void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s) {
-    k_p_restrict<T><<<nblk(ne * 8), 256, 0, s>>>(ne, N, r, r1);
+    launch_k(k_p_restrict<T>, nblk(ne * 8), 256, 0, s, ne, N, r, r1);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s) {
-    k_p_prolong_add<T><<<nblk(ne * 8), 256, 0, s>>>(ne, N, e1, y);
+    launch_k(k_p_prolong_add<T>, nblk(ne * 8), 256, 0, s, ne, N, e1, y);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_pcd(int nx, int ny, const T* v, T* out, cudaStream_t s) {
-    k_pcd<T><<<nblk(size_t(nx) * ny * 8), 256, 0, s>>>(nx, ny, v, out);
+    launch_k(k_pcd<T>, nblk(size_t(nx) * ny * 8), 256, 0, s, nx, ny, v, out);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_rdc(int nx, int ny, const T* r, T* out, cudaStream_t s) {
-    k_rdc<T><<<nblk(size_t(nx + 1) * (ny + 1) * 2), 256, 0, s>>>(nx, ny, r, out);
+    launch_k(k_rdc<T>, nblk(size_t(nx + 1) * (ny + 1) * 2), 256, 0, s, nx, ny, r, out);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -370,26 +388,26 @@ void launch_stencil_apply(int nvx, int nvy, const T* S, const T* x, T* y, T alph
                           T beta, cudaStream_t s) {
     const unsigned nb = nblk(size_t(nvx) * nvy * 2);
     if (pair_aligned(S) && pair_aligned(x))
-        k_stencil_apply<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
+        launch_k(k_stencil_apply<T, true>, nb, 256, 0, s, nvx, nvy, S, x, y, alpha, z, beta);
     else
-        k_stencil_apply<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, x, y, alpha, z, beta);
+        launch_k(k_stencil_apply<T, false>, nb, 256, 0, s, nvx, nvy, S, x, y, alpha, z, beta);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_stencil_dinv(size_t nv, const T* S, T* dinv, cudaStream_t s) {
-    k_stencil_dinv<T><<<nblk(nv * 2), 256, 0, s>>>(nv, S, dinv);
+    launch_k(k_stencil_dinv<T>, nblk(nv * 2), 256, 0, s, nv, S, dinv);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_jacobi_cheb(size_t n, const T* r, const T* dinv, T* d, T* x, T c1, T c2, bool x_zero,
                         cudaStream_t s) {
-    k_jacobi_cheb<T><<<nblk(n), 256, 0, s>>>(n, r, dinv, d, x, c1, c2, x_zero ? 1 : 0);
+    launch_k(k_jacobi_cheb<T>, nblk(n), 256, 0, s, n, r, dinv, d, x, c1, c2, x_zero ? 1 : 0);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_hcheb_first(size_t n, const T* b, const T* dinv, T* r, T* d, T* x, T c2,
                         cudaStream_t s) {
-    k_hcheb_first<T><<<nblk(n), 256, 0, s>>>(n, b, dinv, r, d, x, c2);
+    launch_k(k_hcheb_first<T>, nblk(n), 256, 0, s, n, b, dinv, r, d, x, c2);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -397,9 +415,9 @@ void launch_hcheb_start(int nvx, int nvy, const T* S, const T* dinv, const T* b,
                         T* d, T c2, cudaStream_t s) {
     const unsigned nb = nblk(size_t(nvx) * nvy * 2);
     if (pair_aligned(S) && pair_aligned(x))
-        k_hcheb_start<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, b, x, r, d, c2);
+        launch_k(k_hcheb_start<T, true>, nb, 256, 0, s, nvx, nvy, S, dinv, b, x, r, d, c2);
     else
-        k_hcheb_start<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, b, x, r, d, c2);
+        launch_k(k_hcheb_start<T, false>, nb, 256, 0, s, nvx, nvy, S, dinv, b, x, r, d, c2);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -407,50 +425,50 @@ void launch_hcheb_step(int nvx, int nvy, const T* S, const T* dinv, T* r, const 
                        T* d_new, T* x, T c1, T c2, bool pend, cudaStream_t s) {
     const unsigned nb = nblk(size_t(nvx) * nvy * 2);
     if (pair_aligned(S) && pair_aligned(d_old))
-        k_hcheb_step<T, true><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
+        launch_k(k_hcheb_step<T, true>, nb, 256, 0, s, nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
                                                  pend ? 1 : 0);
     else
-        k_hcheb_step<T, false><<<nb, 256, 0, s>>>(nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
+        launch_k(k_hcheb_step<T, false>, nb, 256, 0, s, nvx, nvy, S, dinv, r, d_old, d_new, x, c1, c2,
                                                   pend ? 1 : 0);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_ph_add(int nxc, int nyc, const T* xc, T* yf, cudaStream_t s) {
-    k_ph_add<T><<<nblk(size_t(2 * nxc + 1) * (2 * nyc + 1) * 2), 256, 0, s>>>(nxc, nyc, xc, yf);
+    launch_k(k_ph_add<T>, nblk(size_t(2 * nxc + 1) * (2 * nyc + 1) * 2), 256, 0, s, nxc, nyc, xc, yf);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_rh(int nxc, int nyc, const T* rf, T* rc, cudaStream_t s) {
-    k_rh<T><<<nblk(size_t(nxc + 1) * (nyc + 1) * 2), 256, 0, s>>>(nxc, nyc, rf, rc);
+    launch_k(k_rh<T>, nblk(size_t(nxc + 1) * (nyc + 1) * 2), 256, 0, s, nxc, nyc, rf, rc);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_probe_vertices(int nvx, int nvy, int col, int cp, T* x, cudaStream_t s) {
-    k_probe_vertices<T><<<nblk(size_t(nvx) * nvy * 2), 256, 0, s>>>(nvx, nvy, col, cp, x);
+    launch_k(k_probe_vertices<T>, nblk(size_t(nvx) * nvy * 2), 256, 0, s, nvx, nvy, col, cp, x);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_extract_stencil(int nvx, int nvy, const T* Y, T* S, cudaStream_t s) {
-    k_extract_stencil<T><<<nblk(size_t(nvx) * nvy * 36), 256, 0, s>>>(nvx, nvy, Y, S);
+    launch_k(k_extract_stencil<T>, nblk(size_t(nvx) * nvy * 36), 256, 0, s, nvx, nvy, Y, S);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_probe_elements(int nx, int ny, int col, int l, T* x, cudaStream_t s) {
-    k_probe_elements<T><<<nblk(size_t(nx) * ny * 8), 256, 0, s>>>(nx, ny, col, l, x);
+    launch_k(k_probe_elements<T>, nblk(size_t(nx) * ny * 8), 256, 0, s, nx, ny, col, l, x);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_dense_symv(int n, const T* M, const T* x, T* y, cudaStream_t s) {
-    k_dense_symv<T><<<nblk(size_t(n) * 32, 128), 128, 0, s>>>(n, M, x, y);
+    launch_k(k_dense_symv<T>, nblk(size_t(n) * 32, 128), 128, 0, s, n, M, x, y);
     SIP_CHECK_LAUNCH();
 }
 void launch_band_chol_inverse(int n, int bw, const double* L, double* X, cudaStream_t s) {
-    k_band_chol_inverse<<<nblk(n, 32), 32, 0, s>>>(n, bw, L, X);
+    launch_k(k_band_chol_inverse, nblk(n, 32), 32, 0, s, n, bw, L, X);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
 void launch_convert(size_t n, const double* a, T* b, cudaStream_t s) {
-    k_convert<T><<<nblk(n), 256, 0, s>>>(n, a, b);
+    launch_k(k_convert<T>, nblk(n), 256, 0, s, n, a, b);
     SIP_CHECK_LAUNCH();
 }
 
