@@ -82,6 +82,15 @@ __global__ void k_pcg_dir(size_t n, const T* __restrict__ z, T* d, const double*
     d[g] = z[g] + T(*num / *den) * d[g];
 }
 
+// v = v / sqrt(*s2) (the scale rounded to T, as a host-side axpby would)
+template <typename T>
+__global__ void k_scale_inv_sqrt(size_t n, const double* __restrict__ s2, T* v) {
+    grid_dep_wait();
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    v[g] = T(1.0 / sqrt(*s2)) * v[g];
+}
+
 template <typename T>
 __global__ void k_axpby(size_t n, T a, const T* __restrict__ x, T b, T* y) {
     grid_dep_wait();
@@ -167,6 +176,12 @@ void launch_pcg_dir(size_t n, const T* z, T* d, const double* num, const double*
 }
 
 template <typename T>
+void launch_scale_inv_sqrt(size_t n, const double* s2, T* v, cudaStream_t s) {
+    launch_k(k_scale_inv_sqrt<T>, nblk(n), 256, 0, s, n, s2, v);
+    SIP_CHECK_LAUNCH();
+}
+
+template <typename T>
 void launch_axpby(size_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
     launch_k(k_axpby<T>, nblk(n), 256, 0, s, n, a, x, b, y);
     SIP_CHECK_LAUNCH();
@@ -204,6 +219,7 @@ void launch_zero_mean_pressure(size_t ne, int mp, double* p, double* ws, cudaStr
     template void launch_pcg_dir<T>(size_t, const T*, T*, const double*, const double*,         \
                                     cudaStream_t);                                               \
     template void launch_axpby<T>(size_t, T, const T*, T, T*, cudaStream_t);                    \
+    template void launch_scale_inv_sqrt<T>(size_t, const double*, T*, cudaStream_t);             \
     template void launch_vmul<T>(size_t, const T*, const T*, T*, cudaStream_t);
 SIP_INST(double)
 SIP_INST(float)

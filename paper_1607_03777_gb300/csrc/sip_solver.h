@@ -67,6 +67,7 @@ template <typename T>
 void launch_pcg_dir(size_t n, const T* z, T* d, const double* num, const double* den,
                     cudaStream_t s);
 template <typename T> void launch_axpby(size_t n, T a, const T* x, T b, T* y, cudaStream_t s);
+template <typename T> void launch_scale_inv_sqrt(size_t n, const double* s2, T* v, cudaStream_t s);
 template <typename T> void launch_vmul(size_t n, const T* x, const T* sc, T* y, cudaStream_t s);
 template <typename Ti, typename To> void launch_cast(size_t n, const Ti* a, To* b, cudaStream_t s);
 void launch_zero_mean_pressure(size_t ne, int mp, double* p, double* ws, cudaStream_t s);

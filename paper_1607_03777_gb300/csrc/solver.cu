@@ -314,9 +314,60 @@ void Multigrid<T>::bj(const T* r, T* z, cudaStream_t s) {
                        eta_inv_of<T>(P), T(0), T(1), true, s);
 }
 
-// Arnoldi (GMRES) estimate of the largest eigenvalue of M^{-1} A (Sec. 6):
-// m steps from M^{-1} b, b = SplitMix64 stream `seed`; classical Gram-Schmidt
-// applied twice; largest real part of the Hessenberg eigenvalues.
+// Arnoldi (GMRES) estimate of the largest eigenvalue of the preconditioned
+// operator (Sec. 6): m steps from the normalised start vector V[0];
+// classical Gram-Schmidt applied twice; largest real part of the Hessenberg
+// eigenvalues.  Every step stays on the device (the projections and norms
+// land in device memory, the normalisation divides by a device scalar); the
+// Hessenberg matrix is read back once at the end, where the first
+// (near-)breakdown truncates it exactly as a step-by-step loop would stop.
+// `op(v, w)` writes w = M^{-1} A v.
+namespace {
+template <typename T, class Op>
+double arnoldi_lmax(size_t n, int m, T* Vp, DeviceBuffer& hbuf, double* ws, HostScalars& hs,
+                    Op op, cudaStream_t s) {
+    // device layout: pass-1 projections [m][m+1], pass-2 projections [m][m+1],
+    // squared norms [m + 1] (slot m: the start vector)
+    const size_t np = size_t(m) * (m + 1);
+    hbuf.alloc((2 * np + m + 1) * sizeof(double));
+    double* H1 = hbuf.as<double>();
+    double* H2 = H1 + np;
+    double* Hn = H2 + np;
+    launch_dot<T>(n, Vp, Vp, Hn + m, ws, s);
+    launch_scale_inv_sqrt<T>(n, Hn + m, Vp, s);
+    for (int j = 0; j < m; ++j) {
+        T* w = Vp + size_t(j + 1) * n;
+        op(Vp + size_t(j) * n, w);
+        launch_mdot<T>(j + 1, n, Vp, n, w, H1 + size_t(j) * (m + 1), ws, s);
+        launch_maxpy<T>(j + 1, n, Vp, n, H1 + size_t(j) * (m + 1), -1.0, w, s);
+        launch_mdot<T>(j + 1, n, Vp, n, w, H2 + size_t(j) * (m + 1), ws, s);
+        launch_maxpy<T>(j + 1, n, Vp, n, H2 + size_t(j) * (m + 1), -1.0, w, s);
+        launch_dot<T>(n, w, w, Hn + j, ws, s);
+        if (j + 1 < m) launch_scale_inv_sqrt<T>(n, Hn + j, w, s);
+    }
+    std::vector<double> hh(2 * np + m + 1);
+    SIP_CUDA(cudaMemcpyAsync(hh.data(), H1, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SIP_CUDA(cudaStreamSynchronize(s));
+    (void)hs;
+    std::vector<double> H(size_t(m + 1) * m, 0.0);
+    int size = m;
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i <= j; ++i)
+            H[size_t(i) * m + j] = hh[size_t(j) * (m + 1) + i] + hh[np + size_t(j) * (m + 1) + i];
+        const double hn = std::sqrt(hh[2 * np + j]);
+        if (j + 1 < m) H[size_t(j + 1) * m + j] = hn;
+        if (!(hn > 1e-14 * std::abs(H[size_t(j) * m + j]))) {
+            size = j + 1;
+            break;
+        }
+    }
+    std::vector<double> Hs(size_t(size) * size);
+    for (int i = 0; i < size; ++i)
+        for (int j = 0; j < size; ++j) Hs[size_t(i) * size + j] = H[size_t(i) * m + j];
+    return hessenberg_max_real_eig(Hs, size);
+}
+}  // namespace
+
 template <typename T>
 double Multigrid<T>::estimate_p(cudaStream_t s) {
     const int m = std::max(1, std::min<int>(P->desc.eig_iters, int(n_u)));
@@ -328,37 +379,13 @@ double Multigrid<T>::estimate_p(cudaStream_t s) {
     launch_splitmix_uniform(n_u, P->desc.seed, b64.as<double>(), s);
     launch_cast<double, T>(n_u, b64.as<double>(), tmp.template as<T>(), s);
     bj(tmp.template as<T>(), Vp, s);
-    std::vector<double> H(size_t(m + 1) * m, 0.0);
-    double* hp = hs.p;
-    launch_dot<T>(n_u, Vp, Vp, sc.as<double>(), ws.as<double>(), s);
-    double nrm = std::sqrt(read_scalar(sc.as<double>(), hp, s));
-    launch_axpby<T>(n_u, T(1.0 / nrm), Vp, T(0), Vp, s);
-    int size = m;
-    for (int j = 0; j < m; ++j) {
-        T* w = Vp + size_t(j + 1) * n_u;
-        launch_apply_sip<T>(N, P->geom, Vp + size_t(j) * n_u, tmp.template as<T>(), eta_of<T>(P), T(1), nullptr,
-                            T(0), s);
-        bj(tmp.template as<T>(), w, s);
-        for (int pass = 0; pass < 2; ++pass) {
-            launch_mdot<T>(j + 1, n_u, Vp, n_u, w, sc.as<double>(), ws.as<double>(), s);
-            launch_maxpy<T>(j + 1, n_u, Vp, n_u, sc.as<double>(), -1.0, w, s);
-            SIP_CUDA(cudaMemcpyAsync(hp, sc.ptr, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            SIP_CUDA(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] += hp[i];
-        }
-        launch_dot<T>(n_u, w, w, sc.as<double>(), ws.as<double>(), s);
-        const double hn = std::sqrt(read_scalar(sc.as<double>(), hp, s));
-        if (j + 1 < m) H[size_t(j + 1) * m + j] = hn;
-        if (!(hn > 1e-14 * std::abs(H[size_t(j) * m + j]))) {
-            size = j + 1;
-            break;
-        }
-        launch_axpby<T>(n_u, T(1.0 / hn), w, T(0), w, s);
-    }
-    std::vector<double> Hs(size_t(size) * size);
-    for (int i = 0; i < size; ++i)
-        for (int j = 0; j < size; ++j) Hs[size_t(i) * size + j] = H[size_t(i) * m + j];
-    return hessenberg_max_real_eig(Hs, size);
+    return arnoldi_lmax<T>(n_u, m, Vp, scr_t2, ws.as<double>(), hs,
+                           [&](const T* v, T* w) {
+                               launch_apply_sip<T>(N, P->geom, v, tmp.template as<T>(), eta_of<T>(P),
+                                                   T(1), nullptr, T(0), s);
+                               bj(tmp.template as<T>(), w, s);
+                           },
+                           s);
 }
 
 template <typename T>
@@ -374,37 +401,13 @@ double Multigrid<T>::estimate_h(int l, cudaStream_t s) {
     launch_splitmix_uniform(n, P->desc.seed + 1 + uint64_t(l), b64.as<double>(), s);
     launch_cast<double, T>(n, b64.as<double>(), tmp.template as<T>(), s);
     launch_vmul<T>(n, tmp.template as<T>(), L.dinv.template as<T>(), Vp, s);
-    std::vector<double> H(size_t(m + 1) * m, 0.0);
-    double* hp = hs.p;
-    launch_dot<T>(n, Vp, Vp, sc.as<double>(), ws.as<double>(), s);
-    double nrm = std::sqrt(read_scalar(sc.as<double>(), hp, s));
-    launch_axpby<T>(n, T(1.0 / nrm), Vp, T(0), Vp, s);
-    int size = m;
-    for (int j = 0; j < m; ++j) {
-        T* w = Vp + size_t(j + 1) * n;
-        launch_stencil_apply<T>(L.nvx, L.nvy, L.S.template as<T>(), Vp + size_t(j) * n, tmp.template as<T>(), T(1),
-                                nullptr, T(0), s);
-        launch_vmul<T>(n, tmp.template as<T>(), L.dinv.template as<T>(), w, s);
-        for (int pass = 0; pass < 2; ++pass) {
-            launch_mdot<T>(j + 1, n, Vp, n, w, sc.as<double>(), ws.as<double>(), s);
-            launch_maxpy<T>(j + 1, n, Vp, n, sc.as<double>(), -1.0, w, s);
-            SIP_CUDA(cudaMemcpyAsync(hp, sc.ptr, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            SIP_CUDA(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] += hp[i];
-        }
-        launch_dot<T>(n, w, w, sc.as<double>(), ws.as<double>(), s);
-        const double hn = std::sqrt(read_scalar(sc.as<double>(), hp, s));
-        if (j + 1 < m) H[size_t(j + 1) * m + j] = hn;
-        if (!(hn > 1e-14 * std::abs(H[size_t(j) * m + j]))) {
-            size = j + 1;
-            break;
-        }
-        launch_axpby<T>(n, T(1.0 / hn), w, T(0), w, s);
-    }
-    std::vector<double> Hs(size_t(size) * size);
-    for (int i = 0; i < size; ++i)
-        for (int j = 0; j < size; ++j) Hs[size_t(i) * size + j] = H[size_t(i) * m + j];
-    return hessenberg_max_real_eig(Hs, size);
+    return arnoldi_lmax<T>(n, m, Vp, scr_t2, ws.as<double>(), hs,
+                           [&](const T* v, T* w) {
+                               launch_stencil_apply<T>(L.nvx, L.nvy, L.S.template as<T>(), v,
+                                                       tmp.template as<T>(), T(1), nullptr, T(0), s);
+                               launch_vmul<T>(n, tmp.template as<T>(), L.dinv.template as<T>(), w, s);
+                           },
+                           s);
 }
 
 template <typename T>

@@ -335,20 +335,23 @@ __global__ void k_dense_symv(int n, const T* __restrict__ M, const T* __restrict
 // stored L[i][bw-1-(i-j)] for i-bw < j <= i): thread = column of the inverse.
 __global__ void k_band_chol_inverse(int n, int bw, const double* __restrict__ L, double* X) {
     grid_dep_wait();
+    // column col of the inverse is kept as X[i][col] (X is symmetric), so the
+    // 32 columns of a warp are contiguous and every access is coalesced; the
+    // forward solve starts at row col (the entries above it are zero)
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= n) return;
-    double* x = X + size_t(col) * n;   // column col of X, stored as a row (X symmetric)
-    for (int i = 0; i < n; ++i) {      // L y = e_col
+    for (int i = 0; i < col; ++i) X[size_t(i) * n + col] = 0.0;
+    for (int i = col; i < n; ++i) {    // L y = e_col
         double s = (i == col) ? 1.0 : 0.0;
-        const int j0 = i - bw + 1 > 0 ? i - bw + 1 : 0;
-        for (int j = j0; j < i; ++j) s -= L[size_t(i) * bw + (bw - 1 - (i - j))] * x[j];
-        x[i] = s / L[size_t(i) * bw + (bw - 1)];
+        const int j0 = i - bw + 1 > col ? i - bw + 1 : col;
+        for (int j = j0; j < i; ++j) s -= L[size_t(i) * bw + (bw - 1 - (i - j))] * X[size_t(j) * n + col];
+        X[size_t(i) * n + col] = s / L[size_t(i) * bw + (bw - 1)];
     }
     for (int i = n - 1; i >= 0; --i) { // L^T x = y
-        double s = x[i];
+        double s = X[size_t(i) * n + col];
         const int j1 = i + bw - 1 < n - 1 ? i + bw - 1 : n - 1;
-        for (int j = i + 1; j <= j1; ++j) s -= L[size_t(j) * bw + (bw - 1 - (j - i))] * x[j];
-        x[i] = s / L[size_t(i) * bw + (bw - 1)];
+        for (int j = i + 1; j <= j1; ++j) s -= L[size_t(j) * bw + (bw - 1 - (j - i))] * X[size_t(j) * n + col];
+        X[size_t(i) * n + col] = s / L[size_t(i) * bw + (bw - 1)];
     }
 }
 
