@@ -15,54 +15,44 @@
 
 namespace sip {
 
-template <int N>
-struct ParityTabs {
-    static constexpr int NB = 2 * N * N;
-    int cls[NB];          // bit 0: x-parity, bit 1: y-parity of dof (c, j, i)
-    int cnt[3][4];        // symmetry type t = 1 (x), 2 (y), 3 (both): size of group g
-    int cols[3][4][NB];   // members of group g = cls & t, in dof order
-};
-
-template <int N>
-constexpr ParityTabs<N> build_parity() {
-    ParityTabs<N> p{};
-    constexpr int NB = 2 * N * N;
-    for (int q = 0; q < NB; ++q) {
-        const int c = q / (N * N), j = (q / N) % N, i = q % N;
-        p.cls[q] = ((i + (c == 0 ? 1 : 0)) & 1) | (((j + (c == 1 ? 1 : 0)) & 1) << 1);
-    }
-    for (int t = 1; t <= 3; ++t)
-        for (int g = 0; g < 4; ++g) {
-            int n = 0;
-            for (int q = 0; q < NB; ++q)
-                if ((p.cls[q] & t) == g) p.cols[t - 1][g][n++] = q;
-            p.cnt[t - 1][g] = n;
-        }
-    return p;
-}
-
-template <int N>
-__device__ constexpr ParityTabs<N> kParity = build_parity<N>();
-
 // Row `row` of M^{-1} r for one element block (NB x NB, symmetric, read by
 // columns so that lanes = rows coalesce); sym = symmetry type of the block
 // (0: none, dense).  Skipped entries are zero by the reflection symmetry.
+// The members of the row's parity group are enumerated arithmetically (no
+// table reads): mode (c, j, i) has x-parity (i + [c = x]) & 1, so for each
+// component the group's i (and, with the y-symmetry, j) run over one parity.
 template <int N, typename T>
 __device__ __forceinline__ T block_row_apply(const T* __restrict__ Minv, const T* rr, int row,
                                              int sym) {
-    constexpr int NB = 2 * N * N;
+    constexpr int NN = N * N;
+    constexpr int NB = 2 * NN;
     T acc = T(0);
     if (sym == 0) {
 #pragma unroll 8
         for (int q = 0; q < NB; ++q) acc += Minv[q * NB + row] * rr[q];
-    } else {
-        const int g = kParity<N>.cls[row] & sym;
-        const int n = kParity<N>.cnt[sym - 1][g];
-        const int* cols = kParity<N>.cols[sym - 1][g];
-#pragma unroll 4
-        for (int k = 0; k < n; ++k) {
-            const int q = cols[k];
-            acc += Minv[q * NB + row] * rr[q];
+        return acc;
+    }
+    const int cr = row / NN, jr = (row / N) % N, ir = row % N;
+    const int px = (ir + (cr == 0 ? 1 : 0)) & 1;
+    const int py = (jr + (cr == 1 ? 1 : 0)) & 1;
+    const bool sx = (sym & 1) != 0, sy = (sym & 2) != 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        // first i (j) of component c in the row's x- (y-) parity group
+        const int i0 = sx ? (px ^ (c == 0 ? 1 : 0)) : 0;
+        const int j0 = sy ? (py ^ (c == 1 ? 1 : 0)) : 0;
+        const int di = sx ? 2 : 1, dj = sy ? 2 : 1;
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            const int j = j0 + b * dj;
+            if (j >= N) break;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const int i = i0 + a * di;
+                if (i >= N) break;
+                const int q = c * NN + j * N + i;
+                acc += Minv[q * NB + row] * rr[q];
+            }
         }
     }
     return acc;
