@@ -48,6 +48,8 @@ def parse():
                     help="form timed by --profile-only")
     ap.add_argument("--profile-n", type=int, default=128,
                     help="mesh side of the --profile-only run (same physics)")
+    ap.add_argument("--profile-k", type=int, default=3,
+                    help="polynomial degree of the --profile-only run")
     ap.add_argument("--inner-loop", default="device", choices=["device", "host"],
                     help="inner PCG loop on the device (one graph launch per inner solve) or "
                          "driven from the host (for profilers that cannot see kernels inside "
@@ -158,7 +160,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     ctx = api.Context(dev.index)
     wl = synth.single_box_inclusion(
-        n=args.profile_n, n_hlevels=synth.levels_to_17(args.profile_n)) if args.profile_only \
+        n=args.profile_n, k=args.profile_k,
+        n_hlevels=synth.levels_to_17(args.profile_n)) if args.profile_only \
         else synth.single_box_inclusion()
     n, k = wl.nx, wl.k
     eta_d, rho_d = ctx.rasterise_inclusions(n, n, wl.shapes)
