@@ -1,4 +1,4 @@
-// Thread-per-element SIP apply for low degrees (N = k+1 <= 5).
+// Thread-per-element SIP apply for low degrees (N = k+1 <= 6).
 //
 // Same operator as k_apply_sip (eq. stiffness_form), organised so that the
 // arithmetic is minimal: one thread owns one element's 2 N^2 coefficients in
@@ -955,6 +955,7 @@ bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* et
         case 3: apply_elem_n<3, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
         case 4: apply_elem_n<4, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
         case 5: apply_elem_n<5, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
+        case 6: apply_elem_n<6, T>(g, x, y, eta, alpha, z, beta, split, s); return true;
         default: return false;
     }
 }

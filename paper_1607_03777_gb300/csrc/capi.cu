@@ -179,7 +179,7 @@ sip_status sip_problem_schedule(const sip_problem* p, int apply[2], int fused[2]
     for (int t = 0; t < 2; ++t) {
         if (apply) {
             const int v = p->geom.variant[t];
-            apply[t] = v != sip::APPLY_AUTO ? v : (p->n <= 5 ? int(sip::APPLY_ELEM2)
+            apply[t] = v != sip::APPLY_AUTO ? v : (p->n <= 6 ? int(sip::APPLY_ELEM2)
                                                              : int(sip::APPLY_TILE));
         }
         if (fused) fused[t] = (p->n <= 4 && p->geom.fused[t]) ? 1 : 0;

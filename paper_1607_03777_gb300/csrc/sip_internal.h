@@ -133,7 +133,7 @@ struct OpGeom {
     double hx, hy;
     int bc[4];
     double pen_x, pen_y;
-    int variant[2];   // ApplyVariant (APPLY_AUTO: component-split for N <= 5, else tile)
+    int variant[2];   // ApplyVariant (APPLY_AUTO: component-split for N <= 6, else tile)
     int fused[2];     // p-level smoother step fused into one launch (1) or not (0)
 };
 
@@ -158,7 +158,7 @@ inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], i
 template <typename T>
 void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                       const T* z, T beta, cudaStream_t s);
-// Thread-per-element variants for N <= 5 (split: two threads per element,
+// Thread-per-element variants for N <= 6 (split: two threads per element,
 // one per velocity component); returns false for other N.
 template <typename T>
 bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,

@@ -119,7 +119,7 @@ void tune_apply_t(sip_problem* P, cudaStream_t s) {
 }  // namespace
 
 void tune_apply(sip_problem* P, cudaStream_t s) {
-    if (!autotune_on() || P->n > 5) return;   // one kernel exists above degree 4
+    if (!autotune_on() || P->n > 6) return;   // one kernel exists above degree 5
     tune_apply_t<double>(P, s);
     if (P->desc.precision != SIP_PREC_FP64) tune_apply_t<float>(P, s);
 }

@@ -98,23 +98,26 @@ def test_server_queues_beyond_slots(ctx):
     srv.close()
 
 
-@pytest.mark.parametrize("k,precision", [(2, "fp64"), (3, "mixed"), (5, "fp64")])
+@pytest.mark.parametrize("k,precision", [(2, "fp64"), (3, "mixed"), (5, "fp64"), (6, "fp64")])
 def test_autotuned_schedule(ctx, k, precision):
     """The first set-up of a shape picks its kernels by timing; a second
     problem of the same shape reuses the choice; the schedule holds only
-    kernels that exist for the degree (degree > 3: the tile kernel, no fused
-    smoother)."""
+    kernels that exist for the degree (fused smoother steps up to degree 3,
+    element kernels up to degree 5, the tile kernel alone above)."""
     n = 48
     shapes = synth.jittered_sinkers(3, (2.0, 2.0))
     a = _alone(ctx, n, k, shapes, precision)
     b = _alone(ctx, n, k, shapes, precision)
     sa, sb = a[0].schedule(), b[0].schedule()
     assert sa == sb
-    if k <= 3:
+    if k <= 5:
         assert all(v in (1, 2, 3) for v in sa["apply"])
+    else:
+        assert sa["apply"] == [3, 3]
+    if k <= 3:
         assert all(v in (0, 1) for v in sa["fused"])
     else:
-        assert sa["apply"] == [3, 3] and sa["fused"] == [0, 0]
+        assert sa["fused"] == [0, 0]
     # same shape, same kernels: bit-identical solves
     assert torch.equal(a[2], b[2]) and torch.equal(a[3], b[3])
 
