@@ -183,33 +183,43 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
     grid_dep_wait();
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
+    static_assert(EB * NB <= 256, "one (element, row) per thread");
     __shared__ T sr[EB * NB];
+    __shared__ const T* s_minv[EB];
+    __shared__ T s_scale[EB];
+    __shared__ int s_sym[EB];
     const int e0 = blockIdx.x * EB;
     const int cnt = min(EB, ne - e0) * NB;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) sr[q] = r[size_t(e0) * NB + q];
-    __syncthreads();
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int el = q / NB, row = q % NB;
-        const int e = e0 + el;
+    // every load that does not depend on another is issued before the
+    // barrier: the residual block, the element's block pointer and scale,
+    // the previous direction and iterate
+    const int q = threadIdx.x;
+    const bool act = q < cnt;
+    const size_t o = size_t(e0) * NB + q;
+    if (act) sr[q] = r[o];
+    if (q < EB && e0 + q < ne) {
+        const int e = e0 + q;
         const int m = emap[e];
-        const T* Minv;
-        T scale;
-        int sym = 0;
         if (m < 0) {
-            Minv = cls_inv + size_t(-m - 1) * NB * NB;
-            scale = eta_inv[e];
-            if (cls_sym) sym = cls_sym[-m - 1];
+            s_minv[q] = cls_inv + size_t(-m - 1) * NB * NB;
+            s_scale[q] = eta_inv[e];
+            s_sym[q] = cls_sym ? cls_sym[-m - 1] : 0;
         } else {
-            Minv = uniq_inv + size_t(m) * NB * NB;
-            scale = T(1);
+            s_minv[q] = uniq_inv + size_t(m) * NB * NB;
+            s_scale[q] = T(1);
+            s_sym[q] = 0;
         }
-        const T acc = block_row_apply<N, T>(Minv, sr + el * NB, row, sym);
-        const size_t o = size_t(e) * NB + row;
-        T v = c2 * scale * acc;
-        if (c1 != T(0)) v += c1 * out[o];
-        out[o] = v;
-        if (x) x[o] = x_zero ? v : x[o] + v;
     }
+    const T out_old = (act && c1 != T(0)) ? out[o] : T(0);
+    const T x_old = (act && x && !x_zero) ? x[o] : T(0);
+    __syncthreads();
+    if (!act) return;
+    const int el = q / NB, row = q % NB;
+    const T acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el]);
+    T v = c2 * s_scale[el] * acc;
+    if (c1 != T(0)) v += c1 * out_old;
+    out[o] = v;
+    if (x) x[o] = x_zero ? v : x_old + v;
 }
 
 template <int N>
