@@ -199,7 +199,9 @@ class HLevel:
 
 
 class HierarchyQ1:
-    """Continuous bilinear h-hierarchy for A_1c (Sec. 6.1.2)."""
+    """Vertex-centred bilinear h-hierarchy: for A_1c on the mesh vertices
+    (Sec. 6.1.2), or for A_0 on the element centres (Sec. 6.1.1); nx x ny
+    intervals, 2 unknowns per vertex."""
 
     def __init__(self, A1c, nx, ny, n_coarsen, seed, steps=3):
         self.levels = []
@@ -226,12 +228,20 @@ class HierarchyQ1:
 
 
 class HPMultigrid:
-    """Algorithm 1 with the p-coarse space Q^2_1 (one cycle, y0 = 0).
+    """Algorithm 1 with the p-coarse space Q^2_1 or Q^2_0 (one cycle, y0 = 0).
 
-    n_hlevels = 0: coarse problem A_1 solved by LU  (A_p(Q^2_1));
-    n_hlevels > 0: coarse correction P_cd V_h(R_dc r) (A_hp(Q^2_1))."""
+    coarse = "q1": n_hlevels = 0: coarse problem A_1 solved by LU
+    (A_p(Q^2_1)); n_hlevels > 0: coarse correction P_cd V_h(R_dc r)
+    (A_hp(Q^2_1)).
+    coarse = "q0" (Sec. 6.1.1): the coarse space is the element-wise
+    constants, A_0 = P^T A P (a 5-point stencil per component); with
+    n_hlevels > 0 it is coarsened as a vertex grid of the element centres
+    (an odd number of elements per side), bilinear R_h = P_h^T, Galerkin
+    coarse operators, Chebyshev / point-Jacobi smoothing, LU at the
+    coarsest level (A_hp(Q^2_0)); n_hlevels = 0: LU of A_0 (A_p(Q^2_0))."""
 
-    def __init__(self, prob, A, n_hlevels, seed, p_steps=2, h_steps=3, blocks=None):
+    def __init__(self, prob, A, n_hlevels, seed, p_steps=2, h_steps=3, blocks=None,
+                 coarse="q1"):
         k, nb = prob.k, prob.num.nb
         self.A = A.tocsr()
         self.steps = p_steps
@@ -240,9 +250,19 @@ class HPMultigrid:
         self.inv_blocks = invert_blocks(blocks)
         self.Minv = lambda r: block_apply(self.inv_blocks, r)
         self.lmax = estimate_lambda_max(lambda v: self.A @ v, self.Minv, self.A.shape[0], seed)
+        self.coarse = coarse
+        self.n_hlevels = n_hlevels
+        if coarse == "q0":
+            self.P = p_prolongation(k, prob.num.ne, 0)
+            self.A0 = (self.P.T @ self.A @ self.P).tocsr()
+            if n_hlevels == 0:
+                self.coarse_lu = sla.lu_factor(self.A0.toarray())
+            else:
+                # element centres as the vertices of an (nx-1) x (ny-1) grid
+                self.h = HierarchyQ1(self.A0, prob.nx - 1, prob.ny - 1, n_hlevels, seed, h_steps)
+            return
         self.P = p_prolongation(k, prob.num.ne, 1)
         self.A1 = (self.P.T @ self.A @ self.P).tocsr()
-        self.n_hlevels = n_hlevels
         if n_hlevels == 0:
             self.coarse_lu = sla.lu_factor(self.A1.toarray())
         else:
@@ -257,6 +277,8 @@ class HPMultigrid:
     def coarse_solve(self, rc):
         if self.n_hlevels == 0:
             return sla.lu_solve(self.coarse_lu, rc)
+        if self.coarse == "q0":
+            return self.h.vcycle(rc)
         return self.Pcd @ self.h.vcycle(self.Pcd.T @ rc)
 
     def __call__(self, b):

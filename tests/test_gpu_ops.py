@@ -119,12 +119,14 @@ def test_rasterise_empty_list(ctx):
     assert (eta.cpu().numpy() == 2.0).all() and (rho.cpu().numpy() == 0.5).all()
 
 
-@pytest.mark.parametrize("n,k,dtype", [(128, 3, "f64"), (512, 4, "f32")])
+@pytest.mark.parametrize("n,k,dtype", [(128, 3, "f64"), (512, 4, "f32"), (512, 4, "f64"),
+                                       (256, 5, "f32"), (256, 5, "f64")])
 def test_apply_A_full_size_sampled(ctx, n, k, dtype):
     """Full-size operator (the single-inclusion 128^2 k=3 and the 512^2 k=4
-    many-disc workloads): sampled element rows rebuilt one by one by the
-    oracle, including corners, edges and elements at the viscosity jumps."""
-    wl = synth.single_box_inclusion() if n == 128 else synth.many_discs()
+    many-disc workloads, and a 256^2 k=5 inclusion mesh): sampled element
+    rows rebuilt one by one by the oracle, including corners, edges and
+    elements at the viscosity jumps."""
+    wl = synth.many_discs() if n == 512 else synth.single_box_inclusion(n=n, k=k)
     eta_d, _ = ctx.rasterise_inclusions(n, n, wl.shapes)
     eta = eta_d.cpu().numpy()
     prob = api.Problem(ctx, n, n, k, eta, bc=wl.bc)

@@ -509,3 +509,77 @@ def test_element_block_reflection_parity(k):
     # the inverse keeps the structure
     inv = np.linalg.inv(centre)
     assert np.abs(inv[~(same_x & same_y)]).max() <= 1e-12 * np.abs(inv).max()
+
+
+def _q0_closed_form(nx, ny, k, eta, bc, lx, ly):
+    """The SIP form restricted to element-wise constants, written out: on a
+    constant the strain vanishes, so only the penalty terms remain.  The
+    constant mode is l_0(x) l_0(y) = 1/2 on the reference square, so a face
+    of length h_t contributes sigma h_t / 4 per pair of traces;
+    sigma = 4 max(eta) (k+1)^2 / h_n inside, 8 eta_K (k+1)^2 / h_n on a
+    Navier (normal component) or Dirichlet (both components) side."""
+    hx, hy = lx / nx, ly / ny
+    n = 2 * nx * ny
+    A = np.zeros((n, n))
+    kk = (k + 1) ** 2
+    for ey in range(ny):
+        for ex in range(nx):
+            e = ey * nx + ex
+            for d, (hn, ht) in enumerate([(hx, hy), (hy, hx)]):
+                for side in (0, 1):
+                    nxe = ex + (side * 2 - 1 if d == 0 else 0)
+                    nye = ey + (side * 2 - 1 if d == 1 else 0)
+                    if 0 <= nxe < nx and 0 <= nye < ny:
+                        if side == 0:
+                            continue            # each interior face once, from its left/bottom side
+                        f = nye * nx + nxe
+                        w = 4.0 * max(eta[e], eta[f]) * kk / hn * ht / 4.0
+                        for c in range(2):
+                            A[2 * e + c, 2 * e + c] += w
+                            A[2 * f + c, 2 * f + c] += w
+                            A[2 * e + c, 2 * f + c] -= w
+                            A[2 * f + c, 2 * e + c] -= w
+                    else:
+                        kind = bc[2 * d + side]
+                        w = 8.0 * eta[e] * kk / hn * ht / 4.0
+                        comps = {"navier": [d], "dirichlet": [0, 1], "neumann": []}[kind]
+                        for c in comps:
+                            A[2 * e + c, 2 * e + c] += w
+    return A
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_q0_galerkin_operator_closed_form(k):
+    """A_0 = P_0^T A P_0 (the element-wise constant coarse space, Sec. 6.1.1)
+    equals the penalty-only 5-point operator written out independently, on a
+    non-square mesh with random viscosity and Navier, Neumann and Dirichlet
+    sides."""
+    nx, ny, lx, ly = 3, 5, 1.5, 1.0
+    eta = 10.0 ** np.random.default_rng(11).uniform(0, 2, nx * ny)
+    bc = ("navier", "dirichlet", "neumann", "navier")
+    prob = sip.Problem(nx, ny, k, eta, bc=bc, lx=lx, ly=ly)
+    A = sip.assemble_A(prob).tocsr()
+    P0 = multigrid.p_prolongation(k, nx * ny, 0)
+    A0 = (P0.T @ A @ P0).toarray()
+    ref = _q0_closed_form(nx, ny, k, eta, bc, lx, ly)
+    assert np.abs(A0 - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nh", [0, 2])
+def test_q0_vcycle_symmetric_and_convergent(nh):
+    """The hp-multigrid cycle with the Q^2_0 coarse space (A_p(Q^2_0) with an
+    exact coarse solve, A_hp(Q^2_0) with two cell-centred coarsenings of a
+    9 x 9 mesh) is a symmetric operator and makes PCG converge."""
+    n, k = 9, 2
+    eta = 10.0 ** np.random.default_rng(12).uniform(0, 2, n * n)
+    prob = sip.Problem(n, n, k, eta, bc=("navier", "navier", "navier", "neumann"))
+    A = sip.assemble_A(prob).tocsr()
+    mg = multigrid.HPMultigrid(prob, A, nh, seed=3, coarse="q0")
+    g = np.random.default_rng(13)
+    x, y = g.standard_normal(A.shape[0]), g.standard_normal(A.shape[0])
+    a, b = x @ mg(y), mg(x) @ y
+    assert abs(a - b) <= 1e-11 * (abs(a) + abs(b))
+    rhs = g.standard_normal(A.shape[0])
+    sol, its = krylov.pcg(lambda v: A @ v, mg, rhs, 1e-8, maxit=200)
+    assert np.linalg.norm(A @ sol - rhs) < 1e-8 * np.linalg.norm(rhs)
+    assert its < 120
