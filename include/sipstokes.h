@@ -87,11 +87,22 @@ typedef struct {
     double cheb_lo, cheb_hi;/* bound factors, paper 0.1 and 1.1                 */
     uint64_t seed;          /* SplitMix64 stream of the eigen-estimate vector   */
     sip_precision precision;
+    /* p-coarse space (Sec. 6.1): SIP_COARSE_Q1 (element-wise bilinear, then the
+     * continuous bilinear h-hierarchy, Sec. 6.1.2) or SIP_COARSE_Q0 (element-
+     * wise constants, A_0 = P^T A P, coarsened as a grid of the element
+     * centres, Sec. 6.1.1: needs nx - 1 and ny - 1 divisible by 2^n_hlevels,
+     * i.e. odd element counts; n_hlevels = 0 solves A_0 directly, at most
+     * 8192 elements). */
+    int coarse;
 } sip_problem_desc;
+
+/* values of sip_problem_desc.coarse */
+enum { SIP_COARSE_Q1 = 0, SIP_COARSE_Q0 = 1 };
 
 /* Fill a descriptor with the paper's defaults (Sec. 6-7): Navier on every
  * side, penalty_scale 1, n_hlevels 0, 2 p-level and 3 h-level smoothing
- * steps, 10 eigen-estimate iterations, bounds 0.1 / 1.1, seed 0, FP64. */
+ * steps, 10 eigen-estimate iterations, bounds 0.1 / 1.1, seed 0, FP64,
+ * Q^2_1 coarse space. */
 void sip_problem_desc_default(sip_problem_desc* desc);
 
 /* ---- context ------------------------------------------------------------ */
@@ -171,21 +182,26 @@ sip_status sip_apply_A1(sip_problem* prob, const double* x1, double* y1, void* s
 sip_status sip_cd_prolong(sip_problem* prob, const double* v, double* u1, void* stream);
 /* v = R_dc u1 = P_cd^T u1. */
 sip_status sip_dc_restrict(sip_problem* prob, const double* u1, double* v, void* stream);
-/* Number of continuous levels (n_hlevels + 1 for A_hp, 0 for A_p) and the
- * vertex grid of level l (l = 0 finest). */
+/* Number of vertex-grid levels (n_hlevels + 1 for A_hp(Q^2_1) and for the
+ * Q^2_0 coarse space, 0 for A_p(Q^2_1)) and the vertex grid of level l
+ * (l = 0 finest: the mesh vertices for Q^2_1, the element centres for
+ * Q^2_0). */
 sip_status sip_hlevel_dims(sip_problem* prob, int level, int* n_levels, int* nvx, int* nvy);
 /* Copy the Galerkin 9-point 2x2-block stencil of level l into S (device,
  * nvx*nvy*36 doubles, S[v][t][c][c'], t = (dy+1)*3 + (dx+1)): level 0 is
- * A_1c = P_cd^T A_1 P_cd, level l+1 is P_h^T A_l P_h (bilinear P_h). */
+ * A_1c = P_cd^T A_1 P_cd (Q^2_1) or A_0 = P_0^T A P_0 (Q^2_0), level l+1 is
+ * P_h^T A_l P_h (bilinear P_h). */
 sip_status sip_hlevel_stencil(sip_problem* prob, int level, double* S, void* stream);
 /* y = A_l x on continuous level l (vectors of 2 nvx nvy). */
 sip_status sip_hlevel_apply(sip_problem* prob, int level, const double* x, double* y, void* stream);
 /* x = A_c^{-1} b on the coarsest level (LU / Cholesky set-up, dense inverse):
- * A_1 itself for n_hlevels = 0, else the coarsest continuous level. */
+ * A_1 (Q^2_1) or A_0 (Q^2_0) itself for n_hlevels = 0, else the coarsest
+ * vertex-grid level. */
 sip_status sip_coarse_solve(sip_problem* prob, const double* b, double* x, void* stream);
 /* z_u = one V-cycle of Algorithm 1 (y0 = 0) applied to r_u: Chebyshev /
- * element-block Jacobi pre-smoothing, restriction to Q_1, coarse correction
- * (LU of A_1, or P_cd + continuous h-cycle + R_dc), prolongation,
+ * element-block Jacobi pre-smoothing, restriction to Q_1 (or Q_0), coarse
+ * correction (LU of A_1, or P_cd + continuous h-cycle + R_dc; with Q^2_0 the
+ * h-cycle of A_0 on the element centres, or its LU), prolongation,
  * post-smoothing. */
 sip_status sip_vcycle(sip_problem* prob, const double* r_u, double* z_u, void* stream);
 /* The same V-cycle computed entirely in FP32 (the mixed-precision form). */

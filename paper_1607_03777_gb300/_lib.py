@@ -18,6 +18,7 @@ STATUS_NAMES = {
 }
 BC = {"navier": 0, "neumann": 1, "dirichlet": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_f32_inner": 2}
+COARSE = {"q1": 0, "q0": 1}
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 
@@ -37,6 +38,7 @@ class ProblemDesc(ctypes.Structure):
         ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("precision", ctypes.c_int),
+        ("coarse", ctypes.c_int),
     ]
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SipError, ProblemDesc, SolveOpts, SolveReport, BC, PREC
+from ._lib import SipError, ProblemDesc, SolveOpts, SolveReport, BC, PREC, COARSE
 
 
 def _ptr(t, dtype):
@@ -76,7 +76,8 @@ class Problem:
 
     def __init__(self, ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0,
                  penalty_scale=1.0, n_hlevels=0, cheb_steps_p=2, cheb_steps_h=3,
-                 eig_iters=10, cheb_lo=0.1, cheb_hi=1.1, seed=0, precision="fp64"):
+                 eig_iters=10, cheb_lo=0.1, cheb_hi=1.1, seed=0, precision="fp64",
+                 coarse="q1"):
         self.ctx = ctx
         lib = ctx.lib
         d = ProblemDesc()
@@ -93,6 +94,7 @@ class Problem:
         d.cheb_lo, d.cheb_hi = cheb_lo, cheb_hi
         d.seed = seed
         d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        d.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
         h = ctypes.c_void_p()
         ctx.check(lib.sip_problem_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -243,7 +245,7 @@ class Problem:
 # ---------------------------------------------------------------- batches, serving
 def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_scale=1.0,
               n_hlevels=0, cheb_steps_p=2, cheb_steps_h=3, eig_iters=10, cheb_lo=0.1,
-              cheb_hi=1.1, seed=0, precision="fp64"):
+              cheb_hi=1.1, seed=0, precision="fp64", coarse="q1"):
     """A filled sip_problem_desc and the host eta array it points to (keep
     both alive while the C side may read them)."""
     d = ProblemDesc()
@@ -257,6 +259,7 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
     d.cheb_steps_p, d.cheb_steps_h, d.eig_iters = cheb_steps_p, cheb_steps_h, eig_iters
     d.cheb_lo, d.cheb_hi, d.seed = cheb_lo, cheb_hi, seed
     d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    d.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
     return d, eta
 
 

@@ -52,6 +52,7 @@ void sip_problem_desc_default(sip_problem_desc* d) {
     d->eta_host = nullptr;
     d->penalty_scale = 1.0;
     d->n_hlevels = 0;
+    d->coarse = SIP_COARSE_Q1;
     d->cheb_steps_p = 2;
     d->cheb_steps_h = 3;
     d->eig_iters = 10;
@@ -111,15 +112,23 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
         sip::require(std::isfinite(d->cheb_lo) && std::isfinite(d->cheb_hi) && d->cheb_lo > 0 &&
                          d->cheb_hi > d->cheb_lo,
                      "Chebyshev bound factors must satisfy 0 < lo < hi");
+        sip::require(d->coarse == SIP_COARSE_Q1 || d->coarse == SIP_COARSE_Q0,
+                     "unknown coarse space");
         {
-            int cx = d->nx, cy = d->ny;
+            // Q^2_1: the mesh vertices are coarsened; Q^2_0: the element
+            // centres, an (nx-1) x (ny-1) grid of intervals
+            int cx = d->coarse == SIP_COARSE_Q0 ? d->nx - 1 : d->nx;
+            int cy = d->coarse == SIP_COARSE_Q0 ? d->ny - 1 : d->ny;
             for (int l = 0; l < d->n_hlevels; ++l) {
-                sip::require(cx % 2 == 0 && cy % 2 == 0,
+                sip::require(cx % 2 == 0 && cy % 2 == 0 && cx > 0 && cy > 0,
                              "mesh cannot be coarsened n_hlevels times");
                 cx /= 2;
                 cy /= 2;
             }
         }
+        if (d->coarse == SIP_COARSE_Q0 && d->n_hlevels == 0)
+            sip::require(int64_t(d->nx) * d->ny <= 8192,
+                         "A_p(Q^2_0) coarse direct solve limited to 8192 elements; use n_hlevels > 0");
         const int64_t ne = int64_t(d->nx) * d->ny;
         sip::require(ne <= (int64_t(1) << 31) / 128, "mesh too large");
         std::vector<double> eta(d->eta_host, d->eta_host + ne);

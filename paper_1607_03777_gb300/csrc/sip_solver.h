@@ -20,8 +20,11 @@ void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, c
                      cudaStream_t s);
 
 // ---- transfer.cu
-template <typename T> void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s);
-template <typename T> void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s);
+// M = 2: Q^2_1 modes (8 per element), M = 1: Q^2_0 (2 per element)
+template <typename T>
+void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s, int M = 2);
+template <typename T>
+void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s, int M = 2);
 template <typename T> void launch_pcd(int nx, int ny, const T* v, T* out, cudaStream_t s);
 template <typename T> void launch_rdc(int nx, int ny, const T* r, T* out, cudaStream_t s);
 template <typename T>

@@ -454,7 +454,8 @@ void Multigrid<T>::setup(cudaStream_t s) {
     tune_smoother(s);
 
     const OpGeom& g1 = P->geom1;
-    if (d.n_hlevels == 0) {
+    const bool q0 = d.coarse == SIP_COARSE_Q0;
+    if (d.n_hlevels == 0 && !q0) {
         // A_p(Q^2_1): the coarse problem A_1 = P^T A P itself, by probing with
         // 9 element colours x 8 local dofs, then a band Cholesky.
         const int n1 = int(ne * 8);
@@ -492,16 +493,20 @@ void Multigrid<T>::setup(cudaStream_t s) {
             }
         build_coarse_from_band(band, n1, bw, s);
     } else {
-        // continuous levels: level 0 = A_1c = P_cd^T A_1 P_cd, then Galerkin
+        // vertex-grid levels: level 0 = A_1c = P_cd^T A_1 P_cd on the mesh
+        // vertices (Q^2_1), or A_0 = P_0^T A P_0 on the element centres
+        // (Q^2_0, an (nx-1) x (ny-1) grid of intervals); then Galerkin
         // P_h^T A_l P_h; stencils formed in FP64 by probing with 9 vertex
-        // colours x 2 components.
+        // colours x 2 components.  With Q^2_0 and no coarsening, level 0 is
+        // the coarsest and is solved directly (A_p(Q^2_0)).
         const int L = d.n_hlevels;
         h.resize(L + 1);
         std::vector<DeviceBuffer>& S64 = scr_S64;
         S64.resize(L + 1);
+        const int gx = q0 ? nx - 1 : nx, gy = q0 ? ny - 1 : ny;
         for (int l = 0; l <= L; ++l) {
-            h[l].nx = nx >> l;
-            h[l].ny = ny >> l;
+            h[l].nx = gx >> l;
+            h[l].ny = gy >> l;
             h[l].nvx = h[l].nx + 1;
             h[l].nvy = h[l].ny + 1;
             h[l].n = size_t(2) * h[l].nvx * h[l].nvy;
@@ -514,8 +519,8 @@ void Multigrid<T>::setup(cudaStream_t s) {
             xv.alloc(Lv.n * sizeof(double));
             DeviceBuffer &t1 = scr_t1, &t2 = scr_t2;
             if (l == 0) {
-                t1.alloc(ne * 8 * sizeof(double));
-                t2.alloc(ne * 8 * sizeof(double));
+                t1.alloc((q0 ? n_u : ne * 8) * sizeof(double));
+                t2.alloc((q0 ? n_u : ne * 8) * sizeof(double));
             } else {
                 t1.alloc(h[l - 1].n * sizeof(double));
                 t2.alloc(h[l - 1].n * sizeof(double));
@@ -524,7 +529,13 @@ void Multigrid<T>::setup(cudaStream_t s) {
                 for (int cp = 0; cp < 2; ++cp) {
                     double* y = Y.as<double>() + size_t(col * 2 + cp) * Lv.n;
                     launch_probe_vertices<double>(Lv.nvx, Lv.nvy, col, cp, xv.as<double>(), s);
-                    if (l == 0) {
+                    if (l == 0 && q0) {
+                        SIP_CUDA(cudaMemsetAsync(t1.ptr, 0, n_u * sizeof(double), s));
+                        launch_p_prolong_add<double>(ne, N, xv.as<double>(), t1.as<double>(), s, 1);
+                        launch_apply_sip<double>(N, P->geom, t1.as<double>(), t2.as<double>(),
+                                                 P->eta_d.as<double>(), 1.0, nullptr, 0.0, s);
+                        launch_p_restrict<double>(ne, N, t2.as<double>(), y, s, 1);
+                    } else if (l == 0) {
                         launch_pcd<double>(nx, ny, xv.as<double>(), t1.as<double>(), s);
                         launch_apply_sip<double>(2, g1, t1.as<double>(), t2.as<double>(),
                                                  P->eta_d.as<double>(), 1.0, nullptr, 0.0, s);
@@ -737,6 +748,12 @@ void Multigrid<T>::hcycle(int l, cudaStream_t s) {
 
 template <typename T>
 void Multigrid<T>::coarse_solve(const T* b1, T* x1, cudaStream_t s) {
+    if (P->desc.coarse == SIP_COARSE_Q0) {   // b1, x1: 2 constants per element
+        SIP_CUDA(cudaMemcpyAsync(h[0].b.ptr, b1, h[0].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        hcycle(0, s);
+        SIP_CUDA(cudaMemcpyAsync(x1, h[0].x.ptr, h[0].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        return;
+    }
     if (h.empty()) {
         launch_dense_symv<T>(nc, cinv.template as<T>(), b1, x1, s);
         return;
@@ -755,6 +772,16 @@ void Multigrid<T>::vcycle_direct(cudaStream_t s) {
 template <typename T>
 void Multigrid<T>::vcycle_on(const T* b, T* y, cudaStream_t s) {
     smooth_p(b, y, true, s);
+    if (P->desc.coarse == SIP_COARSE_Q0) {
+        // coarse correction on the element-wise constants: the residual's
+        // (0,0) modes are the finest vertex-grid level's right-hand side
+        launch_apply_sip<T>(N, P->geom, y, pr.template as<T>(), eta_of<T>(P), T(-1), b, T(1), s);
+        launch_p_restrict<T>(ne, N, pr.template as<T>(), h[0].b.template as<T>(), s, 1);
+        hcycle(0, s);
+        launch_p_prolong_add<T>(ne, N, h[0].x.template as<T>(), y, s, 1);
+        smooth_p(b, y, false, s);
+        return;
+    }
     // r1 = R (b - A y)
     if (!use_fused() ||
         !launch_residual_restrict_elem<T>(N, P->geom, y, b, eta_of<T>(P), r1.template as<T>(), s)) {

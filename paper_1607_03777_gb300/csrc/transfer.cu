@@ -17,23 +17,29 @@ namespace {
 constexpr double kInvSqrt2 = 0.70710678118654752440;   // int L_p l_0 for the two end hats
 constexpr double kInvSqrt6 = 0.40824829046386301637;   // |int L_p l_1|
 
+// p-transfers to the coarse space of the M x M lowest modes per component
+// (M = 2: Q^2_1, M = 1: Q^2_0), coarse layout [e][c][j][i] with i, j < M.
 template <typename T>
-__global__ void k_p_restrict(size_t ne, int N, const T* __restrict__ r, T* __restrict__ r1) {
+__global__ void k_p_restrict(size_t ne, int N, int M, const T* __restrict__ r,
+                             T* __restrict__ r1) {
     grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= ne * 8) return;
-    const size_t e = g / 8;
-    const int l = int(g % 8), c = l / 4, j = (l / 2) % 2, i = l % 2;
+    const int per = 2 * M * M;
+    if (g >= ne * per) return;
+    const size_t e = g / per;
+    const int l = int(g % per), c = l / (M * M), j = (l / M) % M, i = l % M;
     r1[g] = r[e * 2 * N * N + c * N * N + j * N + i];
 }
 
 template <typename T>
-__global__ void k_p_prolong_add(size_t ne, int N, const T* __restrict__ e1, T* __restrict__ y) {
+__global__ void k_p_prolong_add(size_t ne, int N, int M, const T* __restrict__ e1,
+                                T* __restrict__ y) {
     grid_dep_wait();
     const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= ne * 8) return;
-    const size_t e = g / 8;
-    const int l = int(g % 8), c = l / 4, j = (l / 2) % 2, i = l % 2;
+    const int per = 2 * M * M;
+    if (g >= ne * per) return;
+    const size_t e = g / per;
+    const int l = int(g % per), c = l / (M * M), j = (l / M) % M, i = l % M;
     y[e * 2 * N * N + c * N * N + j * N + i] += e1[g];
 }
 
@@ -367,13 +373,13 @@ inline unsigned nblk(size_t n, int t = 256) { return unsigned((n + t - 1) / t); 
 }  // namespace
 
 template <typename T>
-void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s) {
-    launch_k(k_p_restrict<T>, nblk(ne * 8), 256, 0, s, ne, N, r, r1);
+void launch_p_restrict(size_t ne, int N, const T* r, T* r1, cudaStream_t s, int M) {
+    launch_k(k_p_restrict<T>, nblk(ne * 2 * M * M), 256, 0, s, ne, N, M, r, r1);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
-void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s) {
-    launch_k(k_p_prolong_add<T>, nblk(ne * 8), 256, 0, s, ne, N, e1, y);
+void launch_p_prolong_add(size_t ne, int N, const T* e1, T* y, cudaStream_t s, int M) {
+    launch_k(k_p_prolong_add<T>, nblk(ne * 2 * M * M), 256, 0, s, ne, N, M, e1, y);
     SIP_CHECK_LAUNCH();
 }
 template <typename T>
@@ -476,8 +482,8 @@ void launch_convert(size_t n, const double* a, T* b, cudaStream_t s) {
 }
 
 #define SIP_INST(T)                                                                              \
-    template void launch_p_restrict<T>(size_t, int, const T*, T*, cudaStream_t);                \
-    template void launch_p_prolong_add<T>(size_t, int, const T*, T*, cudaStream_t);             \
+    template void launch_p_restrict<T>(size_t, int, const T*, T*, cudaStream_t, int);           \
+    template void launch_p_prolong_add<T>(size_t, int, const T*, T*, cudaStream_t, int);        \
     template void launch_pcd<T>(int, int, const T*, T*, cudaStream_t);                          \
     template void launch_rdc<T>(int, int, const T*, T*, cudaStream_t);                          \
     template void launch_stencil_apply<T>(int, int, const T*, const T*, T*, T, const T*, T,     \

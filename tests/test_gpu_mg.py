@@ -26,8 +26,9 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def pair(ctx, nx, ny, k, bc, eta, nh=0, seed=3, precision="fp64"):
-    prob = api.Problem(ctx, nx, ny, k, eta, bc=bc, n_hlevels=nh, seed=seed, precision=precision)
+def pair(ctx, nx, ny, k, bc, eta, nh=0, seed=3, precision="fp64", coarse="q1"):
+    prob = api.Problem(ctx, nx, ny, k, eta, bc=bc, n_hlevels=nh, seed=seed, precision=precision,
+                       coarse=coarse)
     ref = sip.Problem(nx, ny, k, eta, bc=bc)
     return prob, ref
 
@@ -257,3 +258,66 @@ def test_inner_loop_device_equals_host(ctx, precision, nx, k, nh):
         (rh["outer_its"], rh["inner_total"], rh["inner_max"])
     assert torch.equal(ud, uh) and torch.equal(pd_, ph)
     assert rd["rel_residual"] == rh["rel_residual"] <= 1e-8
+
+
+
+# ---- Q^2_0 coarse space (Sec. 6.1.1)
+@pytest.mark.parametrize("nh,n,k,bc", [(2, 17, 2, SINK), (1, 9, 3, ("navier",) * 4),
+                                       (0, 9, 2, ("dirichlet",) * 4)])
+def test_q0_levels_and_vcycle(ctx, nh, n, k, bc):
+    """Element-wise constant coarse space: the level-0 stencil equals the
+    oracle's A_0 = P_0^T A P_0 on the element centres, the coarser levels its
+    Galerkin products, the coarsest direct solve the dense solve, and one
+    V-cycle the oracle's, to 1e-9."""
+    eta, _ = materials.rasterise_inclusions(n, n, synth.single_box_inclusion(n, k, 1e3).shapes)
+    prob, ref = pair(ctx, n, n, k, bc, eta, nh=nh, seed=6, coarse="q0")
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, nh, seed=6, coarse="q0")
+    nl, nvx, nvy = prob.hlevel_dims(0)
+    assert (nl, nvx, nvy) == (nh + 1, n, n)
+    mats = [lv.A for lv in mg.h.levels] + [mg.h.coarse_A] if nh else [mg.A0.toarray()]
+    for l in range(nh + 1):
+        _, nvx, nvy = prob.hlevel_dims(l)
+        x = synth.random_vector(2 * nvx * nvy, 40 + l)
+        y = torch.empty_like(dev(x))
+        prob.hlevel_apply(l, dev(x), y)
+        assert rel(host(y), mats[l] @ x) < 1e-10, l
+        if l < nh:
+            assert abs(prob.lambda_max(l) - mg.h.levels[l].lmax) < 1e-9 * mg.h.levels[l].lmax
+    _, nvx, nvy = prob.hlevel_dims(nh)
+    b = synth.random_vector(2 * nvx * nvy, 7)
+    x = torch.empty_like(dev(b))
+    prob.coarse_solve(dev(b), x)
+    assert rel(host(x), np.linalg.solve(np.asarray(mats[nh]), b)) < 1e-9
+    assert abs(prob.lambda_max(-1) - mg.lmax) < 1e-9 * mg.lmax
+    r = synth.random_vector(prob.n_u, 78)
+    z = torch.empty_like(dev(r))
+    prob.vcycle(dev(r), z)
+    assert rel(host(z), mg(r)) < 1e-9
+    prob.vcycle(dev(r), z)
+    assert rel(host(z), mg(r)) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_q0_box_inclusion(ctx, precision):
+    """A_hp(Q^2_0): the box-inclusion Stokes problem on a 17 x 17 mesh (two
+    cell-centred coarsenings) reaches the 1e-8 true residual and the
+    sparse-direct solution."""
+    n, k = 17, 2
+    wl = synth.single_box_inclusion(n, k, 1e4, n_hlevels=2)
+    eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
+    prob, ref = pair(ctx, n, n, k, wl.bc, eta, nh=2, seed=1, precision=precision, coarse="q0")
+    f = sip.rhs_body_force(ref, rho)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-8, max_outer=1000)
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.05e-8, rep
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-5
+
+
+def test_q0_rejects_even_meshes(ctx):
+    """Cell-centred coarsening needs nx - 1 and ny - 1 divisible by 2^n_hlevels."""
+    with pytest.raises(api.SipError):
+        api.Problem(ctx, 16, 16, 2, np.ones(256), n_hlevels=1, coarse="q0")
