@@ -56,7 +56,7 @@ def parse():
                          "graphs with conditional nodes)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "coarse"],
                     help="solve: the headline line; batch / serve: the batched and served "
                          "forms on bounded samples of their workloads (extra lines)")
     ap.add_argument("--count", type=int, default=32,
@@ -510,6 +510,52 @@ def run_serve(args):
                        "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8}}
 
 
+def run_coarse(args):
+    """Coarse-space comparison (Sec. 7.1 table of the four preconditioners):
+    A_p(Q^2_0), A_hp(Q^2_0), A_p(Q^2_1), A_hp(Q^2_1) on the box-inclusion
+    problem (eta 1e4) with k = 2, FP64, rtol 1e-8; element-wise constant
+    spaces on odd meshes (n + 1 elements per side) as the paper does, direct
+    coarse solves only where the coarse problem has at most 8192 elements.
+    Each solve includes its multigrid set-up; best of three."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    ctx = api.Context(0)
+    k = 2
+    rows = []
+    for n in (64, 128, 256):
+        for coarse, hp in (("q0", False), ("q0", True), ("q1", False), ("q1", True)):
+            m = n + 1 if coarse == "q0" else n
+            if not hp and m * m > 8192:
+                continue
+            nh = synth.levels_to_17(m - 1 if coarse == "q0" else m) if hp else 0
+            wl = synth.single_box_inclusion(n=m, k=k)
+            eta, rho = ctx.rasterise_inclusions(m, m, wl.shapes)
+            pr = api.Problem(ctx, m, m, k, eta.cpu().numpy(), bc=wl.bc, n_hlevels=nh, seed=1,
+                             coarse=coarse)
+            f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
+            u = torch.empty_like(f)
+            p = torch.empty(pr.n_p, dtype=torch.float64, device="cuda")
+            pr.rhs_body_force(rho, synth.GRAVITY, f)
+            best, rep = 1e30, None
+            for _ in range(3):
+                pr.update_eta(eta)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = pr.solve(f, u, p, rtol=1e-8, max_outer=1000, check=False)
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            name = ("A_hp" if hp else "A_p") + ("(Q2_0)" if coarse == "q0" else "(Q2_1)")
+            rows.append({"preconditioner": name, "elements": f"{m}x{m}", "n_hlevels": nh,
+                         "status": rep["status"], "outer_its": rep["outer_its"],
+                         "inner_avg": round(rep["inner_avg"], 2), "inner_max": rep["inner_max"],
+                         "rel_residual": rep["rel_residual"], "ms": round(best * 1e3, 2),
+                         "solves_per_s": round(1.0 / best, 3)})
+            del pr
+    return {"metric": "coarse_space_comparison", "unit": UNIT, "rows": rows,
+            "config": {"workload": "single_box_inclusion eta 1e4, k = 2, FP64, rtol 1e-8",
+                       "precision": "fp64"}}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -517,7 +563,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.mode != "solve":
         if rank == 0:
-            out = run_batch(args) if args.mode == "batch" else run_serve(args)
+            out = {"batch": run_batch, "serve": run_serve, "coarse": run_coarse}[args.mode](args)
             print(json.dumps(out), flush=True)
         return 0
     if args.impl == "reference":
