@@ -56,9 +56,12 @@ def parse():
                          "graphs with conditional nodes)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "coarse"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "batch", "serve", "coarse", "sinkers"],
                     help="solve: the headline line; batch / serve: the batched and served "
-                         "forms on bounded samples of their workloads (extra lines)")
+                         "forms on bounded samples of their workloads; coarse: the four "
+                         "coarse-space preconditioners; sinkers: the six-sinker iteration "
+                         "sweep (extra lines)")
     ap.add_argument("--count", type=int, default=32,
                     help="instances (batch) or requests (serve) in the bounded sample")
     return ap.parse_args()
@@ -556,6 +559,42 @@ def run_coarse(args):
                        "precision": "fp64"}}
 
 
+def run_sinkers(args):
+    """The six sedimenting inclusions of Sec. 7.3 (positions and radii as
+    listed there, rho 1.2 against 1, Neumann top, Navier elsewhere),
+    A_hp(Q^2_1) with 2, 3, 4 h-coarsenings at 64^2, 128^2, 256^2, k = 1..3,
+    contrasts 1e3, 1e6, 1e8, FP64, outer rtol 1e-6 and inner rtol 1e-3 as in
+    the paper (which ran GCR for both solves; here FGMRES and CG)."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    ctx = api.Context(0)
+    rows = []
+    for eta_in in (1e3, 1e6, 1e8):
+        for n in (64, 128, 256):
+            for k in (1, 2, 3):
+                wl = synth.six_sinkers(n=n, k=k, eta_in=eta_in, n_hlevels=synth.levels_to_17(n))
+                eta, rho = ctx.rasterise_inclusions(n, n, wl.shapes)
+                pr = api.Problem(ctx, n, n, k, eta.cpu().numpy(), bc=wl.bc,
+                                 n_hlevels=wl.n_hlevels, seed=1)
+                f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
+                u = torch.empty_like(f)
+                p = torch.empty(pr.n_p, dtype=torch.float64, device="cuda")
+                pr.rhs_body_force(rho, synth.GRAVITY, f)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = pr.solve(f, u, p, rtol=1e-6, max_outer=500, check=False)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                rows.append({"eta": eta_in, "elements": f"{n}x{n}", "k": k, "status": rep["status"],
+                             "outer_its": rep["outer_its"], "inner_avg": round(rep["inner_avg"], 1),
+                             "inner_max": rep["inner_max"], "rel_residual": rep["rel_residual"],
+                             "ms": round(dt * 1e3, 1)})
+                del pr
+    return {"metric": "six_sinkers_iterations", "unit": "iterations", "rows": rows,
+            "config": {"workload": "six sinkers (Sec. 7.3), A_hp(Q2_1), FP64, rtol 1e-6",
+                       "precision": "fp64"}}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -563,7 +602,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.mode != "solve":
         if rank == 0:
-            out = {"batch": run_batch, "serve": run_serve, "coarse": run_coarse}[args.mode](args)
+            out = {"batch": run_batch, "serve": run_serve, "coarse": run_coarse,
+                   "sinkers": run_sinkers}[args.mode](args)
             print(json.dumps(out), flush=True)
         return 0
     if args.impl == "reference":

@@ -49,8 +49,14 @@ def solve_direct(prob, A, B, f, g=None):
     return sol[:n_u], sol[n_u:n_u + n_p]
 
 
-def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
-    """Preconditioned CG for A y = x; stops when ||A y - x|| < rtol ||x||.
+def pcg(apply_A, precond, x, rtol, maxit=200, y0=None, norm="true"):
+    """Preconditioned CG for A y = x.
+
+    norm = "true": stops when ||A y - x|| < rtol ||x|| (the residual itself);
+    norm = "preconditioned": stops when ||B r|| < rtol ||B r_0||, B the
+    preconditioner, r = x - A y: the preconditioned residual that CG forms
+    anyway for its next direction (the default test of PETSc's CG, which the
+    paper ran).  The iterates are the same; only the stopping point differs.
 
     Returns (y, iterations)."""
     y = np.zeros_like(x) if y0 is None else y0.copy()
@@ -59,6 +65,7 @@ def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
     if nx == 0.0:
         return y, 0
     z = precond(r)
+    nz0 = np.linalg.norm(z)
     d = z.copy()
     rz = r @ z
     for it in range(1, maxit + 1):
@@ -66,18 +73,20 @@ def pcg(apply_A, precond, x, rtol, maxit=200, y0=None):
         alpha = rz / (d @ q)
         y += alpha * d
         r -= alpha * q
-        if np.linalg.norm(r) < rtol * nx:
+        if norm == "true" and np.linalg.norm(r) < rtol * nx:
             return y, it
         z = precond(r)
+        if norm == "preconditioned" and np.linalg.norm(z) < rtol * nz0:
+            return y, it
         rz_new = r @ z
         d = z + (rz_new / rz) * d
         rz = rz_new
     return y, maxit
 
 
-def fcg(apply_A, precond, x, rtol, maxit=200):
+def fcg(apply_A, precond, x, rtol, maxit=200, norm="true"):
     """Flexible conjugate gradients, FCG(1) (Notay, SIAM J. Sci. Comput. 22,
-    2000), for A y = x from y = 0; stops when ||A y - x|| < rtol ||x||.
+    2000), for A y = x from y = 0; stopping test as in ``pcg`` (``norm``).
 
     Each new direction is made A-orthogonal to the previous one explicitly,
     beta = <z, q_prev> / <d_prev, q_prev>, and the step is the exact line
@@ -91,9 +100,10 @@ def fcg(apply_A, precond, x, rtol, maxit=200):
     nx = np.linalg.norm(x)
     if nx == 0.0:
         return y, 0
+    z = precond(r)
+    nz0 = np.linalg.norm(z)
     d = q = None
     for it in range(1, maxit + 1):
-        z = precond(r)
         if d is None:
             d = z.copy()
         else:
@@ -102,7 +112,10 @@ def fcg(apply_A, precond, x, rtol, maxit=200):
         alpha = (d @ r) / (d @ q)
         y += alpha * d
         r -= alpha * q
-        if np.linalg.norm(r) < rtol * nx:
+        if norm == "true" and np.linalg.norm(r) < rtol * nx:
+            return y, it
+        z = precond(r)
+        if norm == "preconditioned" and np.linalg.norm(z) < rtol * nz0:
             return y, it
     return y, maxit
 
@@ -113,12 +126,13 @@ class BlockPreconditioner:
         y_p = -S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
 
     def __init__(self, A, B, s_diag, inner_precond, inner_rtol=1e-3,
-                 inner_maxit=200, null_p=None, inner="pcg"):
+                 inner_maxit=200, null_p=None, inner="pcg", inner_norm="true"):
         self.A, self.B, self.s = A, B, s_diag
         self.inner_precond = inner_precond
         self.inner_rtol, self.inner_maxit = inner_rtol, inner_maxit
         self.null_p = null_p
         self.inner = {"pcg": pcg, "fcg": fcg}[inner]
+        self.inner_norm = inner_norm
         self.inner_its = []
 
     def __call__(self, x):
@@ -129,7 +143,7 @@ class BlockPreconditioner:
             yp = project_out(yp, self.null_p)
         t = xu - self.B @ yp
         yu, its = self.inner(lambda v: self.A @ v, self.inner_precond, t,
-                             self.inner_rtol, self.inner_maxit)
+                             self.inner_rtol, self.inner_maxit, norm=self.inner_norm)
         self.inner_its.append(its)
         return np.concatenate([yu, yp])
 

@@ -583,3 +583,23 @@ def test_q0_vcycle_symmetric_and_convergent(nh):
     sol, its = krylov.pcg(lambda v: A @ v, mg, rhs, 1e-8, maxit=200)
     assert np.linalg.norm(A @ sol - rhs) < 1e-8 * np.linalg.norm(rhs)
     assert its < 120
+
+
+@pytest.mark.parametrize("solver", ["pcg", "fcg"])
+def test_inner_preconditioned_norm_stopping(solver):
+    """The preconditioned-residual stopping test (||B r|| < rtol ||B r_0||, B
+    the preconditioner) changes only where CG stops: the iterate is the one
+    the true-residual variant has after the same number of steps, the test
+    holds there, and it did not hold one step earlier."""
+    A = _spd(50, 21, cond=1e3)
+    dinv = 1.0 / np.diag(A)
+    x = np.random.default_rng(22).standard_normal(50)
+    f = getattr(krylov, solver)
+    B = lambda r: dinv * r
+    y, its = f(lambda v: A @ v, B, x, 1e-4, maxit=400, norm="preconditioned")
+    assert 1 < its < 400
+    assert np.linalg.norm(B(x - A @ y)) < 1e-4 * np.linalg.norm(B(x))
+    y2, its2 = f(lambda v: A @ v, B, x, 1e-30, maxit=its, norm="true")
+    assert its2 == its and np.linalg.norm(y2 - y) <= 1e-12 * np.linalg.norm(y)
+    y3, _ = f(lambda v: A @ v, B, x, 1e-30, maxit=its - 1, norm="true")
+    assert not np.linalg.norm(B(x - A @ y3)) < 1e-4 * np.linalg.norm(B(x))
