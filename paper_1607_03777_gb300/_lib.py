@@ -51,6 +51,7 @@ class SolveOpts(ctypes.Structure):
         ("max_inner", ctypes.c_int),
         ("inner_loop", ctypes.c_int),
         ("inner_krylov", ctypes.c_int),
+        ("inner_norm", ctypes.c_int),
     ]
 
 

@@ -479,6 +479,7 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->max_inner = 200;
     o->inner_loop = 0;
     o->inner_krylov = 0;
+    o->inner_norm = 1;
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -494,7 +495,9 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
                          o.restart <= 250 &&
                          std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1 &&
                          (o.inner_loop == 0 || o.inner_loop == 1) && o.inner_krylov >= 0 &&
-                         o.inner_krylov <= 2 && !(o.inner_loop == 1 && o.inner_krylov == 2),
+                         o.inner_krylov <= 2 && !(o.inner_loop == 1 && o.inner_krylov == 2) &&
+                         (o.inner_norm == 0 || o.inner_norm == 1) &&
+                         !(o.inner_loop == 1 && o.inner_norm == 1),
                      "bad solve options");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));

@@ -28,7 +28,7 @@ constexpr int kRT = 256;
 struct PcgState {
     const double* t;   // right-hand side (set before each launch)
     double* y;         // iterate (set before each launch)
-    double nt, rz, alpha, beta, rr, dq;
+    double nt, rz, alpha, beta, rr, dq, nz0, nz;
     int it, status;    // status 0 ok, 1 non-finite
 };
 
@@ -247,6 +247,77 @@ __global__ void __launch_bounds__(kRT) k_ctl_final(PcgState* st, const double* p
     }
 }
 
+// ---- stopping on the preconditioned residual ||V r|| (the default test of
+// PETSc's CG, which the paper ran): the V-cycle moves to the end of the pass,
+// so that the test sees the z it produces; one V-cycle of the initial
+// residual precedes the loop.
+
+// partial sums of z.z (partial[0..kRB)) and z.w (partial[kRB..2kRB)), with
+// z = widen(zs) stored into zd when zd != nullptr; w = r (PCG) or q (FCG)
+template <typename Tz>
+__global__ void __launch_bounds__(kRT) k_dot_zz_zw(size_t n, const double* __restrict__ w,
+                                                   const Tz* __restrict__ zs, double* zd,
+                                                   double* partial) {
+    grid_dep_wait();
+    double a1 = 0.0, a2 = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        const double z = double(zs[g]);
+        if (zd) zd[g] = z;
+        a1 += z * z;
+        a2 += w[g] * z;
+    }
+    a1 = block_sum(a1);
+    a2 = block_sum(a2);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = a1;
+        partial[kRB + blockIdx.x] = a2;
+    }
+}
+
+// after z_0 = V(r_0): ||z_0||, rz = r.z (PCG), beta = 0, first condition
+__global__ void __launch_bounds__(kRT) k_pn_first_final(PcgState* st, const double* partial,
+                                                        cudaGraphConditionalHandle h) {
+    grid_dep_wait();
+    const double zz = final_sum(partial);
+    const double zw = final_sum(partial + kRB);
+    if (threadIdx.x == 0) {
+        const double nz0 = sqrt(zz);
+        st->nz0 = nz0;
+        st->nz = nz0;
+        st->rz = zw;
+        st->beta = 0.0;
+        if (!isfinite(nz0)) st->status = 1;
+        const bool go = st->status == 0 && st->nt > 0.0 && nz0 > 0.0;
+        cudaGraphSetConditional(h, go ? 1u : 0u);
+    }
+}
+
+// end of a pass: counter, test ||z|| < rtol ||z_0||, the next beta
+// (PCG: rz_new / rz; FCG, stored negated: -(z.q) / (d.q)), loop condition
+__global__ void __launch_bounds__(kRT) k_pn_ctl_final(PcgState* st, const double* partial,
+                                                      double rtol, int maxit, int flexible,
+                                                      cudaGraphConditionalHandle h) {
+    grid_dep_wait();
+    const double zz = final_sum(partial);
+    const double zw = final_sum(partial + kRB);
+    if (threadIdx.x == 0) {
+        const double nz = sqrt(zz);
+        const int it = st->it + 1;
+        st->it = it;
+        st->nz = nz;
+        if (flexible) {
+            st->beta = -(zw / st->dq);
+        } else {
+            st->beta = zw / st->rz;
+            st->rz = zw;
+        }
+        if (!isfinite(nz)) st->status = 1;
+        const bool more = isfinite(nz) && !(nz < rtol * st->nz0) && it < maxit;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
 inline unsigned nblk(size_t n) { return unsigned((n + 255) / 256); }
 
 }  // namespace
@@ -259,6 +330,7 @@ struct InnerLoop {
     HostScalars hs;             // pinned read-back of the state
     bool mixed = false;
     bool flexible = false;
+    bool pnorm = false;   // stop on the preconditioned residual
     double rtol = -1.0;
     int maxit = -1;
     int gen = -1;
@@ -332,6 +404,57 @@ void capture_body(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphCondition
     SIP_CHECK_LAUNCH();
 }
 
+// z = V(r) (z stored in FP64) with the partial sums of z.z and z.w
+void vcycle_dots(sip_problem* P, Workspace& W, InnerLoop& L, const double* w, cudaStream_t cs) {
+    const size_t n_u = size_t(P->n_u);
+    double* r = W.cg_r.as<double>();
+    double* z = W.cg_z.as<double>();
+    double* part = L.partial.as<double>();
+    if (L.mixed) {
+        Multigrid<float>& mg = *P->mg32;
+        float* vin = mg.vin.as<float>();
+        float* vout = mg.vout.as<float>();
+        launch_cast<double, float>(n_u, r, vin, cs);
+        mg.vcycle_on(vin, vout, cs);
+        launch_k(k_dot_zz_zw<float>, kRB, kRT, 0, cs, n_u, w, vout, z, part);
+    } else {
+        P->mg64->vcycle_on(r, z, cs);
+        launch_k(k_dot_zz_zw<double>, kRB, kRT, 0, cs, n_u, w, z, nullptr, part);
+    }
+    SIP_CHECK_LAUNCH();
+}
+
+// One pass of the preconditioned-norm loop: d = z + beta d, q = A d, alpha,
+// y += alpha d, r -= alpha q, z = V(r), test ||z||.
+void capture_body_pnorm(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphConditionalHandle h,
+                        cudaStream_t cs) {
+    const size_t n_u = size_t(P->n_u);
+    double* r = W.cg_r.as<double>();
+    double* d = W.cg_d.as<double>();
+    double* q = W.cg_q.as<double>();
+    double* z = W.cg_z.as<double>();
+    double* part = L.partial.as<double>();
+    PcgState* st = L.state.as<PcgState>();
+    launch_k(k_dir, nblk(n_u), 256, 0, cs, n_u, z, d, st);
+    SIP_CHECK_LAUNCH();
+    launch_apply_sip<double>(P->n, P->geom, d, q, P->eta_d.as<double>(), 1.0, nullptr, 0.0, cs);
+    if (L.flexible) {
+        launch_k(k_dot_dq_dr, kRB, kRT, 0, cs, n_u, d, q, r, part);
+        SIP_CHECK_LAUNCH();
+        launch_k(k_alpha_fcg_final, 1, kRT, 0, cs, st, part);
+    } else {
+        launch_k(k_dot, kRB, kRT, 0, cs, n_u, d, q, part);
+        SIP_CHECK_LAUNCH();
+        launch_k(k_alpha_final, 1, kRT, 0, cs, st, part);
+    }
+    SIP_CHECK_LAUNCH();
+    launch_k(k_update_rr, kRB, kRT, 0, cs, n_u, d, q, r, st, part);
+    SIP_CHECK_LAUNCH();
+    vcycle_dots(P, W, L, L.flexible ? q : r, cs);
+    launch_k(k_pn_ctl_final, 1, kRT, 0, cs, st, part, L.rtol, L.maxit, L.flexible ? 1 : 0, h);
+    SIP_CHECK_LAUNCH();
+}
+
 void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
     // plain launches inside the graph that holds the conditional node
     PdlOffScope pdl_off;
@@ -363,6 +486,19 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
         launch_k(k_init_final, 1, kRT, 0, L.cs, L.state.as<PcgState>(), L.partial.as<double>(), h);
         e = cudaGetLastError();
     }
+    int64_t pre_kernels = 2;
+    if (e == cudaSuccess && L.pnorm) {   // z_0 = V(r_0) and its norm before the loop
+        const int64_t c0 = launch_counter();
+        try {
+            vcycle_dots(P, W, L, W.cg_r.as<double>(), L.cs);
+            launch_k(k_pn_first_final, 1, kRT, 0, L.cs, L.state.as<PcgState>(),
+                     L.partial.as<double>(), h);
+            SIP_CHECK_LAUNCH();
+        } catch (const Error&) {
+            e = cudaErrorUnknown;
+        }
+        pre_kernels += launch_counter() - c0;
+    }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -383,13 +519,16 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
     const cudaError_t ee = cudaStreamEndCapture(L.cs, &gout);
     SIP_CUDA(e);
     SIP_CUDA(ee);
-    L.top_kernels = 2;
+    L.top_kernels = pre_kernels;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     SIP_CUDA(cudaStreamBeginCaptureToGraph(L.cs, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal));
     const int64_t b0 = launch_counter();
     try {
-        capture_body(P, W, L, h, L.cs);
+        if (L.pnorm)
+            capture_body_pnorm(P, W, L, h, L.cs);
+        else
+            capture_body(P, W, L, h, L.cs);
     } catch (...) {
         cudaGraph_t tmp;
         cudaStreamEndCapture(L.cs, &tmp);
@@ -405,8 +544,8 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
 
 }  // namespace
 
-int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, const double* t,
-                    double* y, double rtol, int maxit, cudaStream_t s) {
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, bool pnorm,
+                    const double* t, double* y, double rtol, int maxit, cudaStream_t s) {
     maxit = std::max(1, std::min(maxit, 100000));
     const size_t n_u = size_t(P->n_u);
     for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
@@ -418,10 +557,12 @@ int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, con
     const void* mg = mixed ? static_cast<const void*>(P->mg32.get())
                            : static_cast<const void*>(P->mg64.get());
     const int gen = mixed ? P->mg32->setup_gen : P->mg64->setup_gen;
-    if (!L.exec || L.mixed != mixed || L.flexible != flexible || L.rtol != rtol ||
+    if (!L.exec || L.mixed != mixed || L.flexible != flexible || L.pnorm != pnorm ||
+        L.rtol != rtol ||
         L.maxit != maxit || L.gen != gen || L.mg != mg) {
         L.mixed = mixed;
         L.flexible = flexible;
+        L.pnorm = pnorm;
         L.rtol = rtol;
         L.maxit = maxit;
         L.gen = gen;

@@ -186,9 +186,10 @@ int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, do
                     int maxit, cudaStream_t s);
 // The same inner solve (FP64 iterate; V-cycle in FP32 when mixed, else FP64)
 // as one graph launch with a device-side loop; returns the iteration count.
-// flexible: FCG(1) directions instead of PCG's.
-int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, const double* t,
-                    double* y, double rtol, int maxit, cudaStream_t s);
+// flexible: FCG(1) directions instead of PCG's; pnorm: stop on the
+// preconditioned residual ||V r|| instead of ||r||.
+int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, bool pnorm,
+                    const double* t, double* y, double rtol, int maxit, cudaStream_t s);
 
 sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,

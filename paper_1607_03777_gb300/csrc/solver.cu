@@ -1019,8 +1019,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                         : P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s,
                                              nullptr);
         } else {
-            its = inner_pcg_graph(P, W, mixed, flexible, W.tu.as<double>(), z, o.inner_rtol,
-                                  o.max_inner, s);
+            its = inner_pcg_graph(P, W, mixed, flexible, o.inner_norm == 1, W.tu.as<double>(), z,
+                                  o.inner_rtol, o.max_inner, s);
         }
         inner_total += its;
         inner_max = std::max(inner_max, its);
