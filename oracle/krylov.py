@@ -7,6 +7,9 @@ Test infrastructure only (see ``oracle/__init__``).
   there is no Neumann face (eq. pressure).
 * ``pcg``           preconditioned CG on A with the relative stopping test
   ||A y - x|| / ||x|| < eps of Sec. 6 (inner viscous solve).
+* ``gcr``           generalised conjugate residual, right-preconditioned,
+  flexible, restarted: the Krylov method the paper ran for the viscous block
+  of the six-inclusion problem (Sec. 7.3); stops on the residual itself.
 * ``fgmres``        right-preconditioned flexible GMRES (Saad's FGMRES) on the
   saddle system with the upper block-triangular preconditioner of
   eq. discretestokespc, S replaced by the diagonal S* (Sec. 5), and
@@ -120,6 +123,56 @@ def fcg(apply_A, precond, x, rtol, maxit=200, norm="true"):
     return y, maxit
 
 
+def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None):
+    """Generalised conjugate residual method (Eisenstat, Elman & Schultz,
+    SIAM J. Numer. Anal. 20, 1983) for A y = x from y = 0, preconditioned on
+    the right, flexible (the preconditioner may change between steps) and
+    restarted: the stored directions are dropped after ``restart`` of them.
+
+    A step preconditions the residual, z = precond(r), and forms q = A z.
+    It then orthogonalises q against the stored q_i and applies the same
+    combination to z, so q = A z still holds: beta_i = <q, q_i> / <q_i, q_i>,
+    q -= sum beta_i q_i, z -= sum beta_i z_i (classical Gram-Schmidt, done
+    twice).  alpha = <r, q> / <q, q> then minimises ||r - alpha q||;
+    y += alpha z, r -= alpha q, and (z, q) is stored.  Within a cycle y is
+    the minimum-residual iterate over the span of the preconditioned
+    residuals.  The test is ||x - A y|| < rtol ||x||, the quantity GCR
+    minimises; ``norm`` must be "true".  ``on_z`` (tests) sees every
+    preconditioned residual before orthogonalisation.
+
+    Returns (y, iterations)."""
+    if norm != "true":
+        raise ValueError("GCR stops on the residual itself")
+    y = np.zeros_like(x)
+    r = x.copy()
+    nx = np.linalg.norm(x)
+    if nx == 0.0:
+        return y, 0
+    Zs, Qs, qq = [], [], []
+    for it in range(1, maxit + 1):
+        if len(Zs) == restart:
+            Zs, Qs, qq = [], [], []
+        z = precond(r)
+        if on_z is not None:
+            on_z(z.copy())
+        q = apply_A(z)
+        for _ in range(2):
+            beta = [(q @ qi) / qqi for qi, qqi in zip(Qs, qq)]
+            for b, zi, qi in zip(beta, Zs, Qs):
+                q = q - b * qi
+                z = z - b * zi
+        qn = q @ q
+        alpha = (r @ q) / qn
+        y += alpha * z
+        r -= alpha * q
+        Zs.append(z)
+        Qs.append(q)
+        qq.append(qn)
+        if np.linalg.norm(r) < rtol * nx:
+            return y, it
+    return y, maxit
+
+
 class BlockPreconditioner:
     """Action of the upper block-triangular preconditioner inverse
     (eq. discretestokespc) with the Schur block -S* and A^{-1} -> inner PCG:
@@ -131,7 +184,7 @@ class BlockPreconditioner:
         self.inner_precond = inner_precond
         self.inner_rtol, self.inner_maxit = inner_rtol, inner_maxit
         self.null_p = null_p
-        self.inner = {"pcg": pcg, "fcg": fcg}[inner]
+        self.inner = {"pcg": pcg, "fcg": fcg, "gcr": gcr}[inner]
         self.inner_norm = inner_norm
         self.inner_its = []
 

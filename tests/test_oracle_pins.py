@@ -603,3 +603,115 @@ def test_inner_preconditioned_norm_stopping(solver):
     assert its2 == its and np.linalg.norm(y2 - y) <= 1e-12 * np.linalg.norm(y)
     y3, _ = f(lambda v: A @ v, B, x, 1e-30, maxit=its - 1, norm="true")
     assert not np.linalg.norm(B(x - A @ y3)) < 1e-4 * np.linalg.norm(B(x))
+
+
+def _nonsym(n, seed):
+    g = np.random.default_rng(seed)
+    return 4.0 * np.eye(n) + g.standard_normal((n, n)) / np.sqrt(n)
+
+
+def _min_residual_update(A, r0, Y):
+    """argmin over y in span(Y) of ||r0 - A y|| by dense least squares."""
+    c, *_ = np.linalg.lstsq(A @ Y, r0, rcond=None)
+    return Y @ c
+
+
+def _right_krylov(A, M, r0, j):
+    """Columns spanning M K_j(A M, r0), built from an orthonormal basis of
+    the Krylov space (modified Gram-Schmidt, so that the columns stay well
+    conditioned)."""
+    V = np.zeros((r0.size, j))
+    v = r0 / np.linalg.norm(r0)
+    for i in range(j):
+        V[:, i] = v
+        w = A @ (M @ v)
+        for l in range(i + 1):
+            w = w - (V[:, l] @ w) * V[:, l]
+        v = w / np.linalg.norm(w)
+    return M @ V
+
+
+def test_gcr_is_minimum_residual_over_right_krylov_space():
+    """With a fixed preconditioner M and no restart, GCR's j-th iterate is
+    the minimiser of ||x - A y|| over y in M K_j(A M, x) (its defining
+    property; Eisenstat, Elman & Schultz 1983), here computed by dense least
+    squares on an explicit Krylov basis, for a nonsymmetric A."""
+    n = 30
+    A = _nonsym(n, 31)
+    g = np.random.default_rng(32)
+    M = np.diag(0.5 + g.random(n)) + 0.05 * g.standard_normal((n, n))
+    x = g.standard_normal(n)
+    for j in (1, 2, 5, 9):
+        y, its = krylov.gcr(lambda v: A @ v, lambda r: M @ r, x, 0.0, maxit=j, restart=50)
+        assert its == j
+        ye = _min_residual_update(A, x, _right_krylov(A, M, x, j))
+        assert np.linalg.norm(y - ye) <= 1e-10 * np.linalg.norm(ye)
+        assert abs(np.linalg.norm(x - A @ y) - np.linalg.norm(x - A @ ye)) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_gcr_restart_minimises_per_cycle():
+    """Restarted after m directions, GCR(m) is a sequence of minimum-residual
+    corrections, each over the right Krylov space of the residual left by
+    the previous cycle (cycles of 3, 3 and 1 steps for 7 iterations)."""
+    n = 24
+    A = _nonsym(n, 33)
+    M = np.diag(np.random.default_rng(34).random(n) + 0.5)
+    x = np.random.default_rng(35).standard_normal(n)
+    y, its = krylov.gcr(lambda v: A @ v, lambda r: M @ r, x, 0.0, maxit=7, restart=3)
+    assert its == 7
+    ye = np.zeros(n)
+    for j in (3, 3, 1):
+        r = x - A @ ye
+        ye = ye + _min_residual_update(A, r, _right_krylov(A, M, r, j))
+    assert np.linalg.norm(y - ye) <= 1e-10 * np.linalg.norm(ye)
+
+
+def test_gcr_flexible_minimises_over_preconditioned_residuals():
+    """With a preconditioner that changes at every application, the iterate
+    minimises the residual over the span of the vectors the preconditioner
+    returned (the flexible property the outer and inner solves rely on)."""
+    n = 28
+    A = _nonsym(n, 36)
+    g = np.random.default_rng(37)
+    x = g.standard_normal(n)
+    prec = lambda r: (0.5 + g.random(n)) * r
+    zs = []
+    y, its = krylov.gcr(lambda v: A @ v, prec, x, 0.0, maxit=6, restart=50, on_z=zs.append)
+    assert its == 6 and len(zs) == 6
+    ye = _min_residual_update(A, x, np.array(zs).T)
+    assert np.linalg.norm(y - ye) <= 1e-10 * np.linalg.norm(ye)
+
+
+def test_gcr_stops_at_first_step_below_tolerance():
+    """GCR stops at the first step whose residual is below rtol ||x||; the
+    minimum residual one step earlier is not."""
+    n = 40
+    A = _nonsym(n, 38)
+    M = np.diag(1.0 / np.diag(A))
+    x = np.random.default_rng(39).standard_normal(n)
+    rtol = 1e-7
+    y, its = krylov.gcr(lambda v: A @ v, lambda r: M @ r, x, rtol, maxit=100, restart=100)
+    assert 1 < its < 100
+    assert np.linalg.norm(x - A @ y) < rtol * np.linalg.norm(x)
+    yp = _min_residual_update(A, x, _right_krylov(A, M, x, its - 1))
+    assert not np.linalg.norm(x - A @ yp) < rtol * np.linalg.norm(x)
+    with pytest.raises(ValueError):
+        krylov.gcr(lambda v: A @ v, lambda r: M @ r, x, rtol, norm="preconditioned")
+
+
+def test_gcr_hpmg_residual_monotone():
+    """GCR preconditioned by the hp-multigrid V-cycle on a heterogeneous SIP
+    viscous block: the residual norm never increases from one step to the
+    next (minimum-residual property) and reaches the inner tolerance."""
+    eta, _ = materials.rasterise_box(8, 8, (0.25, 0.75, 0.25, 0.75), 1e4, 1.0)
+    prob = sip.Problem(8, 8, 2, eta, bc=("navier", "navier", "navier", "neumann"))
+    A = sip.assemble_A(prob).tocsr()
+    mg = multigrid.HPMultigrid(prob, A, 1, seed=3)
+    x = np.random.default_rng(40).standard_normal(A.shape[0])
+    res = []
+    for j in range(1, 9):
+        y, _ = krylov.gcr(lambda v: A @ v, mg, x, 0.0, maxit=j)
+        res.append(np.linalg.norm(x - A @ y))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res, res[1:]))
+    y, its = krylov.gcr(lambda v: A @ v, mg, x, 1e-3)
+    assert its < 30 and np.linalg.norm(x - A @ y) < 1e-3 * np.linalg.norm(x)
