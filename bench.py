@@ -64,6 +64,12 @@ def parse():
                          "sweep (extra lines)")
     ap.add_argument("--count", type=int, default=32,
                     help="instances (batch) or requests (serve) in the bounded sample")
+    ap.add_argument("--sinker-inner", default="gcr",
+                    choices=["gcr", "pcg-true", "pcg-preconditioned"],
+                    help="inner Krylov method of the six-sinker sweep: GCR (the paper's, "
+                         "Sec. 7.3) or PCG with either stopping test")
+    ap.add_argument("--sinker-max-eta", type=float, default=1e8,
+                    help="largest viscosity contrast of the six-sinker sweep")
     return ap.parse_args()
 
 
@@ -567,12 +573,18 @@ def run_sinkers(args):
     listed there, rho 1.2 against 1, Neumann top, Navier elsewhere),
     A_hp(Q^2_1) with 2, 3, 4 h-coarsenings at 64^2, 128^2, 256^2, k = 1..3,
     contrasts 1e3, 1e6, 1e8, FP64, outer rtol 1e-6 and inner rtol 1e-3 as in
-    the paper (which ran GCR for both solves; here FGMRES and CG)."""
+    the paper.  The paper ran GCR for both solves; here the outer method is
+    FGMRES (the same minimum-residual iterate for a fixed preconditioner) and
+    the inner one GCR (default) or PCG with either stopping test."""
     import torch
     from paper_1607_03777_gb300 import api, synth
     ctx = api.Context(0)
+    inner = {"gcr": dict(inner_krylov="gcr", inner_norm="true"),
+             "pcg-true": dict(inner_krylov="pcg", inner_norm="true"),
+             "pcg-preconditioned": dict(inner_krylov="pcg", inner_norm="preconditioned")}
+    ikw = inner[args.sinker_inner]
     rows = []
-    for eta_in in (1e3, 1e6, 1e8):
+    for eta_in in [e for e in (1e3, 1e6, 1e8) if e <= args.sinker_max_eta]:
         for n in (64, 128, 256):
             for k in (1, 2, 3):
                 wl = synth.six_sinkers(n=n, k=k, eta_in=eta_in, n_hlevels=synth.levels_to_17(n))
@@ -585,7 +597,7 @@ def run_sinkers(args):
                 pr.rhs_body_force(rho, synth.GRAVITY, f)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                rep = pr.solve(f, u, p, rtol=1e-6, max_outer=500, check=False)
+                rep = pr.solve(f, u, p, rtol=1e-6, max_outer=500, check=False, **ikw)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 rows.append({"eta": eta_in, "elements": f"{n}x{n}", "k": k, "status": rep["status"],
@@ -595,7 +607,7 @@ def run_sinkers(args):
                 del pr
     return {"metric": "six_sinkers_iterations", "unit": "iterations", "rows": rows,
             "config": {"workload": "six sinkers (Sec. 7.3), A_hp(Q2_1), FP64, rtol 1e-6",
-                       "precision": "fp64"}}
+                       "precision": "fp64", "outer": "fgmres", "inner": args.sinker_inner}}
 
 
 def main():

@@ -226,13 +226,20 @@ typedef struct {
     int inner_krylov;   /* 0: automatic (PCG for SIP_PREC_FP64, flexible CG for the *
                          *    mixed forms, whose FP32 V-cycle is not exactly the    *
                          *    same linear operator at every application);          *
-                         *    1: PCG; 2: flexible CG, FCG(1) (device loop only)     */
+                         *    1: PCG; 2: flexible CG, FCG(1) (device loop only);    *
+                         *    3: GCR, restarted after inner_restart directions, the *
+                         *    method of the six-inclusion runs (Sec. 7.3): flexible,*
+                         *    minimises and tests ||t - A y||_2 (inner_norm does   *
+                         *    not apply); device loop only, not with               *
+                         *    SIP_PREC_MIXED_F32_INNER                              */
     int inner_norm;     /* inner stopping test, relative to the first value:        *
                          *    1 (default): the preconditioned residual             *
                          *    ||V(t - A y)||_2, the default test of PETSc's CG     *
                          *    that the paper ran (Sec. 7.1; device loop only);     *
                          *    0: the residual ||t - A y||_2 (needed with           *
                          *    inner_loop 1)                                         */
+    int inner_restart;  /* GCR restart length, 1..64 (default 30); GCR stores      *
+                         *    2 x inner_restart FP64 vectors of n_u on the device  */
 } sip_solve_opts;
 
 typedef struct {
@@ -249,7 +256,7 @@ typedef struct {
 } sip_solve_report;
 
 /* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
- * inner_loop 0, inner_krylov 0, inner_norm 1. */
+ * inner_loop 0, inner_krylov 0, inner_norm 1, inner_restart 30. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES with the upper block-triangular preconditioner

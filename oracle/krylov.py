@@ -175,12 +175,15 @@ def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None
 
 class BlockPreconditioner:
     """Action of the upper block-triangular preconditioner inverse
-    (eq. discretestokespc) with the Schur block -S* and A^{-1} -> inner PCG:
+    (eq. discretestokespc) with the Schur block -S* and A^{-1} -> an inner
+    Krylov solve (PCG, FCG or GCR):
         y_p = -S*^{-1} x_p,   y_u ~= A^{-1} (x_u - B y_p)."""
 
     def __init__(self, A, B, s_diag, inner_precond, inner_rtol=1e-3,
-                 inner_maxit=200, null_p=None, inner="pcg", inner_norm="true"):
+                 inner_maxit=200, null_p=None, inner="pcg", inner_norm="true",
+                 inner_restart=30):
         self.A, self.B, self.s = A, B, s_diag
+        self.inner_kw = {"restart": inner_restart} if inner == "gcr" else {}
         self.inner_precond = inner_precond
         self.inner_rtol, self.inner_maxit = inner_rtol, inner_maxit
         self.null_p = null_p
@@ -196,7 +199,8 @@ class BlockPreconditioner:
             yp = project_out(yp, self.null_p)
         t = xu - self.B @ yp
         yu, its = self.inner(lambda v: self.A @ v, self.inner_precond, t,
-                             self.inner_rtol, self.inner_maxit, norm=self.inner_norm)
+                             self.inner_rtol, self.inner_maxit, norm=self.inner_norm,
+                             **self.inner_kw)
         self.inner_its.append(its)
         return np.concatenate([yu, yp])
 

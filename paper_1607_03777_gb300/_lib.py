@@ -52,6 +52,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_loop", ctypes.c_int),
         ("inner_krylov", ctypes.c_int),
         ("inner_norm", ctypes.c_int),
+        ("inner_restart", ctypes.c_int),
     ]
 
 

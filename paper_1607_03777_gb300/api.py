@@ -224,15 +224,16 @@ class Problem:
     # -- Stokes solve --------------------------------------------------------
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
               max_inner=200, inner_loop="device", inner_krylov="auto",
-              inner_norm="preconditioned", stream=None, check=True):
+              inner_norm="preconditioned", inner_restart=30, stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
         ``check``).  ``inner_loop`` = "device" (one graph launch per inner
         solve) or "host" (host-driven loop); ``inner_krylov`` = "auto",
-        "pcg" or "fcg"; ``inner_norm`` = "preconditioned" (V-cycle applied
+        "pcg", "fcg" or "gcr" (restarted after ``inner_restart`` directions,
+        device loop only); ``inner_norm`` = "preconditioned" (V-cycle applied
         to the residual, the default) or "true" (the residual; required with
-        the host loop)."""
+        the host loop; GCR always tests the residual)."""
         o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
-                  inner_krylov, inner_norm)
+                  inner_krylov, inner_norm, inner_restart)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -267,12 +268,13 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
 
 
 INNER_LOOP = {"device": 0, "host": 1}
-INNER_KRYLOV = {"auto": 0, "pcg": 1, "fcg": 2}
+INNER_KRYLOV = {"auto": 0, "pcg": 1, "fcg": 2, "gcr": 3}
 INNER_NORM = {"true": 0, "preconditioned": 1}
 
 
 def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
-          inner_loop="device", inner_krylov="auto", inner_norm="preconditioned"):
+          inner_loop="device", inner_krylov="auto", inner_norm="preconditioned",
+          inner_restart=30):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
@@ -281,6 +283,7 @@ def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner
     o.inner_krylov = (INNER_KRYLOV[inner_krylov] if isinstance(inner_krylov, str)
                       else int(inner_krylov))
     o.inner_norm = INNER_NORM[inner_norm] if isinstance(inner_norm, str) else int(inner_norm)
+    o.inner_restart = int(inner_restart)
     return o
 
 

@@ -480,6 +480,7 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->inner_loop = 0;
     o->inner_krylov = 0;
     o->inner_norm = 1;
+    o->inner_restart = 30;
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -495,10 +496,13 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
                          o.restart <= 250 &&
                          std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1 &&
                          (o.inner_loop == 0 || o.inner_loop == 1) && o.inner_krylov >= 0 &&
-                         o.inner_krylov <= 2 && !(o.inner_loop == 1 && o.inner_krylov == 2) &&
+                         o.inner_krylov <= 3 && !(o.inner_loop == 1 && o.inner_krylov >= 2) &&
                          (o.inner_norm == 0 || o.inner_norm == 1) &&
                          !(o.inner_loop == 1 && o.inner_norm == 1),
                      "bad solve options");
+        sip::require(o.inner_krylov != 3 || (o.inner_restart >= 1 && o.inner_restart <= 64 &&
+                                             p->desc.precision != SIP_PREC_MIXED_F32_INNER),
+                     "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
         if (st != SIP_OK) {

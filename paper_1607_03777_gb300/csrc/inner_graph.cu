@@ -1,6 +1,6 @@
-// Inner PCG of the block preconditioner (Sec. 5: the viscous block solved
-// to a relative tolerance by CG preconditioned with one hp-multigrid V-cycle)
-// as ONE CUDA graph launch per solve: the iteration is a device-side `while`
+// Inner Krylov solve of the block preconditioner (Sec. 5: the viscous block
+// solved to a relative tolerance by CG -- or GCR, Sec. 7.3 -- preconditioned
+// with one hp-multigrid V-cycle) as ONE CUDA graph launch per solve: the iteration is a device-side `while`
 // conditional node, the stopping test (||r|| < rtol ||t|| or the iteration
 // cap) is taken by a one-block kernel at the end of every pass, and alpha,
 // beta, the norms and the counter stay in device memory.  No host round trip
@@ -29,7 +29,8 @@ struct PcgState {
     const double* t;   // right-hand side (set before each launch)
     double* y;         // iterate (set before each launch)
     double nt, rz, alpha, beta, rr, dq, nz0, nz;
-    int it, status;    // status 0 ok, 1 non-finite
+    int it, status;    // status 0 ok, 1 non-finite (or a GCR direction with A z = 0)
+    int cnt;           // GCR: directions stored in the current cycle
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kRT) k_init_final(PcgState* st, const double* 
         st->rr = nt;
         st->rz = 0.0;
         st->it = 0;
+        st->cnt = 0;
         st->status = isfinite(nt) ? 0 : 1;
         cudaGraphSetConditional(h, (isfinite(nt) && nt > 0.0) ? 1u : 0u);
     }
@@ -318,6 +320,160 @@ __global__ void __launch_bounds__(kRT) k_pn_ctl_final(PcgState* st, const double
     }
 }
 
+
+// ---- GCR (Eisenstat, Elman & Schultz, SIAM J. Numer. Anal. 20, 1983),
+// restarted after m directions, flexible; the method the paper ran for the
+// viscous block of the six-inclusion problem (Sec. 7.3).  A pass: z = V(r),
+// q = A z; q is orthogonalised against the stored q_i with the same
+// combination applied to z (classical Gram-Schmidt, twice), the pair is
+// written to slot cnt of the direction arrays Zs, Qs ([m][n] each), then
+// alpha = <r, q> / <q, q>, y += alpha z, r -= alpha q.  The stopping test is
+// ||r|| < rtol ||t||.  The number of stored pairs is read on the device, so
+// one captured body serves every pass.
+
+constexpr int kGcrMax = 64;   // restart length cap (coefficients in shared memory)
+
+// partial sums <q, Qs[i]> for i < cnt into partial[i * kRB + block]; q is the
+// fixed buffer (first pass) or slot cnt itself (second pass, q == nullptr)
+__global__ void __launch_bounds__(kRT) k_gcr_mdot(size_t n, const double* __restrict__ q,
+                                                  const double* __restrict__ Qs,
+                                                  const PcgState* st, double* partial) {
+    grid_dep_wait();
+    const int cnt = st->cnt;
+    const double* qv = q ? q : Qs + size_t(cnt) * n;
+    for (int i0 = 0; i0 < cnt; i0 += 4) {
+        const int nb = min(4, cnt - i0);
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        const double* Q0 = Qs + size_t(i0) * n;
+        for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+             g += size_t(gridDim.x) * blockDim.x) {
+            const double v = qv[g];
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l < nb) a[l] += v * Q0[size_t(l) * n + g];
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (l < nb) {   // nb is uniform over the block: the barriers inside are safe
+                const double t = block_sum(a[l]);
+                if (threadIdx.x == 0) partial[size_t(i0 + l) * kRB + blockIdx.x] = t;
+            }
+        }
+    }
+}
+
+// beta_i = <q, q_i> / <q_i, q_i>, block i per coefficient
+__global__ void __launch_bounds__(kRT) k_gcr_coef_final(const PcgState* st, const double* partial,
+                                                        const double* qq, double* beta) {
+    grid_dep_wait();
+    const int i = blockIdx.x;
+    if (i >= st->cnt) return;   // uniform over the block
+    const double s = final_sum(partial + size_t(i) * kRB);
+    if (threadIdx.x == 0) beta[i] = s / qq[i];
+}
+
+// Qs[cnt] = q - sum_i beta_i Qs[i], Zs[cnt] = z - sum_i beta_i Zs[i] (q, z the
+// fixed buffers on the first pass; slot cnt in place on the second, z ==
+// nullptr).  On the last pass also the partial sums of <q, q> and <r, q>.
+__global__ void __launch_bounds__(kRT) k_gcr_orth(size_t n, const double* __restrict__ z,
+                                                  const double* __restrict__ q, double* Zs,
+                                                  double* Qs, const double* __restrict__ r,
+                                                  const PcgState* st, const double* beta,
+                                                  int last, double* partial) {
+    grid_dep_wait();
+    __shared__ double sb[kGcrMax];
+    const int cnt = st->cnt;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sb[i] = beta[i];
+    __syncthreads();
+    double* zo = Zs + size_t(cnt) * n;
+    double* qo = Qs + size_t(cnt) * n;
+    const double* zi = z ? z : zo;
+    const double* qi = q ? q : qo;
+    double a1 = 0.0, a2 = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        double zv = zi[g], qv = qi[g];
+        for (int i = 0; i < cnt; ++i) {
+            const double b = sb[i];
+            zv -= b * Zs[size_t(i) * n + g];
+            qv -= b * Qs[size_t(i) * n + g];
+        }
+        zo[g] = zv;
+        qo[g] = qv;
+        if (last) {
+            a1 += qv * qv;
+            a2 += r[g] * qv;
+        }
+    }
+    if (last) {
+        a1 = block_sum(a1);
+        a2 = block_sum(a2);
+        if (threadIdx.x == 0) {
+            partial[blockIdx.x] = a1;
+            partial[kRB + blockIdx.x] = a2;
+        }
+    }
+}
+
+// alpha = <r, q> / <q, q>; <q, q> kept for the later coefficients
+__global__ void __launch_bounds__(kRT) k_gcr_alpha_final(PcgState* st, const double* partial,
+                                                         double* qq) {
+    grid_dep_wait();
+    const double qn = final_sum(partial);
+    const double rq = final_sum(partial + kRB);
+    if (threadIdx.x == 0) {
+        const int cnt = st->cnt;
+        qq[cnt] = qn;
+        if (!(qn > 0.0) || !isfinite(qn) || !isfinite(rq)) {
+            st->status = 1;
+            st->alpha = 0.0;
+        } else {
+            st->alpha = rq / qn;
+        }
+    }
+}
+
+// y += alpha Zs[cnt]; r -= alpha Qs[cnt]; partial sums of r.r
+__global__ void __launch_bounds__(kRT) k_gcr_step(size_t n, const double* __restrict__ Zs,
+                                                  const double* __restrict__ Qs, double* r,
+                                                  const PcgState* st, double* partial) {
+    grid_dep_wait();
+    const double a = st->alpha;
+    const int cnt = st->cnt;
+    const double* zc = Zs + size_t(cnt) * n;
+    const double* qc = Qs + size_t(cnt) * n;
+    double* y = st->y;
+    double acc = 0.0;
+    for (size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+         g += size_t(gridDim.x) * blockDim.x) {
+        y[g] += a * zc[g];
+        const double rv = r[g] - a * qc[g];
+        r[g] = rv;
+        acc += rv * rv;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// end of a GCR pass: counter, next slot (restart after m), stopping test
+__global__ void __launch_bounds__(kRT) k_gcr_ctl_final(PcgState* st, const double* partial,
+                                                       double rtol, int maxit, int m,
+                                                       cudaGraphConditionalHandle h) {
+    grid_dep_wait();
+    const double s = final_sum(partial);
+    if (threadIdx.x == 0) {
+        const double rr = sqrt(s);
+        const int it = st->it + 1;
+        st->it = it;
+        st->rr = rr;
+        const int c = st->cnt + 1;
+        st->cnt = c == m ? 0 : c;
+        if (!isfinite(rr)) st->status = 1;
+        const bool more = st->status == 0 && !(rr < rtol * st->nt) && it < maxit;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
 inline unsigned nblk(size_t n) { return unsigned((n + 255) / 256); }
 
 }  // namespace
@@ -331,6 +487,9 @@ struct InnerLoop {
     bool mixed = false;
     bool flexible = false;
     bool pnorm = false;   // stop on the preconditioned residual
+    int gcr = 0;          // GCR restart length (0: a CG variant)
+    const void* gcr_buf = nullptr;
+    DeviceBuffer gcr_coef;   // beta[kGcrMax], <q_i, q_i>[kGcrMax]
     double rtol = -1.0;
     int maxit = -1;
     int gen = -1;
@@ -455,6 +614,54 @@ void capture_body_pnorm(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphCon
     SIP_CHECK_LAUNCH();
 }
 
+// One GCR pass (see the kernels above).
+void capture_body_gcr(sip_problem* P, Workspace& W, InnerLoop& L, cudaGraphConditionalHandle h,
+                      cudaStream_t cs) {
+    const size_t n_u = size_t(P->n_u);
+    double* r = W.cg_r.as<double>();
+    double* q = W.cg_q.as<double>();
+    double* z = W.cg_z.as<double>();
+    double* Zs = W.gcr_z.as<double>();
+    double* Qs = W.gcr_q.as<double>();
+    double* part = L.partial.as<double>();
+    double* beta = L.gcr_coef.as<double>();
+    double* qq = beta + kGcrMax;
+    PcgState* st = L.state.as<PcgState>();
+    if (L.mixed) {
+        Multigrid<float>& mg = *P->mg32;
+        float* vin = mg.vin.as<float>();
+        float* vout = mg.vout.as<float>();
+        launch_cast<double, float>(n_u, r, vin, cs);
+        mg.vcycle_on(vin, vout, cs);
+        launch_cast<float, double>(n_u, vout, z, cs);
+    } else {
+        P->mg64->vcycle_on(r, z, cs);
+    }
+    launch_apply_sip<double>(P->n, P->geom, z, q, P->eta_d.as<double>(), 1.0, nullptr, 0.0, cs);
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool first = pass == 0;
+        launch_k(k_gcr_mdot, kRB, kRT, 0, cs, n_u, first ? static_cast<const double*>(q) : nullptr,
+                 static_cast<const double*>(Qs), static_cast<const PcgState*>(st), part);
+        SIP_CHECK_LAUNCH();
+        launch_k(k_gcr_coef_final, unsigned(L.gcr), kRT, 0, cs, static_cast<const PcgState*>(st),
+                 static_cast<const double*>(part), static_cast<const double*>(qq), beta);
+        SIP_CHECK_LAUNCH();
+        launch_k(k_gcr_orth, kRB, kRT, 0, cs, n_u, first ? static_cast<const double*>(z) : nullptr,
+                 first ? static_cast<const double*>(q) : nullptr, Zs, Qs,
+                 static_cast<const double*>(r), static_cast<const PcgState*>(st),
+                 static_cast<const double*>(beta), first ? 0 : 1, part);
+        SIP_CHECK_LAUNCH();
+    }
+    launch_k(k_gcr_alpha_final, 1, kRT, 0, cs, st, static_cast<const double*>(part), qq);
+    SIP_CHECK_LAUNCH();
+    launch_k(k_gcr_step, kRB, kRT, 0, cs, n_u, static_cast<const double*>(Zs),
+             static_cast<const double*>(Qs), r, static_cast<const PcgState*>(st), part);
+    SIP_CHECK_LAUNCH();
+    launch_k(k_gcr_ctl_final, 1, kRT, 0, cs, st, static_cast<const double*>(part), L.rtol, L.maxit,
+             L.gcr, h);
+    SIP_CHECK_LAUNCH();
+}
+
 void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
     // plain launches inside the graph that holds the conditional node
     PdlOffScope pdl_off;
@@ -487,7 +694,7 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
         e = cudaGetLastError();
     }
     int64_t pre_kernels = 2;
-    if (e == cudaSuccess && L.pnorm) {   // z_0 = V(r_0) and its norm before the loop
+    if (e == cudaSuccess && L.pnorm && !L.gcr) {   // z_0 = V(r_0), its norm, before the loop
         const int64_t c0 = launch_counter();
         try {
             vcycle_dots(P, W, L, W.cg_r.as<double>(), L.cs);
@@ -525,7 +732,9 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
                                            cudaStreamCaptureModeThreadLocal));
     const int64_t b0 = launch_counter();
     try {
-        if (L.pnorm)
+        if (L.gcr)
+            capture_body_gcr(P, W, L, h, L.cs);
+        else if (L.pnorm)
             capture_body_pnorm(P, W, L, h, L.cs);
         else
             capture_body(P, W, L, h, L.cs);
@@ -545,24 +754,34 @@ void build_loop(sip_problem* P, Workspace& W, InnerLoop& L, cudaStream_t s) {
 }  // namespace
 
 int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, bool pnorm,
-                    const double* t, double* y, double rtol, int maxit, cudaStream_t s) {
+                    const double* t, double* y, double rtol, int maxit, cudaStream_t s,
+                    int gcr_restart) {
     maxit = std::max(1, std::min(maxit, 100000));
     const size_t n_u = size_t(P->n_u);
     for (DeviceBuffer* b : {&W.cg_r, &W.cg_d, &W.cg_q, &W.cg_z}) b->alloc(n_u * sizeof(double));
     if (!W.loop) W.loop.reset(new InnerLoop());
     InnerLoop& L = *W.loop;
     static_assert(sizeof(PcgState) <= 256 * sizeof(double), "state fits the pinned block");
+    if (gcr_restart < 0 || gcr_restart > kGcrMax) throw Error(SIP_ERR_INVALID_ARG, "GCR restart");
     L.state.alloc(sizeof(PcgState));
-    L.partial.alloc(2 * kRB * sizeof(double));
+    L.partial.alloc(size_t(std::max(2, gcr_restart)) * kRB * sizeof(double));
+    if (gcr_restart) {
+        W.gcr_z.alloc(size_t(gcr_restart) * n_u * sizeof(double));
+        W.gcr_q.alloc(size_t(gcr_restart) * n_u * sizeof(double));
+        L.gcr_coef.alloc(2 * kGcrMax * sizeof(double));
+    }
     const void* mg = mixed ? static_cast<const void*>(P->mg32.get())
                            : static_cast<const void*>(P->mg64.get());
     const int gen = mixed ? P->mg32->setup_gen : P->mg64->setup_gen;
+    const void* gbuf = gcr_restart ? W.gcr_z.ptr : nullptr;
     if (!L.exec || L.mixed != mixed || L.flexible != flexible || L.pnorm != pnorm ||
-        L.rtol != rtol ||
+        L.gcr != gcr_restart || L.gcr_buf != gbuf || L.rtol != rtol ||
         L.maxit != maxit || L.gen != gen || L.mg != mg) {
         L.mixed = mixed;
         L.flexible = flexible;
         L.pnorm = pnorm;
+        L.gcr = gcr_restart;
+        L.gcr_buf = gbuf;
         L.rtol = rtol;
         L.maxit = maxit;
         L.gen = gen;
@@ -576,7 +795,9 @@ int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, boo
     SIP_CUDA(cudaStreamSynchronize(s));
     const PcgState& hs = *reinterpret_cast<const PcgState*>(L.hs.p);
     launch_counter() += L.top_kernels + L.body_kernels * hs.it;
-    if (hs.status != 0) throw Error(SIP_ERR_BREAKDOWN, "non-finite inner residual");
+    if (hs.status != 0)
+        throw Error(SIP_ERR_BREAKDOWN, gcr_restart ? "inner GCR breakdown (non-finite or A z = 0)"
+                                                   : "non-finite inner residual");
     return hs.it;
 }
 

@@ -171,6 +171,7 @@ struct Workspace {
     size_t n = 0;
     DeviceBuffer V, Z, w, x, r, b, tu, yu64, sinv, ws, sc, hbuf;
     DeviceBuffer cg_r, cg_d, cg_q, cg_z, sc_in;   // FP64 inner PCG of the mixed form
+    DeviceBuffer gcr_z, gcr_q;                    // inner GCR directions [m][n_u] each
     DeviceBuffer t32, y32;                        // FP32 inner PCG (SIP_PREC_MIXED_F32_INNER)
     HostScalars hs, hs_in;
     std::unique_ptr<InnerLoop, InnerLoopDeleter> loop;
@@ -187,9 +188,12 @@ int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, do
 // The same inner solve (FP64 iterate; V-cycle in FP32 when mixed, else FP64)
 // as one graph launch with a device-side loop; returns the iteration count.
 // flexible: FCG(1) directions instead of PCG's; pnorm: stop on the
-// preconditioned residual ||V r|| instead of ||r||.
+// preconditioned residual ||V r|| instead of ||r||; gcr_restart > 0: GCR
+// restarted after that many directions (<= 64) instead of CG, stopping on
+// ||r|| (flexible and pnorm are then ignored).
 int inner_pcg_graph(sip_problem* P, Workspace& W, bool mixed, bool flexible, bool pnorm,
-                    const double* t, double* y, double rtol, int maxit, cudaStream_t s);
+                    const double* t, double* y, double rtol, int maxit, cudaStream_t s,
+                    int gcr_restart = 0);
 
 sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,

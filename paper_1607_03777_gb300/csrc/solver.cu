@@ -907,7 +907,8 @@ int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, do
 int64_t Workspace::bytes() const {
     return int64_t(V.bytes + Z.bytes + w.bytes + x.bytes + r.bytes + b.bytes + tu.bytes +
                    yu64.bytes + sinv.bytes + ws.bytes + sc.bytes + hbuf.bytes + cg_r.bytes +
-                   cg_d.bytes + cg_q.bytes + cg_z.bytes + sc_in.bytes);
+                   cg_d.bytes + cg_q.bytes + cg_z.bytes + sc_in.bytes + gcr_z.bytes +
+                   gcr_q.bytes);
 }
 
 namespace {
@@ -1000,8 +1001,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
     // the inner PCG runs as one graph launch with a device-side loop unless
     // the options ask for the host-driven loop (same arithmetic)
     const bool host_loop = o.inner_loop == 1;
-    // flexible CG where the V-cycle is FP32 (automatic choice), else PCG
+    // flexible CG where the V-cycle is FP32 (automatic choice), else PCG;
+    // inner_krylov 3: GCR restarted after inner_restart directions
     const bool flexible = o.inner_krylov == 2 || (o.inner_krylov == 0 && mixed && !host_loop);
+    const int gcr_restart = o.inner_krylov == 3 ? o.inner_restart : 0;
     // z = P^{-1} v
     auto precond = [&](const double* v, double* z) {
         launch_vmul<double>(n_p, v + n_u, W.sinv.as<double>(), z + n_u, s);   // y_p = -S*^{-1} v_p
@@ -1020,7 +1023,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                                              nullptr);
         } else {
             its = inner_pcg_graph(P, W, mixed, flexible, o.inner_norm == 1, W.tu.as<double>(), z,
-                                  o.inner_rtol, o.max_inner, s);
+                                  o.inner_rtol, o.max_inner, s, gcr_restart);
         }
         inner_total += its;
         inner_max = std::max(inner_max, its);

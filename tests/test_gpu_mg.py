@@ -354,3 +354,53 @@ def test_solve_inner_preconditioned_norm(ctx, precision):
         _, its, _ = krylov.fgmres(lambda v: K @ v, pc, b, 1e-8, restart=100, maxit=1000)
         assert abs(rep["outer_its"] - its) <= 1
         assert abs(rep["inner_avg"] - np.mean(pc.inner_its)) <= 0.5
+
+
+@pytest.mark.parametrize("precision,restart", [("fp64", 30), ("fp64", 3), ("mixed", 30)])
+def test_solve_inner_gcr(ctx, precision, restart):
+    """Inner solves by restarted GCR (the method of the six-inclusion runs,
+    Sec. 7.3), on the device loop: the Stokes solve reaches the 1e-8 true
+    residual and the sparse-direct solution; in FP64 the outer and inner
+    iteration counts follow the oracle's FGMRES with inner GCR of the same
+    restart length."""
+    nx = ny = 16
+    k = 3
+    wl = synth.single_box_inclusion(nx, k, 1e4, n_hlevels=1)
+    eta, rho = materials.rasterise_inclusions(nx, ny, wl.shapes)
+    prob, ref = pair(ctx, nx, ny, k, wl.bc, eta, nh=1, seed=1, precision=precision)
+    f = sip.rhs_body_force(ref, rho)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-8, max_outer=1000, inner_krylov="gcr",
+                     inner_restart=restart)
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.05e-8, rep
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-5
+    if restart == 3:
+        assert rep["inner_max"] > 3, rep   # the restart was exercised
+    if precision == "fp64":
+        mg = multigrid.HPMultigrid(ref, A, 1, seed=1)
+        pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(ref), mg, inner="gcr",
+                                        inner_restart=restart)
+        K = krylov.stokes_matrix(A, B).tocsr()
+        b = np.concatenate([f, np.zeros(B.shape[1])])
+        _, its, _ = krylov.fgmres(lambda v: K @ v, pc, b, 1e-8, restart=100, maxit=1000)
+        assert abs(rep["outer_its"] - its) <= 1, (rep, its)
+        assert abs(rep["inner_avg"] - np.mean(pc.inner_its)) <= 0.5, (rep, np.mean(pc.inner_its))
+
+
+def test_gcr_options_rejected(ctx):
+    """GCR runs on the device loop only, with 1 <= inner_restart <= 64."""
+    nx = ny = 8
+    eta = np.ones(nx * ny)
+    prob = api.Problem(ctx, nx, ny, 2, eta, n_hlevels=1, seed=1)
+    f = torch.ones(prob.n_u, dtype=torch.float64, device="cuda")
+    u = torch.empty_like(f)
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    for kw in ({"inner_loop": "host", "inner_norm": "true"}, {"inner_restart": 0},
+               {"inner_restart": 65}):
+        with pytest.raises(api.SipError):
+            prob.solve(f, u, p, inner_krylov="gcr", **kw)
+    rep = prob.solve(f, u, p, inner_krylov="gcr", inner_restart=64)
+    assert rep["status"] == 0
