@@ -10,6 +10,9 @@ Test infrastructure only (see ``oracle/__init__``).
 * ``gcr``           generalised conjugate residual, right-preconditioned,
   flexible, restarted: the Krylov method the paper ran for the viscous block
   of the six-inclusion problem (Sec. 7.3); stops on the residual itself.
+* ``gcr_outer``     the same GCR as the outer Stokes solve with the block
+  preconditioner (the paper's outer method for the six inclusions), with
+  the true residual checked whenever the recurrence reports convergence.
 * ``fgmres``        right-preconditioned flexible GMRES (Saad's FGMRES) on the
   saddle system with the upper block-triangular preconditioner of
   eq. discretestokespc, S replaced by the diagonal S* (Sec. 5), and
@@ -123,7 +126,7 @@ def fcg(apply_A, precond, x, rtol, maxit=200, norm="true"):
     return y, maxit
 
 
-def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None):
+def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None, proj=None):
     """Generalised conjugate residual method (Eisenstat, Elman & Schultz,
     SIAM J. Numer. Anal. 20, 1983) for A y = x from y = 0, preconditioned on
     the right, flexible (the preconditioner may change between steps) and
@@ -138,7 +141,9 @@ def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None
     the minimum-residual iterate over the span of the preconditioned
     residuals.  The test is ||x - A y|| < rtol ||x||, the quantity GCR
     minimises; ``norm`` must be "true".  ``on_z`` (tests) sees every
-    preconditioned residual before orthogonalisation.
+    preconditioned residual before orthogonalisation; ``proj`` (the Stokes
+    solve without a Neumann side) is applied to z and to q = A z, keeping
+    the constant pressure out of both (Sec. 5).
 
     Returns (y, iterations)."""
     if norm != "true":
@@ -153,9 +158,13 @@ def gcr(apply_A, precond, x, rtol, maxit=200, norm="true", restart=30, on_z=None
         if len(Zs) == restart:
             Zs, Qs, qq = [], [], []
         z = precond(r)
+        if proj is not None:
+            z = proj(z)
         if on_z is not None:
             on_z(z.copy())
         q = apply_A(z)
+        if proj is not None:
+            q = proj(q)
         for _ in range(2):
             beta = [(q @ qi) / qqi for qi, qqi in zip(Qs, qq)]
             for b, zi, qi in zip(beta, Zs, Qs):
@@ -274,3 +283,36 @@ def fgmres(apply_K, precond, b, rtol, restart=100, maxit=200, null_p=None, n_u=N
         if np.linalg.norm(r) <= rtol * beta0:
             break
     return x, total, hist
+
+
+def gcr_outer(apply_K, precond, b, rtol, restart=100, maxit=200, null_p=None, n_u=None):
+    """GCR (``gcr``) on the saddle system K x = b from x = 0 with the block
+    preconditioner: stops when ||b - K x||_2 <= rtol ||b||_2 for the residual
+    recomputed from x.  Each call of ``gcr`` solves for a correction of the
+    current residual r = b - K x to the absolute level rtol ||b||; when the
+    recurrence's residual meets it but the recomputed one does not, GCR
+    starts again from the recomputed residual.  ``null_p`` as in ``fgmres``.
+    Returns (x, iterations)."""
+    x = np.zeros(b.size)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0
+
+    def proj(v):
+        if null_p is None:
+            return v
+        v = v.copy()
+        v[n_u:] = project_out(v[n_u:], null_p)
+        return v
+
+    total = 0
+    while total < maxit:
+        r = proj(b - apply_K(x))
+        nr = np.linalg.norm(r)
+        if nr <= rtol * nb:
+            break
+        dx, its = gcr(apply_K, precond, r, rtol * nb / nr, maxit - total, restart=restart,
+                      proj=proj if null_p is not None else None)
+        x = x + dx
+        total += its
+    return x, total

@@ -715,3 +715,52 @@ def test_gcr_hpmg_residual_monotone():
     assert all(b <= a * (1 + 1e-12) for a, b in zip(res, res[1:]))
     y, its = krylov.gcr(lambda v: A @ v, mg, x, 1e-3)
     assert its < 30 and np.linalg.norm(x - A @ y) < 1e-3 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("sign", [-1.0, 1.0])
+def test_gcr_outer_exact_block_preconditioner_two_iterations(sign):
+    """The outer GCR with the exact block preconditioner (either Schur sign)
+    converges in at most 2 iterations, like FGMRES: the preconditioned
+    saddle operator has a minimal polynomial of degree 2 (Sec. 5), and GCR
+    minimises the residual over the same space for a fixed preconditioner."""
+    pr = _prob(3, 3, 2, ("navier", "navier", "navier", "neumann"), seed=4)
+    A, B = sip.assemble_A(pr).toarray(), sip.assemble_B(pr).toarray()
+    Ainv = np.linalg.inv(A)
+    Sinv = np.linalg.inv(sign * (B.T @ Ainv @ B))
+    n_u = A.shape[0]
+    K = np.block([[A, B], [B.T, np.zeros((B.shape[1],) * 2)]])
+    b = np.random.default_rng(0).standard_normal(K.shape[0])
+
+    def prec(x):
+        yp = Sinv @ x[n_u:]
+        return np.concatenate([Ainv @ (x[:n_u] - B @ yp), yp])
+
+    x, its = krylov.gcr_outer(lambda v: K @ v, prec, b, 1e-10)
+    assert its <= 3
+    assert np.linalg.norm(b - K @ x) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_gcr_outer_hpmg_singular_pressure_solves_to_direct_solution():
+    """GCR outer and inner with the hp-multigrid V-cycle on an all-Dirichlet
+    problem (constant pressure in the null space, projected out): reaches
+    the sparse-direct solution, and the iteration count is that of FGMRES
+    with the same preconditioner to within two (both minimise the residual;
+    the spaces differ only through the inexact inner solve)."""
+    sol = exact.SmoothDirichlet()
+    pr = sip.Problem(8, 8, 2, np.ones(64), bc=("dirichlet",) * 4)
+    A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+    f = sip.rhs_force(pr, sol.f)
+    mg = multigrid.HPMultigrid(pr, A, 1, seed=7)
+    null = sip.pressure_constant(pr)
+    K = krylov.stokes_matrix(A, B)
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    n_u = A.shape[0]
+    Pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3, null_p=null, inner="gcr")
+    x, its = krylov.gcr_outer(lambda v: K @ v, Pc, b, 1e-10, null_p=null, n_u=n_u)
+    Pf = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3, null_p=null, inner="gcr")
+    _, its_f, _ = krylov.fgmres(lambda v: K @ v, Pf, b, 1e-10, null_p=null, n_u=n_u)
+    u, p = krylov.solve_direct(pr, A, B, f)
+    assert abs(its - its_f) <= 2, (its, its_f)
+    assert np.linalg.norm(b - K @ x) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(x[:n_u] - u) <= 1e-8 * np.linalg.norm(u)
+    assert abs(null @ x[n_u:]) <= 1e-10 * np.linalg.norm(x[n_u:]) * np.linalg.norm(null)
