@@ -232,14 +232,22 @@ typedef struct {
                          *    minimises and tests ||t - A y||_2 (inner_norm does   *
                          *    not apply); device loop only, not with               *
                          *    SIP_PREC_MIXED_F32_INNER                              */
-    int inner_norm;     /* inner stopping test, relative to the first value:        *
-                         *    1 (default): the preconditioned residual             *
+    int inner_norm;     /* inner stopping test of the CG variants, relative to the  *
+                         *    first value: 0 (default): the residual               *
+                         *    ||t - A y||_2, whose outer iteration counts stay      *
+                         *    flat in the viscosity contrast (six inclusions,       *
+                         *    Sec. 7.3); 1: the preconditioned residual            *
                          *    ||V(t - A y)||_2, the default test of PETSc's CG     *
-                         *    that the paper ran (Sec. 7.1; device loop only);     *
-                         *    0: the residual ||t - A y||_2 (needed with           *
-                         *    inner_loop 1)                                         */
+                         *    that the paper ran for SolCx (Sec. 7.1): fewer       *
+                         *    V-cycles on a single inclusion, but the outer count  *
+                         *    grows with the contrast on the six inclusions (device *
+                         *    loop only)                                            */
     int inner_restart;  /* GCR restart length, 1..64 (default 30); GCR stores      *
                          *    2 x inner_restart FP64 vectors of n_u on the device  */
+    int outer_krylov;   /* 0: FGMRES (default); 1: GCR, restarted after `restart`  *
+                         *    directions, the outer method of the six-inclusion    *
+                         *    runs (Sec. 7.3); both minimise the residual, both     *
+                         *    stop on the residual recomputed from x               */
 } sip_solve_opts;
 
 typedef struct {
@@ -256,15 +264,17 @@ typedef struct {
 } sip_solve_report;
 
 /* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
- * inner_loop 0, inner_krylov 0, inner_norm 1, inner_restart 30. */
+ * inner_loop 0, inner_krylov 0, inner_norm 0, inner_restart 30,
+ * outer_krylov 0. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
- * preconditioned FGMRES with the upper block-triangular preconditioner
- * (eq. discretestokespc) whose Schur block is the saddle matrix's own Schur
- * complement -B^T A^{-1} B approximated by -S*, S* the pressure mass scaled by
- * 1/eta_K (diagonal, Sec. 5): y_p = -S*^{-1} x_p,
- * y_u ~ A^{-1}(x_u - B y_p) by the inner PCG with the
- * hp-multigrid V-cycle.  Orthogonalisation: classical Gram-Schmidt twice.
+ * preconditioned FGMRES (or GCR, opts->outer_krylov) with the upper
+ * block-triangular preconditioner (eq. discretestokespc) whose Schur block is
+ * the saddle matrix's own Schur complement -B^T A^{-1} B approximated by -S*,
+ * S* the pressure mass scaled by 1/eta_K (diagonal, Sec. 5): y_p = -S*^{-1}
+ * x_p, y_u ~ A^{-1}(x_u - B y_p) by the inner Krylov solve (PCG, FCG or
+ * GCR) with the hp-multigrid V-cycle.  Orthogonalisation: classical
+ * Gram-Schmidt twice.
  * Without a Neumann side the constant pressure is projected out of every
  * pressure vector and p is returned with zero mean (Sec. 5).  g_p may be NULL
  * (g = 0, eq. rhs_f).  Outer state, residuals and S* are FP64; the

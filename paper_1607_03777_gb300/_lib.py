@@ -53,6 +53,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_krylov", ctypes.c_int),
         ("inner_norm", ctypes.c_int),
         ("inner_restart", ctypes.c_int),
+        ("outer_krylov", ctypes.c_int),
     ]
 
 

@@ -224,16 +224,18 @@ class Problem:
     # -- Stokes solve --------------------------------------------------------
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
               max_inner=200, inner_loop="device", inner_krylov="auto",
-              inner_norm="preconditioned", inner_restart=30, stream=None, check=True):
+              inner_norm="true", inner_restart=30, outer_krylov="fgmres",
+              stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
         ``check``).  ``inner_loop`` = "device" (one graph launch per inner
         solve) or "host" (host-driven loop); ``inner_krylov`` = "auto",
         "pcg", "fcg" or "gcr" (restarted after ``inner_restart`` directions,
-        device loop only); ``inner_norm`` = "preconditioned" (V-cycle applied
-        to the residual, the default) or "true" (the residual; required with
-        the host loop; GCR always tests the residual)."""
+        device loop only); ``inner_norm`` = "true" (the residual, the
+        default; GCR always tests it) or "preconditioned" (the V-cycle
+        applied to the residual; device loop only); ``outer_krylov`` =
+        "fgmres" (default) or "gcr"."""
         o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
-                  inner_krylov, inner_norm, inner_restart)
+                  inner_krylov, inner_norm, inner_restart, outer_krylov)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -270,11 +272,12 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
 INNER_LOOP = {"device": 0, "host": 1}
 INNER_KRYLOV = {"auto": 0, "pcg": 1, "fcg": 2, "gcr": 3}
 INNER_NORM = {"true": 0, "preconditioned": 1}
+OUTER_KRYLOV = {"fgmres": 0, "gcr": 1}
 
 
 def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
-          inner_loop="device", inner_krylov="auto", inner_norm="preconditioned",
-          inner_restart=30):
+          inner_loop="device", inner_krylov="auto", inner_norm="true",
+          inner_restart=30, outer_krylov="fgmres"):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
@@ -284,6 +287,8 @@ def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner
                       else int(inner_krylov))
     o.inner_norm = INNER_NORM[inner_norm] if isinstance(inner_norm, str) else int(inner_norm)
     o.inner_restart = int(inner_restart)
+    o.outer_krylov = (OUTER_KRYLOV[outer_krylov] if isinstance(outer_krylov, str)
+                      else int(outer_krylov))
     return o
 
 

@@ -479,8 +479,9 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->max_inner = 200;
     o->inner_loop = 0;
     o->inner_krylov = 0;
-    o->inner_norm = 1;
+    o->inner_norm = 0;
     o->inner_restart = 30;
+    o->outer_krylov = 0;
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -503,6 +504,7 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
         sip::require(o.inner_krylov != 3 || (o.inner_restart >= 1 && o.inner_restart <= 64 &&
                                              p->desc.precision != SIP_PREC_MIXED_F32_INNER),
                      "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
+        sip::require(o.outer_krylov == 0 || o.outer_krylov == 1, "outer_krylov is 0 or 1");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
         st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
         if (st != SIP_OK) {

@@ -1046,7 +1046,72 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         throw Error(SIP_ERR_INVALID_ARG, "non-finite right-hand side");
     }
     std::vector<double> H(size_t(restart + 1) * restart), cs(restart), sn(restart), gv(restart + 1);
-    while (st == SIP_ERR_NOT_CONVERGED && total < o.max_outer) {
+    if (o.outer_krylov == 1 && st == SIP_ERR_NOT_CONVERGED) {
+        // GCR (Eisenstat, Elman & Schultz 1983), the outer method of the
+        // six-inclusion runs (Sec. 7.3): z_j = P^{-1} r, q_j = K z_j, both
+        // orthogonalised against the stored pairs (classical Gram-Schmidt
+        // twice, coefficients on the device) and scaled to ||q_j|| = 1;
+        // x += <r, q_j> z_j, r -= <r, q_j> q_j.  The pairs live in V (q) and
+        // Z (z) and are dropped after `restart` of them; whenever the
+        // recurrence's residual meets the tolerance, the residual is
+        // recomputed from x and GCR continues from it if it does not.
+        double* sq = sc + restart + 1;     // ||q_j||^2
+        double* sa = sc + restart + 2;     // <r, q_j>
+        double* sone = sc + restart + 3;   // 1.0
+        static const double one = 1.0;
+        SIP_CUDA(cudaMemcpyAsync(sone, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+        bool broke = false;
+        for (;;) {
+            applyK(x, r);
+            launch_axpby<double>(n, 1.0, b, -1.0, r, s);
+            project(r);
+            const double rn = norm(r);
+            rel = rn / beta0;
+            if (!std::isfinite(rn)) {
+                st = SIP_ERR_BREAKDOWN;
+                break;
+            }
+            if (rn <= o.rtol * beta0) {
+                st = SIP_OK;
+                break;
+            }
+            if (broke) {
+                st = SIP_ERR_BREAKDOWN;
+                break;
+            }
+            if (total >= o.max_outer) break;
+            int j = 0;
+            while (total < o.max_outer) {
+                if (j == restart) j = 0;
+                double* zj = Z + size_t(j) * n;
+                double* qj = V + size_t(j) * n;
+                precond(r, zj);
+                applyK(zj, qj);
+                project(qj);
+                if (j > 0) {
+                    for (int pass = 0; pass < 2; ++pass) {
+                        launch_mdot<double>(j, n, V, n, qj, sc, wsd, s);
+                        launch_maxpy<double>(j, n, V, n, sc, -1.0, qj, s);
+                        launch_maxpy<double>(j, n, Z, n, sc, -1.0, zj, s);
+                    }
+                }
+                launch_dot<double>(n, qj, qj, sq, wsd, s);
+                launch_scale_inv_sqrt<double>(n, sq, qj, s);
+                launch_scale_inv_sqrt<double>(n, sq, zj, s);
+                launch_dot<double>(n, r, qj, sa, wsd, s);
+                launch_pcg_update<double>(n, zj, qj, x, r, sa, sone, s);
+                ++total;
+                ++j;
+                const double rr = norm(r);   // non-finite after a breakdown (q_j = 0)
+                if (!std::isfinite(rr)) {
+                    broke = true;
+                    break;
+                }
+                if (rr <= o.rtol * beta0) break;
+            }
+        }
+    }
+    while (o.outer_krylov == 0 && st == SIP_ERR_NOT_CONVERGED && total < o.max_outer) {
         const double beta = norm(r);
         if (!std::isfinite(beta)) {
             st = SIP_ERR_BREAKDOWN;

@@ -404,3 +404,52 @@ def test_gcr_options_rejected(ctx):
             prob.solve(f, u, p, inner_krylov="gcr", **kw)
     rep = prob.solve(f, u, p, inner_krylov="gcr", inner_restart=64)
     assert rep["status"] == 0
+
+
+@pytest.mark.parametrize("inner", ["gcr", "pcg"])
+def test_solve_outer_gcr(ctx, inner):
+    """GCR as the outer method (the paper's choice for the six inclusions,
+    Sec. 7.3): reaches the 1e-8 true residual and the sparse-direct
+    solution, and its outer and inner iteration counts follow the oracle's
+    outer GCR with the same inner method."""
+    nx = ny = 16
+    k = 3
+    wl = synth.single_box_inclusion(nx, k, 1e4, n_hlevels=1)
+    eta, rho = materials.rasterise_inclusions(nx, ny, wl.shapes)
+    prob, ref = pair(ctx, nx, ny, k, wl.bc, eta, nh=1, seed=1)
+    f = sip.rhs_body_force(ref, rho)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-8, max_outer=1000, outer_krylov="gcr",
+                     inner_krylov=inner, inner_norm="true")
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.05e-8, rep
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-5
+    mg = multigrid.HPMultigrid(ref, A, 1, seed=1)
+    pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(ref), mg, inner=inner)
+    K = krylov.stokes_matrix(A, B).tocsr()
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    _, its = krylov.gcr_outer(lambda v: K @ v, pc, b, 1e-8, restart=100, maxit=1000)
+    assert abs(rep["outer_its"] - its) <= 1, (rep, its)
+    assert abs(rep["inner_avg"] - np.mean(pc.inner_its)) <= 0.5, (rep, np.mean(pc.inner_its))
+
+
+def test_solve_outer_gcr_dirichlet_restarted(ctx):
+    """Outer GCR restarted after 4 directions on the all-Dirichlet
+    manufactured problem (constant pressure projected out): the sparse-direct
+    solution to 1e-10 with a zero-mean pressure."""
+    sol = exact.SmoothDirichlet()
+    nx = ny = 8
+    prob, ref = pair(ctx, nx, ny, 2, ("dirichlet",) * 4, np.ones(64), nh=0, seed=7)
+    f = sip.rhs_force(ref, sol.f)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+    rep = prob.solve(dev(f), u, p, rtol=1e-10, restart=4, max_outer=400, outer_krylov="gcr",
+                     inner_krylov="gcr")
+    assert rep["outer_its"] > 4, rep
+    res, A, B = _true_residual(ref, host(u), host(p), f)
+    assert res <= 1.5e-10, rep
+    u_ref, p_ref = krylov.solve_direct(ref, A, B, f)
+    assert rel(host(u), u_ref) < 1e-8
+    assert abs(host(p)[::4].mean()) < 1e-12
