@@ -234,14 +234,12 @@ typedef struct {
                          *    SIP_PREC_MIXED_F32_INNER                              */
     int inner_norm;     /* inner stopping test of the CG variants, relative to the  *
                          *    first value: 0 (default): the residual               *
-                         *    ||t - A y||_2, whose outer iteration counts stay      *
-                         *    flat in the viscosity contrast (six inclusions,       *
-                         *    Sec. 7.3); 1: the preconditioned residual            *
-                         *    ||V(t - A y)||_2, the default test of PETSc's CG     *
-                         *    that the paper ran for SolCx (Sec. 7.1): fewer       *
-                         *    V-cycles on a single inclusion, but the outer count  *
-                         *    grows with the contrast on the six inclusions (device *
-                         *    loop only)                                            */
+                         *    ||t - A y||_2 (Sec. 7.1), whose outer iteration      *
+                         *    counts stay flat in the viscosity contrast; 1: the   *
+                         *    preconditioned residual ||V(t - A y)||_2 (PETSc's    *
+                         *    CG default): fewer V-cycles on a single jump, but    *
+                         *    the outer count grows with the contrast on the six   *
+                         *    inclusions of Sec. 7.3 (device loop only)            */
     int inner_restart;  /* GCR restart length, 1..64 (default 30); GCR stores      *
                          *    2 x inner_restart FP64 vectors of n_u on the device  */
     int outer_krylov;   /* 0: FGMRES (default); 1: GCR, restarted after `restart`  *

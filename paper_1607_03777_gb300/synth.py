@@ -115,6 +115,20 @@ def batch_instances(count=128, seed=4, log10_contrast=(2.0, 5.0)):
     return out
 
 
+def checkerboard(n=64, k=2, eta_hi=1e6, n_hlevels=3):
+    """A 2 x 2 viscosity checkerboard on the unit square (the SolCx jump at
+    x = 1/2 plus one at y = 1/2, Sec. 7.2): eta_hi in the lower-left and
+    upper-right quadrants, 1 elsewhere, Navier on every side.  The paper's
+    SolCx forcing is only cited, so the flow is driven by a disc of density
+    1.2 (unit viscosity) at (0.3, 0.65), radius 0.1, inside the upper-left
+    quadrant; its sinking crosses both jumps."""
+    shapes = np.stack([box(0.0, 0.5, 0.0, 0.5, eta_hi, 1.0),
+                       box(0.5, 1.0, 0.5, 1.0, eta_hi, 1.0),
+                       disc(0.3, 0.65, 0.1, 1.0, 1.2)])
+    return Workload("checkerboard", n, n, k, shapes, bc=(NAVIER,) * 4, n_hlevels=n_hlevels,
+                    rtol=1e-6, meta={"eta_hi": eta_hi})
+
+
 def levels_to_17(n):
     """Number of h-coarsenings that brings an n-element side down to 16
     elements (17 vertices), the coarsest grid the paper keeps."""
