@@ -73,6 +73,11 @@ def parse():
     ap.add_argument("--checker-inner", default="pcg-true",
                     choices=["pcg-true", "pcg-preconditioned", "gcr"],
                     help="inner Krylov method and stopping test of the checkerboard sweep")
+    ap.add_argument("--sinker-refine", type=int, default=0,
+                    help="iterative refinement with a double-double residual in the "
+                         "six-sinker sweep: the most correction solves (0: off)")
+    ap.add_argument("--sinker-min-eta", type=float, default=1e3,
+                    help="smallest viscosity contrast of the six-sinker sweep")
     ap.add_argument("--sinker-max-eta", type=float, default=1e8,
                     help="largest viscosity contrast of the six-sinker sweep")
     return ap.parse_args()
@@ -607,9 +612,11 @@ def run_sinkers(args):
     inner = {"gcr": dict(inner_krylov="gcr", inner_norm="true"),
              "pcg-true": dict(inner_krylov="pcg", inner_norm="true"),
              "pcg-preconditioned": dict(inner_krylov="pcg", inner_norm="preconditioned")}
-    ikw = dict(inner[args.sinker_inner], outer_krylov=args.sinker_outer)
+    ikw = dict(inner[args.sinker_inner], outer_krylov=args.sinker_outer,
+               refine=args.sinker_refine)
     rows = []
-    for eta_in in [e for e in (1e3, 1e6, 1e8) if e <= args.sinker_max_eta]:
+    for eta_in in [e for e in (1e3, 1e6, 1e8, 1e10)
+                   if args.sinker_min_eta <= e <= args.sinker_max_eta]:
         for n in (64, 128, 256):
             for k in (1, 2, 3):
                 wl = synth.six_sinkers(n=n, k=k, eta_in=eta_in, n_hlevels=synth.levels_to_17(n))
@@ -628,12 +635,13 @@ def run_sinkers(args):
                 rows.append({"eta": eta_in, "elements": f"{n}x{n}", "k": k, "status": rep["status"],
                              "outer_its": rep["outer_its"], "inner_avg": round(rep["inner_avg"], 1),
                              "inner_max": rep["inner_max"], "rel_residual": rep["rel_residual"],
-                             "ms": round(dt * 1e3, 1)})
+                             "refine_steps": rep["refine_steps"], "ms": round(dt * 1e3, 1)})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)   # progress
                 del pr
     return {"metric": "six_sinkers_iterations", "unit": "iterations", "rows": rows,
             "config": {"workload": "six sinkers (Sec. 7.3), A_hp(Q2_1), FP64, rtol 1e-6",
                        "precision": "fp64", "outer": args.sinker_outer,
-                       "inner": args.sinker_inner}}
+                       "inner": args.sinker_inner, "refine": args.sinker_refine}}
 
 
 def run_checkerboard(args):

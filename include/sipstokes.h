@@ -245,7 +245,20 @@ typedef struct {
     int outer_krylov;   /* 0: FGMRES (default); 1: GCR, restarted after `restart`  *
                          *    directions, the outer method of the six-inclusion    *
                          *    runs (Sec. 7.3); both minimise the residual, both     *
-                         *    stop on the residual recomputed from x               */
+                         *    stop on the residual recomputed from x, and both     *
+                         *    stop early (NOT_CONVERGED) when two consecutive      *
+                         *    restarts on which the recurrence met rtol fail to    *
+                         *    halve that residual (the FP64 attainable accuracy)   */
+    int refine;         /* 0 (default): off.  n > 0: iterative refinement, at most *
+                         *    n correction solves: x and r = b - K x are carried   *
+                         *    in double-double (sip_residual_dd), each correction  *
+                         *    K d = r is an ordinary solve in the problem's        *
+                         *    precision asking for the reduction still missing.    *
+                         *    Stops when ||r|| <= rtol ||b|| (evaluated in         *
+                         *    double-double) or when a step fails to halve ||r||. *
+                         *    Reaches residuals below FP64's attainable accuracy   *
+                         *    for high viscosity contrasts, in place of the        *
+                         *    paper's quadruple precision (Sec. 7.4).             */
 } sip_solve_opts;
 
 typedef struct {
@@ -254,16 +267,18 @@ typedef struct {
     int inner_total;       /* inner PCG iterations, summed                      */
     int inner_max;
     double inner_avg;
-    double rel_residual;   /* ||b - K x||_2 / ||b||_2 recomputed in FP64        */
+    double rel_residual;   /* ||b - K x||_2 / ||b||_2 recomputed in FP64        *
+                            * (in double-double with refine > 0)               */
     double setup_ms;       /* multigrid set-up time of this call (0 if reused)  */
     double solve_ms;
     double lambda_max_p;
     int64_t kernel_launches;
+    int refine_steps;      /* correction solves of iterative refinement (0: off) */
 } sip_solve_report;
 
 /* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
  * inner_loop 0, inner_krylov 0, inner_norm 0, inner_restart 30,
- * outer_krylov 0. */
+ * outer_krylov 0, refine 0. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES (or GCR, opts->outer_krylov) with the upper
@@ -282,6 +297,18 @@ void sip_solve_opts_default(sip_solve_opts* opts);
 sip_status sip_solve(sip_problem* prob, const double* f_u, const double* g_p, double* u,
                      double* p, const sip_solve_opts* opts, sip_solve_report* report,
                      void* stream);
+
+/* r = b - K x for b = [f_u; g_p] (g_p may be NULL: 0) and x = [x_u; x_p] in
+ * double-double arithmetic (about 106 significant bits): the operator of
+ * sip_apply_A / sip_apply_B / sip_apply_Bt (eq. discretestokes, the same
+ * FP64 coefficients) evaluated exactly enough that the residual of an FP64
+ * iterate is not lost in rounding at high viscosity contrast (the precision
+ * question of Sec. 7.4).  x_u, x_p, r_u, r_p are device arrays of
+ * interleaved (hi, lo) double pairs, value = hi + lo: 2 n_u and 2 n_p
+ * doubles, caller-owned, not overlapping.  Stream-ordered. */
+sip_status sip_residual_dd(sip_problem* prob, const double* f_u, const double* g_p,
+                           const double* x_u, const double* x_p, double* r_u, double* r_p,
+                           void* stream);
 
 /* ---- batches and serving ----------------------------------------------------
  * Not in the paper (it solves one problem at a time on one CPU core): many

@@ -13,6 +13,9 @@ Test infrastructure only (see ``oracle/__init__``).
 * ``gcr_outer``     the same GCR as the outer Stokes solve with the block
   preconditioner (the paper's outer method for the six inclusions), with
   the true residual checked whenever the recurrence reports convergence.
+* ``exact_residual`` / ``refine``  b - K x in exact rational arithmetic and
+  iterative refinement of an FP64 solver with it (the precision question of
+  Sec. 7.4, answered for the residual only).
 * ``fgmres``        right-preconditioned flexible GMRES (Saad's FGMRES) on the
   saddle system with the upper block-triangular preconditioner of
   eq. discretestokespc, S replaced by the diagonal S* (Sec. 5), and
@@ -28,6 +31,8 @@ in two iterations (eigenvalue 1 with a 2x2 Jordan block for this sign,
 +-1 for the other); with the inexact inner solve this sign reproduces the
 paper's outer iteration counts and the other does not.
 """
+from fractions import Fraction
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -316,3 +321,44 @@ def gcr_outer(apply_K, precond, b, rtol, restart=100, maxit=200, null_p=None, n_
         x = x + dx
         total += its
     return x, total
+
+
+def exact_residual(K, b, x):
+    """b - K x evaluated exactly: K a scipy sparse matrix of FP64 entries, b
+    FP64, x a sequence of exact rationals (``Fraction``); every FP64 number
+    is a dyadic rational, so the result is the exact residual of the FP64
+    matrix.  Returns a list of ``Fraction``."""
+    K = K.tocsr()
+    out = []
+    for i in range(K.shape[0]):
+        acc = Fraction(float(b[i]))
+        for j in range(K.indptr[i], K.indptr[i + 1]):
+            acc -= Fraction(float(K.data[j])) * x[K.indices[j]]
+        out.append(acc)
+    return out
+
+
+def refine(K, solve, b, rtol, max_steps=10):
+    """Iterative refinement: x accumulated exactly (rationals), r = b - K x
+    exact (``exact_residual``), and each correction K d = r solved by the
+    FP64 routine ``solve(r_fp64, rtol_step)`` asked for the reduction still
+    missing, rtol_step = min(1/2, rtol ||b|| / ||r||).  Stops when
+    ||r|| <= rtol ||b|| or when a step fails to halve ||r||.
+    Returns (x as float64, list of exact relative residual norms)."""
+    n = b.size
+    x = [Fraction(0)] * n
+    nb = float(np.linalg.norm(b))
+    r = np.array(b, dtype=np.float64)
+    nr = nb
+    hist = []
+    for _ in range(max_steps):
+        d = solve(r, min(0.5, rtol * nb / nr))
+        x = [xi + Fraction(float(di)) for xi, di in zip(x, d)]
+        rx = exact_residual(K, b, x)
+        r = np.array([float(v) for v in rx])
+        nr_new = float(np.linalg.norm(r))
+        hist.append(nr_new / nb)
+        if nr_new <= rtol * nb or nr_new > 0.5 * nr:
+            break
+        nr = nr_new
+    return np.array([float(v) for v in x]), hist

@@ -54,6 +54,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_norm", ctypes.c_int),
         ("inner_restart", ctypes.c_int),
         ("outer_krylov", ctypes.c_int),
+        ("refine", ctypes.c_int),
     ]
 
 
@@ -69,6 +70,7 @@ class SolveReport(ctypes.Structure):
         ("solve_ms", ctypes.c_double),
         ("lambda_max_p", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64),
+        ("refine_steps", ctypes.c_int),
     ]
 
 
@@ -89,6 +91,7 @@ SIGNATURES = {
     "sip_apply_A_f32": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_B": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_Bt": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sip_residual_dd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sip_problem_setup": (ctypes.c_int, [_VP, _VP]),
     "sip_problem_update_eta": (ctypes.c_int, [_VP, _VP, _VP]),
     "sip_lambda_max": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),

@@ -146,6 +146,18 @@ class Problem:
         self.ctx.check(self.ctx.lib.sip_apply_Bt(self.handle, _ptr(xu, torch.float64),
                                                  _ptr(yp, torch.float64), _stream(stream)))
 
+    def residual_dd(self, f, x_u, x_p, r_u, r_p, g=None, stream=None):
+        """sip_residual_dd: r = b - K x in double-double; x_u, x_p, r_u, r_p
+        are float64 tensors of 2 n_u / 2 n_p entries, (hi, lo) pairs."""
+        for t, m in ((x_u, self.n_u), (x_p, self.n_p), (r_u, self.n_u), (r_p, self.n_p)):
+            if t.numel() != 2 * m:
+                raise ValueError("double-double vectors hold 2 doubles per entry")
+        self.ctx.check(self.ctx.lib.sip_residual_dd(
+            self.handle, _ptr(f, torch.float64),
+            _ptr(g, torch.float64) if g is not None else None, _ptr(x_u, torch.float64),
+            _ptr(x_p, torch.float64), _ptr(r_u, torch.float64), _ptr(r_p, torch.float64),
+            _stream(stream)))
+
     def rhs_body_force(self, rho, g, f, stream=None):
         self.ctx.check(self.ctx.lib.sip_rhs_body_force(self.handle, _ptr(rho, torch.float64),
                                                        float(g), _ptr(f, torch.float64),
@@ -224,7 +236,7 @@ class Problem:
     # -- Stokes solve --------------------------------------------------------
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
               max_inner=200, inner_loop="device", inner_krylov="auto",
-              inner_norm="true", inner_restart=30, outer_krylov="fgmres",
+              inner_norm="true", inner_restart=30, outer_krylov="fgmres", refine=0,
               stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
         ``check``).  ``inner_loop`` = "device" (one graph launch per inner
@@ -233,9 +245,10 @@ class Problem:
         device loop only); ``inner_norm`` = "true" (the residual, the
         default; GCR always tests it) or "preconditioned" (the V-cycle
         applied to the residual; device loop only); ``outer_krylov`` =
-        "fgmres" (default) or "gcr"."""
+        "fgmres" (default) or "gcr"; ``refine`` = the most correction solves
+        of iterative refinement with a double-double residual (0: off)."""
         o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
-                  inner_krylov, inner_norm, inner_restart, outer_krylov)
+                  inner_krylov, inner_norm, inner_restart, outer_krylov, refine)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -277,7 +290,7 @@ OUTER_KRYLOV = {"fgmres": 0, "gcr": 1}
 
 def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
           inner_loop="device", inner_krylov="auto", inner_norm="true",
-          inner_restart=30, outer_krylov="fgmres"):
+          inner_restart=30, outer_krylov="fgmres", refine=0):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
@@ -289,6 +302,7 @@ def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner
     o.inner_restart = int(inner_restart)
     o.outer_krylov = (OUTER_KRYLOV[outer_krylov] if isinstance(outer_krylov, str)
                       else int(outer_krylov))
+    o.refine = int(refine)
     return o
 
 

@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <mutex>
 
+#include "dd.cuh"
 #include "sip_face.cuh"
 #include "sip_internal.h"
 
@@ -528,6 +529,25 @@ void launch_apply_Bt(int k, const OpGeom& g, const T* u, T* y, cudaStream_t s) {
     SIP_CHECK_LAUNCH();
 }
 template void launch_apply_Bt<double>(int, const OpGeom&, const double*, double*, cudaStream_t);
+
+// Double-double instances (residual of iterative refinement): the tile
+// kernel, B and B^T evaluate the same operator with the same FP64
+// coefficients in ~106-bit arithmetic.
+void launch_apply_sip_dd(int N, const OpGeom& g, const dd* x, dd* y, const dd* eta, const dd* z,
+                         cudaStream_t s) {
+    const dd one(1.0);
+    switch (N) {
+        case 2: apply_sip_n<2, dd>(g, x, y, eta, one, z, one, s); break;
+        case 3: apply_sip_n<3, dd>(g, x, y, eta, one, z, one, s); break;
+        case 4: apply_sip_n<4, dd>(g, x, y, eta, one, z, one, s); break;
+        case 5: apply_sip_n<5, dd>(g, x, y, eta, one, z, one, s); break;
+        case 6: apply_sip_n<6, dd>(g, x, y, eta, one, z, one, s); break;
+        case 7: apply_sip_n<7, dd>(g, x, y, eta, one, z, one, s); break;
+        default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
+    }
+}
+template void launch_apply_B<dd>(int, const OpGeom&, const dd*, dd*, cudaStream_t);
+template void launch_apply_Bt<dd>(int, const OpGeom&, const dd*, dd*, cudaStream_t);
 
 void launch_rhs_body_force(int k, const OpGeom& g, const double* rho, double grav, double* f,
                            cudaStream_t s) {

@@ -482,6 +482,19 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->inner_norm = 0;
     o->inner_restart = 30;
     o->outer_krylov = 0;
+    o->refine = 0;
+}
+
+sip_status sip_residual_dd(sip_problem* p, const double* f, const double* g, const double* x_u,
+                           const double* x_p, double* r_u, double* r_p, void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    return guarded_s(p->ctx, stream, [&] {
+        sip::require(f && x_u && x_p && r_u && r_p, "null vector");
+        sip::require(r_u != x_u && r_p != x_p && r_u != x_p && r_p != x_u,
+                     "r and x must not overlap");
+        SIP_CUDA(cudaSetDevice(p->ctx->device));
+        sip::residual_dd(p, f, g, x_u, x_p, r_u, r_p, as_stream(stream));
+    });
 }
 
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
@@ -505,8 +518,10 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
                                              p->desc.precision != SIP_PREC_MIXED_F32_INNER),
                      "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
         sip::require(o.outer_krylov == 0 || o.outer_krylov == 1, "outer_krylov is 0 or 1");
+        sip::require(o.refine >= 0 && o.refine <= 100, "refine is 0..100");
         SIP_CUDA(cudaSetDevice(p->ctx->device));
-        st = sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
+        st = o.refine > 0 ? sip::run_solve_refined(p, f, g, u, pp, o, rep, as_stream(stream))
+                          : sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
         if (st != SIP_OK) {
             throw Error(st, st == SIP_ERR_NOT_CONVERGED ? "FGMRES did not reach the tolerance"
                                                         : "Krylov breakdown");

@@ -182,6 +182,10 @@ bool launch_cheb_elem(int N, const OpGeom& g, const T* x, const T* z, T* r, cons
                       const int* emap, const T* cls_inv, const int* cls_sym, const T* uniq_inv,
                       const T* eta_inv, const T* d_old, T* d_new, T* yv, T c1, T c2, bool pend,
                       cudaStream_t s);
+struct dd;
+// y = A x + z in double-double (the tile kernel with T = dd)
+void launch_apply_sip_dd(int N, const OpGeom& g, const dd* x, dd* y, const dd* eta, const dd* z,
+                         cudaStream_t s);
 template <typename T>
 void launch_apply_B(int k, const OpGeom& g, const T* p, T* y, cudaStream_t s);
 template <typename T>

@@ -199,6 +199,18 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                      double* p, const sip_solve_opts& o, sip_solve_report* rep,
                      cudaStream_t s);
 
+// r = b - K x with b = [f; g] (g may be null: 0) and x, r in double-double
+// (interleaved hi, lo pairs): velocity and pressure parts separately.
+void residual_dd(sip_problem* P, const double* f_u, const double* g_p, const double* x_u,
+                 const double* x_p, double* r_u, double* r_p, cudaStream_t s);
+
+// Iterative refinement (o.refine > 0): FP64 / mixed solves of K d = r for
+// the residual r = b - K x evaluated in double-double, x accumulated in
+// double-double, until the residual meets o.rtol or stops halving.
+sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_p, double* u,
+                             double* p, const sip_solve_opts& o, sip_solve_report* rep,
+                             cudaStream_t s);
+
 }  // namespace sip
 
 struct sip_problem {
@@ -215,6 +227,9 @@ struct sip_problem {
     std::unique_ptr<sip::Multigrid<double>> mg64;
     std::unique_ptr<sip::Multigrid<float>> mg32;
     std::unique_ptr<sip::Workspace> ws;
+    // iterative refinement: eta, x, K x, B x_p in double-double; residual and
+    // correction in FP64
+    sip::DeviceBuffer eta_dd, rf_x, rf_y, rf_t, rf_r, rf_d;
     double setup_ms = 0.0;
     int64_t device_bytes() const;
     void ensure_setup(cudaStream_t s);

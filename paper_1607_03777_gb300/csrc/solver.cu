@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "dd.cuh"
 #include "sip_solver.h"
 
 namespace sip {
@@ -1046,6 +1047,14 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         throw Error(SIP_ERR_INVALID_ARG, "non-finite right-hand side");
     }
     std::vector<double> H(size_t(restart + 1) * restart), cs(restart), sn(restart), gv(restart + 1);
+    bool recur_conv = false;   // the last cycle ended on the recurrence's residual
+    double rn_false = 0.0;     // residual after the previous such cycle
+    auto stagnated = [&](double rn) {
+        if (!recur_conv) return false;
+        if (rn_false > 0.0 && rn > 0.5 * rn_false) return true;
+        rn_false = rn;
+        return false;
+    };
     if (o.outer_krylov == 1 && st == SIP_ERR_NOT_CONVERGED) {
         // GCR (Eisenstat, Elman & Schultz 1983), the outer method of the
         // six-inclusion runs (Sec. 7.3): z_j = P^{-1} r, q_j = K z_j, both
@@ -1079,8 +1088,9 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                 st = SIP_ERR_BREAKDOWN;
                 break;
             }
-            if (total >= o.max_outer) break;
+            if (total >= o.max_outer || stagnated(rn)) break;
             int j = 0;
+            recur_conv = false;
             while (total < o.max_outer) {
                 if (j == restart) j = 0;
                 double* zj = Z + size_t(j) * n;
@@ -1107,7 +1117,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                     broke = true;
                     break;
                 }
-                if (rr <= o.rtol * beta0) break;
+                if (rr <= o.rtol * beta0) {
+                    recur_conv = true;
+                    break;
+                }
             }
         }
     }
@@ -1123,6 +1136,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         gv[0] = beta;
         int j = 0, jdone = 0;
         bool broke = false;
+        recur_conv = false;
         for (j = 0; j < restart && total < o.max_outer; ++j) {
             double* vj = V + size_t(j) * n;
             double* zj = Z + size_t(j) * n;
@@ -1163,6 +1177,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
             ++total;
             jdone = j + 1;
             if (std::abs(gv[j + 1]) <= o.rtol * beta0 || hn <= 1e-300) {
+                recur_conv = true;
                 break;
             }
         }
@@ -1195,7 +1210,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
             st = SIP_ERR_BREAKDOWN;
             break;
         }
-        // the recurrence may report convergence while the true residual does not: restart
+        // the recurrence may report convergence while the true residual does
+        // not: restart; a second such cycle that does not halve the residual
+        // means FP64 has reached its attainable accuracy for this system
+        if (stagnated(rn)) break;
     }
     if (singular) launch_zero_mean_pressure(size_t(P->ne), P->mp, x + n_u, wsd, s);
     SIP_CUDA(cudaMemcpyAsync(u_out, x, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1212,6 +1230,172 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         rep->solve_ms = now_ms() - t_start - setup_ms;
         rep->lambda_max_p = mixed ? P->mg32->lmax_p : P->mg64->lmax_p;
         rep->kernel_launches = launch_counter() - launches0;
+        rep->refine_steps = 0;
+    }
+    return st;
+}
+
+namespace {
+
+__global__ void k_to_dd(size_t n, const double* __restrict__ a, dd* b) {
+    grid_dep_wait();
+    const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = dd(a[g]);
+}
+
+// r = [f; g] - y over n entries (the first n_u from f, the rest from g or 0)
+__global__ void k_dd_b_minus(size_t n_u, size_t n, const double* __restrict__ f,
+                             const double* __restrict__ gp, const dd* __restrict__ y, dd* r) {
+    grid_dep_wait();
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double b = i < n_u ? f[i] : (gp ? gp[i - n_u] : 0.0);
+    r[i] = dd(b) - y[i];
+}
+
+// x += d (double-double accumulation of an FP64 correction)
+__global__ void k_dd_add(size_t n, const double* __restrict__ d, dd* x) {
+    grid_dep_wait();
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + dd(d[i]);
+}
+
+// v = hi + lo rounded to FP64 (the leading part of a normalised pair)
+__global__ void k_dd_round(size_t n, const dd* __restrict__ x, double* v) {
+    grid_dep_wait();
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = x[i].hi + x[i].lo;
+}
+
+inline unsigned blocks_of(size_t n) { return unsigned((n + 255) / 256); }
+
+// r = b - K x with x, r contiguous [u; p] double-double vectors
+void residual_dd_contig(sip_problem* P, const double* f_u, const double* g_p, const dd* x, dd* r,
+                        cudaStream_t s) {
+    const size_t n_u = size_t(P->n_u), n_p = size_t(P->n_p), n = n_u + n_p;
+    const size_t ne = size_t(P->ne);
+    P->eta_dd.alloc(ne * sizeof(dd));
+    P->rf_y.alloc(n * sizeof(dd));
+    P->rf_t.alloc(n_u * sizeof(dd));
+    dd* eta = P->eta_dd.as<dd>();
+    dd* y = P->rf_y.as<dd>();
+    dd* t = P->rf_t.as<dd>();
+    launch_k(k_to_dd, blocks_of(ne), 256, 0, s, ne, P->eta_d.as<double>(), eta);
+    SIP_CHECK_LAUNCH();
+    launch_apply_B<dd>(P->k, P->geom, x + n_u, t, s);                       // t = B x_p
+    launch_apply_sip_dd(P->n, P->geom, x, y, eta, t, s);                    // y_u = A x_u + t
+    launch_apply_Bt<dd>(P->k, P->geom, x, y + n_u, s);                      // y_p = B^T x_u
+    launch_k(k_dd_b_minus, blocks_of(n), 256, 0, s, n_u, n, f_u, g_p, static_cast<const dd*>(y),
+             r);
+    SIP_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void residual_dd(sip_problem* P, const double* f_u, const double* g_p, const double* x_u,
+                 const double* x_p, double* r_u, double* r_p, cudaStream_t s) {
+    const size_t n_u = size_t(P->n_u), n_p = size_t(P->n_p), n = n_u + n_p;
+    P->rf_x.alloc(n * sizeof(dd));
+    P->rf_r.alloc(n * sizeof(dd));
+    dd* x = P->rf_x.as<dd>();
+    dd* r = P->rf_r.as<dd>();
+    SIP_CUDA(cudaMemcpyAsync(x, x_u, n_u * sizeof(dd), cudaMemcpyDeviceToDevice, s));
+    SIP_CUDA(cudaMemcpyAsync(x + n_u, x_p, n_p * sizeof(dd), cudaMemcpyDeviceToDevice, s));
+    residual_dd_contig(P, f_u, g_p, x, r, s);
+    SIP_CUDA(cudaMemcpyAsync(r_u, r, n_u * sizeof(dd), cudaMemcpyDeviceToDevice, s));
+    SIP_CUDA(cudaMemcpyAsync(r_p, r + n_u, n_p * sizeof(dd), cudaMemcpyDeviceToDevice, s));
+}
+
+sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_p, double* u_out,
+                             double* p_out, const sip_solve_opts& o, sip_solve_report* rep,
+                             cudaStream_t s) {
+    const double t_start = now_ms();
+    const int64_t launches0 = launch_counter();
+    const size_t n_u = size_t(P->n_u), n_p = size_t(P->n_p), n = n_u + n_p;
+    P->rf_x.alloc(n * sizeof(dd));
+    P->rf_r.alloc(n * sizeof(dd));
+    P->rf_d.alloc(2 * n * sizeof(double));   // FP64 residual [n] and correction [n]
+    dd* x = P->rf_x.as<dd>();
+    dd* r = P->rf_r.as<dd>();
+    double* r64 = P->rf_d.as<double>();
+    double* d64 = r64 + n;
+    SIP_CUDA(cudaMemsetAsync(x, 0, n * sizeof(dd), s));
+    SIP_CUDA(cudaMemcpyAsync(r64, f_u, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (g_p)
+        SIP_CUDA(cudaMemcpyAsync(r64 + n_u, g_p, n_p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else
+        SIP_CUDA(cudaMemsetAsync(r64 + n_u, 0, n_p * sizeof(double), s));
+    // norms through a small device scratch (the reduction kernels of the solve)
+    DeviceBuffer scr, part;
+    scr.alloc(8 * sizeof(double));
+    part.alloc(reduction_workspace_doubles(2) * sizeof(double));
+    HostScalars hs;
+    auto norm = [&](const double* v) {
+        launch_dot<double>(n, v, v, scr.as<double>(), part.as<double>(), s);
+        return std::sqrt(read_scalar(scr.as<double>(), hs.p, s));
+    };
+    const double nb = norm(r64);
+    sip_solve_opts o1 = o;
+    o1.refine = 0;
+    sip_status st = SIP_ERR_NOT_CONVERGED;
+    int outer = 0, inner_total = 0, inner_max = 0, steps = 0;
+    double inner_calls = 0.0, setup_ms = 0.0, rel = nb == 0.0 ? 0.0 : 1.0, nr = nb;
+    if (nb == 0.0) st = SIP_OK;
+    if (!std::isfinite(nb)) throw Error(SIP_ERR_INVALID_ARG, "non-finite right-hand side");
+    while (st == SIP_ERR_NOT_CONVERGED && steps < o.refine && outer < o.max_outer) {
+        // the correction solve asks for what is left of the reduction
+        o1.rtol = std::min(0.5, o.rtol * nb / nr);
+        o1.max_outer = o.max_outer - outer;
+        sip_solve_report r1{};
+        const sip_status s1 = run_solve(P, r64, r64 + n_u, d64, d64 + n_u, o1, &r1, s);
+        ++steps;
+        outer += r1.outer_its;
+        inner_total += r1.inner_total;
+        inner_max = std::max(inner_max, r1.inner_max);
+        if (r1.inner_avg > 0.0) inner_calls += double(r1.inner_total) / r1.inner_avg;
+        setup_ms += r1.setup_ms;
+        if (s1 == SIP_ERR_BREAKDOWN && !std::isfinite(norm(d64))) {
+            st = SIP_ERR_BREAKDOWN;
+            break;
+        }
+        launch_k(k_dd_add, blocks_of(n), 256, 0, s, n, static_cast<const double*>(d64), x);
+        SIP_CHECK_LAUNCH();
+        residual_dd_contig(P, f_u, g_p, x, r, s);
+        launch_k(k_dd_round, blocks_of(n), 256, 0, s, n, static_cast<const dd*>(r), r64);
+        SIP_CHECK_LAUNCH();
+        const double nr_new = norm(r64);
+        if (!std::isfinite(nr_new)) {
+            st = SIP_ERR_BREAKDOWN;
+            break;
+        }
+        rel = nr_new / nb;
+        if (nr_new <= o.rtol * nb) {
+            st = SIP_OK;
+            break;
+        }
+        if (nr_new > 0.5 * nr) break;   // the correction no longer halves the residual
+        nr = nr_new;
+    }
+    launch_k(k_dd_round, blocks_of(n), 256, 0, s, n, static_cast<const dd*>(x), d64);
+    SIP_CHECK_LAUNCH();
+    const bool singular = P->desc.bc[0] != SIP_BC_NEUMANN && P->desc.bc[1] != SIP_BC_NEUMANN &&
+                          P->desc.bc[2] != SIP_BC_NEUMANN && P->desc.bc[3] != SIP_BC_NEUMANN;
+    if (singular) launch_zero_mean_pressure(size_t(P->ne), P->mp, d64 + n_u, part.as<double>(), s);
+    SIP_CUDA(cudaMemcpyAsync(u_out, d64, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SIP_CUDA(cudaMemcpyAsync(p_out, d64 + n_u, n_p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SIP_CUDA(cudaStreamSynchronize(s));
+    if (rep) {
+        rep->status = st;
+        rep->outer_its = outer;
+        rep->inner_total = inner_total;
+        rep->inner_max = inner_max;
+        rep->inner_avg = inner_calls > 0.0 ? double(inner_total) / inner_calls : 0.0;
+        rep->rel_residual = rel;
+        rep->setup_ms = setup_ms;
+        rep->solve_ms = now_ms() - t_start - setup_ms;
+        rep->lambda_max_p = P->mg32 ? P->mg32->lmax_p : (P->mg64 ? P->mg64->lmax_p : 0.0);
+        rep->kernel_launches = launch_counter() - launches0;
+        rep->refine_steps = steps;
     }
     return st;
 }
@@ -1223,6 +1407,7 @@ int64_t sip_problem::device_bytes() const {
     if (mg64) b += mg64->bytes();
     if (mg32) b += mg32->bytes();
     if (ws) b += ws->bytes();
+    b += int64_t(eta_dd.bytes + rf_x.bytes + rf_y.bytes + rf_t.bytes + rf_r.bytes + rf_d.bytes);
     return b;
 }
 

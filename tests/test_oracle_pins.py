@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import basis, exact, krylov, materials, multigrid, rng, sip
+from paper_1607_03777_gb300 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 BCS = [("navier",) * 4, ("dirichlet",) * 4, ("navier", "navier", "navier", "neumann"),
@@ -764,3 +765,48 @@ def test_gcr_outer_hpmg_singular_pressure_solves_to_direct_solution():
     assert np.linalg.norm(b - K @ x) <= 1e-10 * np.linalg.norm(b)
     assert np.linalg.norm(x[:n_u] - u) <= 1e-8 * np.linalg.norm(u)
     assert abs(null @ x[n_u:]) <= 1e-10 * np.linalg.norm(x[n_u:]) * np.linalg.norm(null)
+
+
+def test_exact_residual_matches_fp64_residual():
+    """The exact rational residual agrees with the FP64 one to FP64 rounding
+    (plumbing check against an independent evaluation)."""
+    pr = _prob(3, 3, 2, ("navier", "navier", "navier", "neumann"), seed=5)
+    A, B = sip.assemble_A(pr), sip.assemble_B(pr)
+    K = krylov.stokes_matrix(A, B).tocsr()
+    g = np.random.default_rng(41)
+    b, x = g.standard_normal(K.shape[0]), g.standard_normal(K.shape[0])
+    from fractions import Fraction
+    r = np.array([float(v) for v in krylov.exact_residual(K, b, [Fraction(float(v)) for v in x])])
+    assert np.linalg.norm(r - (b - K @ x)) <= 1e-13 * np.linalg.norm(b - K @ x)
+
+
+def test_refine_reaches_below_fp64_floor():
+    """Six inclusions, contrast 1e8, 16^2, k = 2: the FP64 FGMRES stalls with
+    an exact residual near 3e-8 (no FP64 vector does much better: the
+    rounding of the refined iterate sits at the same floor), while
+    refinement with the exact residual takes the iterate below 1e-11 in one
+    cheap correction (Sec. 7.4's precision question, for the residual)."""
+    from fractions import Fraction
+    n, k = 16, 2
+    wl = synth.six_sinkers(n=n, k=k, eta_in=1e8, n_hlevels=1)
+    eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
+    pr = sip.Problem(n, n, k, eta, bc=wl.bc)
+    A, B = sip.assemble_A(pr).tocsr(), sip.assemble_B(pr).tocsr()
+    mg = multigrid.HPMultigrid(pr, A, 1, seed=1)
+    f = sip.rhs_body_force(pr, rho, 10.0)
+    K = krylov.stokes_matrix(A, B).tocsr()
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+
+    def solve(r, rt):
+        pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3)
+        return krylov.fgmres(lambda v: K @ v, pc, r, rt, restart=100, maxit=60)[0]
+
+    x64 = solve(b, 1e-12)
+    nb = np.linalg.norm(b)
+    exact_rel = lambda x: np.linalg.norm(
+        [float(v) for v in krylov.exact_residual(K, b, [Fraction(float(t)) for t in x])]) / nb
+    plain = exact_rel(x64)
+    assert plain > 1e-9
+    x_ir, hist = krylov.refine(K, solve, b, 1e-11, max_steps=4)
+    assert hist[-1] <= 1e-11 and len(hist) <= 3, hist
+    assert exact_rel(x_ir) > 100 * hist[-1]   # the FP64 rounding is back at the floor
