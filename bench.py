@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--checker-inner", default="pcg-true",
                     choices=["pcg-true", "pcg-preconditioned", "gcr"],
                     help="inner Krylov method and stopping test of the checkerboard sweep")
+    ap.add_argument("--refine", type=int, default=4,
+                    help="batch / serve: iterative refinement with a double-double residual, "
+                         "the most correction solves (0: off), in both arms")
     ap.add_argument("--sinker-refine", type=int, default=0,
                     help="iterative refinement with a double-double residual in the "
                          "six-sinker sweep: the most correction solves (0: off)")
@@ -450,9 +453,10 @@ def _instance(ctx, wl, precision, seed):
 def run_batch(args):
     """Batched form: the first ``--count`` instances of the seeded list
     (side in {32, 64, 128, 256}, k in {2..5}, the six inclusions of Sec. 7.3
-    jittered, contrast 10^U[2,5]), mixed precision (FP32 V-cycle, FP64
+    jittered, contrast 10^U[2,6]), mixed precision (FP32 V-cycle, FP64
     Krylov), solved concurrently on 8 streams; against the plain FP64 form
-    solved one at a time.  Set-up is inside both timed regions."""
+    solved one at a time.  Both arms refine with a double-double residual
+    (``--refine``).  Set-up is inside both timed regions."""
     import torch
     from paper_1607_03777_gb300 import api, synth
     ctx = api.Context(0)
@@ -464,14 +468,14 @@ def run_batch(args):
         pr.setup()
     st, reps = api.solve_batch(ctx, [m[0] for m in mixed], [m[1] for m in mixed],
                                [m[2] for m in mixed], [m[3] for m in mixed], n_streams=8,
-                               rtol=1e-8)
+                               rtol=1e-8, refine=args.refine)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     t1 = time.perf_counter()
     plain = []
     for wl in insts:
         pr, f, u, p = _instance(ctx, wl, "fp64", 4)
-        rep = pr.solve(f, u, p, rtol=1e-8, check=False)
+        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.refine, check=False)
         plain.append((rep, u))
         del pr
     torch.cuda.synchronize()
@@ -484,17 +488,19 @@ def run_batch(args):
             "max_rel_residual": max(r["rel_residual"] for r in reps),
             "u_rel_diff_vs_fp64": {"max": max(err), "median": float(sorted(err)[len(err) // 2])},
             "config": {"workload": "batch_instances(seed 4): sides 32-256, k 2-5, "
-                                   "jittered six inclusions, contrast 1e2-1e5",
-                       "count": len(insts), "precision": "mixed", "streams": 8, "rtol": 1e-8}}
+                                   "jittered six inclusions, contrast 1e2-1e6",
+                       "count": len(insts), "precision": "mixed", "streams": 8, "rtol": 1e-8,
+                       "refine": args.refine}}
 
 
 def run_serve(args):
     """Served form: the first ``--count`` requests of the seeded Poisson
     stream (200 requests/s, side log-uniform in [32, 512], k in {2..6}, the
-    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,5]) replayed in real
+    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,6]) replayed in real
     time into the server (mixed precision, 8 slots, HBM admission budget =
     free HBM - 10%); latency = submit to result on the host.  Against the
-    same requests solved one at a time in plain FP64."""
+    same requests solved one at a time in plain FP64.  Both arms refine with
+    a double-double residual (``--refine``)."""
     import numpy as np
     import torch
     from paper_1607_03777_gb300 import api, synth
@@ -515,7 +521,8 @@ def run_serve(args):
             time.sleep(wait)
         eta, rho = eta_rho[i]
         keep.append(srv.submit(i, wl.nx, wl.ny, wl.k, eta, rho, g=synth.GRAVITY, bc=wl.bc,
-                               n_hlevels=wl.n_hlevels, seed=5, precision="mixed"))
+                               n_hlevels=wl.n_hlevels, seed=5, precision="mixed",
+                               opts={"rtol": 1e-8, "refine": args.refine}))
     srv.drain()
     dt = time.perf_counter() - t0
     done = srv.poll(cap=max(256, len(wls)))
@@ -528,7 +535,7 @@ def run_serve(args):
     for wl in wls:
         ts = time.perf_counter()
         pr, f, u, p = _instance(ctx, wl, "fp64", 5)
-        rep = pr.solve(f, u, p, rtol=1e-8, check=False)
+        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.refine, check=False)
         torch.cuda.synchronize()
         base_lat.append((time.perf_counter() - ts) * 1e3)
         base_ok += rep["status"] == 0
@@ -548,8 +555,9 @@ def run_serve(args):
                                    "solve_ms_p99": float(np.percentile(base_lat, 99)),
                                    "converged": int(base_ok)},
             "config": {"workload": "request_stream(seed 5): 200 req/s, sides 32-512, k 2-6, "
-                                   "jittered six inclusions, contrast 1-1e5",
-                       "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8}}
+                                   "jittered six inclusions, contrast 1-1e6",
+                       "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8,
+                       "refine": args.refine}}
 
 
 def run_coarse(args):

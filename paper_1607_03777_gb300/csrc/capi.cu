@@ -40,6 +40,26 @@ sip_status guarded_s(sip_ctx* ctx, void* stream, F&& f) {
 }  // namespace
 
 
+namespace sip {
+
+void require_valid_opts(const sip_solve_opts& o, int precision) {
+    require(std::isfinite(o.rtol) && o.rtol > 0 && o.max_outer >= 1 && o.restart >= 1 &&
+                o.restart <= 250 && std::isfinite(o.inner_rtol) && o.inner_rtol > 0 &&
+                o.max_inner >= 1 && (o.inner_loop == 0 || o.inner_loop == 1) &&
+                o.inner_krylov >= 0 && o.inner_krylov <= 3 &&
+                !(o.inner_loop == 1 && o.inner_krylov >= 2) &&
+                (o.inner_norm == 0 || o.inner_norm == 1) &&
+                !(o.inner_loop == 1 && o.inner_norm == 1),
+            "bad solve options");
+    require(o.inner_krylov != 3 || (o.inner_restart >= 1 && o.inner_restart <= 64 &&
+                                    precision != SIP_PREC_MIXED_F32_INNER),
+            "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
+    require(o.outer_krylov == 0 || o.outer_krylov == 1, "outer_krylov is 0 or 1");
+    require(o.refine >= 0 && o.refine <= 100, "refine is 0..100");
+}
+
+}  // namespace sip
+
 extern "C" {
 
 void sip_problem_desc_default(sip_problem_desc* d) {
@@ -506,22 +526,9 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
         sip_solve_opts o;
         sip_solve_opts_default(&o);
         if (opts) o = *opts;
-        sip::require(std::isfinite(o.rtol) && o.rtol > 0 && o.max_outer >= 1 && o.restart >= 1 &&
-                         o.restart <= 250 &&
-                         std::isfinite(o.inner_rtol) && o.inner_rtol > 0 && o.max_inner >= 1 &&
-                         (o.inner_loop == 0 || o.inner_loop == 1) && o.inner_krylov >= 0 &&
-                         o.inner_krylov <= 3 && !(o.inner_loop == 1 && o.inner_krylov >= 2) &&
-                         (o.inner_norm == 0 || o.inner_norm == 1) &&
-                         !(o.inner_loop == 1 && o.inner_norm == 1),
-                     "bad solve options");
-        sip::require(o.inner_krylov != 3 || (o.inner_restart >= 1 && o.inner_restart <= 64 &&
-                                             p->desc.precision != SIP_PREC_MIXED_F32_INNER),
-                     "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
-        sip::require(o.outer_krylov == 0 || o.outer_krylov == 1, "outer_krylov is 0 or 1");
-        sip::require(o.refine >= 0 && o.refine <= 100, "refine is 0..100");
+        sip::require_valid_opts(o, p->desc.precision);
         SIP_CUDA(cudaSetDevice(p->ctx->device));
-        st = o.refine > 0 ? sip::run_solve_refined(p, f, g, u, pp, o, rep, as_stream(stream))
-                          : sip::run_solve(p, f, g, u, pp, o, rep, as_stream(stream));
+        st = sip::solve_dispatch(p, f, g, u, pp, o, rep, as_stream(stream));
         if (st != SIP_OK) {
             throw Error(st, st == SIP_ERR_NOT_CONVERGED ? "FGMRES did not reach the tolerance"
                                                         : "Krylov breakdown");

@@ -55,6 +55,15 @@ int64_t estimate_problem_bytes(const sip_problem_desc& d, int restart) {
     return b;
 }
 
+int64_t estimate_problem_bytes(const sip_problem_desc& d, const sip_solve_opts& o) {
+    int64_t b = estimate_problem_bytes(d, std::max(1, std::min(o.restart, o.max_outer)));
+    const int64_t ne = int64_t(d.nx) * d.ny;
+    const int64_t n = d.k + 1, n_u = ne * 2 * n * n, nk = n_u + ne * int64_t(d.k) * d.k;
+    if (o.inner_krylov == 3) b += 2 * int64_t(o.inner_restart) * n_u * 8;   // GCR directions
+    if (o.refine > 0) b += ne * 16 + 3 * nk * 16 + n_u * 16 + 2 * nk * 8;  // refinement
+    return b;
+}
+
 }  // namespace sip
 
 // ------------------------------------------------------------------ batch
@@ -108,7 +117,7 @@ void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n
             Job& j = jobs[i];
             try {
                 sip_solve_report local{};
-                j.st = sip::run_solve(j.prob, j.f, nullptr, j.u, j.p, o, j.rep ? j.rep : &local, s);
+                j.st = sip::solve_dispatch(j.prob, j.f, nullptr, j.u, j.p, o, j.rep ? j.rep : &local, s);
             } catch (const Error& e) {
                 j.st = e.status;
                 j.err = e.what();
@@ -180,7 +189,7 @@ sip_status sip_server::solve_one(ServerRequest& r, cudaStream_t s, sip_solve_rep
         SIP_CUDA(cudaMallocAsync(&rho, ne * sizeof(double), s));
         SIP_CUDA(cudaMemcpyAsync(rho, r.rho.data(), ne * sizeof(double), cudaMemcpyHostToDevice, s));
         sip::launch_rhs_body_force(prob->k, prob->geom, rho, r.g, f, s);
-        st = sip::run_solve(prob, f, nullptr, u, p, r.opts, &rep, s);
+        st = sip::solve_dispatch(prob, f, nullptr, u, p, r.opts, &rep, s);
         SIP_CUDA(cudaMemcpyAsync(r.u_host, u, n_u * sizeof(double), cudaMemcpyDeviceToHost, s));
         SIP_CUDA(cudaMemcpyAsync(r.p_host, p, n_p * sizeof(double), cudaMemcpyDeviceToHost, s));
         SIP_CUDA(cudaStreamSynchronize(s));
@@ -258,6 +267,12 @@ sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* probs, const
             ctx->err = "bad batch entry " + std::to_string(i);
             return SIP_ERR_INVALID_ARG;
         }
+        try {
+            sip::require_valid_opts(o, probs[i]->desc.precision);
+        } catch (const sip::Error& e) {
+            ctx->err = e.what();
+            return SIP_ERR_INVALID_ARG;
+        }
         jobs[i] = Job{probs[i], f_u[i], u[i], p[i], reports ? &reports[i] : nullptr};
     }
     run_jobs(ctx->device, jobs, o, n_streams < 1 ? 8 : n_streams);
@@ -318,7 +333,12 @@ sip_status sip_server_submit(sip_server* sv, const sip_problem_desc* desc, const
     r.p_host = p_host;
     sip_solve_opts_default(&r.opts);
     if (opts) r.opts = *opts;
-    r.bytes = sip::estimate_problem_bytes(r.desc, std::min(r.opts.restart, r.opts.max_outer));
+    try {
+        sip::require_valid_opts(r.opts, r.desc.precision);
+    } catch (const sip::Error&) {
+        return SIP_ERR_INVALID_ARG;
+    }
+    r.bytes = sip::estimate_problem_bytes(r.desc, r.opts);
     r.t_submit = wall_ms();
     {
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -211,6 +211,20 @@ sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_
                              double* p, const sip_solve_opts& o, sip_solve_report* rep,
                              cudaStream_t s);
 
+// Throws Error(SIP_ERR_INVALID_ARG) unless the options are valid for a
+// problem of this precision (every solve entry point checks them).
+void require_valid_opts(const sip_solve_opts& o, int precision);
+// Device bytes of one problem solved with these options (admission).
+int64_t estimate_problem_bytes(const sip_problem_desc& d, const sip_solve_opts& o);
+
+// run_solve_refined when o.refine > 0, else run_solve (every entry point)
+inline sip_status solve_dispatch(sip_problem* P, const double* f_u, const double* g_p, double* u,
+                                 double* p, const sip_solve_opts& o, sip_solve_report* rep,
+                                 cudaStream_t s) {
+    return o.refine > 0 ? run_solve_refined(P, f_u, g_p, u, p, o, rep, s)
+                        : run_solve(P, f_u, g_p, u, p, o, rep, s);
+}
+
 }  // namespace sip
 
 struct sip_problem {

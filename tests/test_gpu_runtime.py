@@ -148,3 +148,30 @@ def test_batch_allocates_then_problems_destroyed(ctx):
     for pr in probs:
         pr.close()
     torch.cuda.synchronize()
+
+
+def test_batch_with_refinement_matches_alone(ctx):
+    """Iterative refinement through the batched path: each instance, solved
+    with refine = 4 to 1e-10 alongside the others, equals the same refined
+    solve run alone, bit for bit, and reports its correction solves; invalid
+    options are refused before any work."""
+    inst = _instances(4, 3)
+    alone = []
+    for n, k, shapes, precision in inst:
+        prob, f, _, _, _, _, _ = _alone(ctx, n, k, shapes, precision)
+        u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+        rep = prob.solve(f, u, p, rtol=1e-10, refine=4)
+        assert rep["refine_steps"] >= 1 and rep["rel_residual"] <= 1e-10, rep
+        alone.append((prob, f, u, p))
+    us = [torch.empty_like(a[2]) for a in alone]
+    ps = [torch.empty_like(a[3]) for a in alone]
+    st, reps = api.solve_batch(ctx, [a[0] for a in alone], [a[1] for a in alone], us, ps,
+                               n_streams=2, rtol=1e-10, refine=4)
+    assert st == _lib.SIP_OK
+    for a, u, p, r in zip(alone, us, ps, reps):
+        assert r["status"] == 0 and r["refine_steps"] >= 1
+        assert torch.equal(u, a[2]) and torch.equal(p, a[3])
+    st, _ = api.solve_batch(ctx, [a[0] for a in alone], [a[1] for a in alone], us, ps,
+                            refine=101)
+    assert _lib.STATUS_NAMES[st] == "SIP_ERR_INVALID_ARG"
