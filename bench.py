@@ -74,8 +74,12 @@ def parse():
                     choices=["pcg-true", "pcg-preconditioned", "gcr"],
                     help="inner Krylov method and stopping test of the checkerboard sweep")
     ap.add_argument("--refine", type=int, default=4,
-                    help="batch / serve: iterative refinement with a double-double residual, "
-                         "the most correction solves (0: off), in both arms")
+                    help="batch: iterative refinement with a double-double residual, the "
+                         "most correction solves (0: off), in both arms")
+    ap.add_argument("--serve-refine", type=int, default=0,
+                    help="serve: the same for the served requests and their FP64 arm")
+    ap.add_argument("--serve-max-log-contrast", type=float, default=5.0,
+                    help="serve: contrasts 10^U[0, this]")
     ap.add_argument("--sinker-refine", type=int, default=0,
                     help="iterative refinement with a double-double residual in the "
                          "six-sinker sweep: the most correction solves (0: off)")
@@ -496,16 +500,16 @@ def run_batch(args):
 def run_serve(args):
     """Served form: the first ``--count`` requests of the seeded Poisson
     stream (200 requests/s, side log-uniform in [32, 512], k in {2..6}, the
-    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,6]) replayed in real
+    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,5] by default) replayed in real
     time into the server (mixed precision, 8 slots, HBM admission budget =
     free HBM - 10%); latency = submit to result on the host.  Against the
-    same requests solved one at a time in plain FP64.  Both arms refine with
-    a double-double residual (``--refine``)."""
+    same requests solved one at a time in plain FP64.  ``--serve-refine``
+    turns on refinement with a double-double residual in both arms."""
     import numpy as np
     import torch
     from paper_1607_03777_gb300 import api, synth
     ctx = api.Context(0)
-    arrivals, wls = synth.request_stream()
+    arrivals, wls = synth.request_stream(log10_contrast=(0.0, args.serve_max_log_contrast))
     arrivals, wls = arrivals[:args.count], wls[:args.count]
     free, _ = torch.cuda.mem_get_info()
     srv = api.Server(ctx, budget_bytes=int(free * 0.9), max_slots=8)
@@ -522,7 +526,7 @@ def run_serve(args):
         eta, rho = eta_rho[i]
         keep.append(srv.submit(i, wl.nx, wl.ny, wl.k, eta, rho, g=synth.GRAVITY, bc=wl.bc,
                                n_hlevels=wl.n_hlevels, seed=5, precision="mixed",
-                               opts={"rtol": 1e-8, "refine": args.refine}))
+                               opts={"rtol": 1e-8, "refine": args.serve_refine}))
     srv.drain()
     dt = time.perf_counter() - t0
     done = srv.poll(cap=max(256, len(wls)))
@@ -535,7 +539,7 @@ def run_serve(args):
     for wl in wls:
         ts = time.perf_counter()
         pr, f, u, p = _instance(ctx, wl, "fp64", 5)
-        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.refine, check=False)
+        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.serve_refine, check=False)
         torch.cuda.synchronize()
         base_lat.append((time.perf_counter() - ts) * 1e3)
         base_ok += rep["status"] == 0
@@ -555,9 +559,10 @@ def run_serve(args):
                                    "solve_ms_p99": float(np.percentile(base_lat, 99)),
                                    "converged": int(base_ok)},
             "config": {"workload": "request_stream(seed 5): 200 req/s, sides 32-512, k 2-6, "
-                                   "jittered six inclusions, contrast 1-1e6",
+                                   "jittered six inclusions, contrast "
+                                   f"1-1e{args.serve_max_log_contrast:g}",
                        "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8,
-                       "refine": args.refine}}
+                       "refine": args.serve_refine}}
 
 
 def run_coarse(args):
