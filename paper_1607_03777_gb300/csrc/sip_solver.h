@@ -242,8 +242,10 @@ struct sip_problem {
     std::unique_ptr<sip::Multigrid<float>> mg32;
     std::unique_ptr<sip::Workspace> ws;
     // iterative refinement: eta, x, K x, B x_p in double-double; residual and
-    // correction in FP64
-    sip::DeviceBuffer eta_dd, rf_x, rf_y, rf_t, rf_r, rf_d;
+    // correction in FP64; norm scratch and its pinned read-back (created on
+    // first use, kept: freeing pinned memory would synchronise the device)
+    sip::DeviceBuffer eta_dd, rf_x, rf_y, rf_t, rf_r, rf_d, rf_scr;
+    std::unique_ptr<sip::HostScalars> rf_hs;
     double setup_ms = 0.0;
     int64_t device_bytes() const;
     void ensure_setup(cudaStream_t s);

@@ -1326,13 +1326,14 @@ sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_
     else
         SIP_CUDA(cudaMemsetAsync(r64 + n_u, 0, n_p * sizeof(double), s));
     // norms through a small device scratch (the reduction kernels of the solve)
-    DeviceBuffer scr, part;
-    scr.alloc(8 * sizeof(double));
-    part.alloc(reduction_workspace_doubles(2) * sizeof(double));
-    HostScalars hs;
+    P->rf_scr.alloc((8 + reduction_workspace_doubles(2)) * sizeof(double));
+    if (!P->rf_hs) P->rf_hs = std::make_unique<HostScalars>();
+    double* scr = P->rf_scr.as<double>();
+    double* part = scr + 8;
+    double* hsp = P->rf_hs->p;
     auto norm = [&](const double* v) {
-        launch_dot<double>(n, v, v, scr.as<double>(), part.as<double>(), s);
-        return std::sqrt(read_scalar(scr.as<double>(), hs.p, s));
+        launch_dot<double>(n, v, v, scr, part, s);
+        return std::sqrt(read_scalar(scr, hsp, s));
     };
     const double nb = norm(r64);
     sip_solve_opts o1 = o;
@@ -1380,7 +1381,7 @@ sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_
     SIP_CHECK_LAUNCH();
     const bool singular = P->desc.bc[0] != SIP_BC_NEUMANN && P->desc.bc[1] != SIP_BC_NEUMANN &&
                           P->desc.bc[2] != SIP_BC_NEUMANN && P->desc.bc[3] != SIP_BC_NEUMANN;
-    if (singular) launch_zero_mean_pressure(size_t(P->ne), P->mp, d64 + n_u, part.as<double>(), s);
+    if (singular) launch_zero_mean_pressure(size_t(P->ne), P->mp, d64 + n_u, part, s);
     SIP_CUDA(cudaMemcpyAsync(u_out, d64, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
     SIP_CUDA(cudaMemcpyAsync(p_out, d64 + n_u, n_p * sizeof(double), cudaMemcpyDeviceToDevice, s));
     SIP_CUDA(cudaStreamSynchronize(s));
@@ -1407,7 +1408,8 @@ int64_t sip_problem::device_bytes() const {
     if (mg64) b += mg64->bytes();
     if (mg32) b += mg32->bytes();
     if (ws) b += ws->bytes();
-    b += int64_t(eta_dd.bytes + rf_x.bytes + rf_y.bytes + rf_t.bytes + rf_r.bytes + rf_d.bytes);
+    b += int64_t(eta_dd.bytes + rf_x.bytes + rf_y.bytes + rf_t.bytes + rf_r.bytes + rf_d.bytes +
+                 rf_scr.bytes);
     return b;
 }
 
