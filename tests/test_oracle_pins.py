@@ -810,3 +810,22 @@ def test_refine_reaches_below_fp64_floor():
     x_ir, hist = krylov.refine(K, solve, b, 1e-11, max_steps=4)
     assert hist[-1] <= 1e-11 and len(hist) <= 3, hist
     assert exact_rel(x_ir) > 100 * hist[-1]   # the FP64 rounding is back at the floor
+
+
+def test_checkerboard_rasterised_quadrants():
+    """The checkerboard input: eta_hi exactly on the elements of the lower-
+    left and upper-right quadrants, 1 elsewhere (the jumps lie on element
+    faces for even meshes); density 1.2 only on elements wholly inside the
+    driving disc, which lies in the upper-left quadrant; Navier sides."""
+    n = 16
+    wl = synth.checkerboard(n=n, k=2, eta_hi=1e6, n_hlevels=2)
+    eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
+    xc = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(xc, xc)            # element centres, row-major (ey, ex)
+    hi = (X < 0.5) == (Y < 0.5)
+    assert np.array_equal(eta.reshape(n, n), np.where(hi, 1e6, 1.0))
+    dense = rho.reshape(n, n) > 1.0
+    assert dense.any() and np.all(rho.reshape(n, n)[dense] == 1.2)
+    assert np.all((X[dense] < 0.5) & (Y[dense] > 0.5))
+    assert np.all((X[dense] - 0.3) ** 2 + (Y[dense] - 0.65) ** 2 < 0.1 ** 2)
+    assert wl.bc == ("navier",) * 4
