@@ -42,3 +42,24 @@ def test_max_over_ranks_and_rate_gloo():
 def test_single_rank_identity():
     assert bench.max_over_ranks(123.0, 1) == 123.0
     assert bench.whole_job_rate(4, 1, 2000.0) == pytest.approx(2.0)
+
+
+def test_reference_arm_line_contract(monkeypatch):
+    """The reference arm (the oracle on the host cores) prints the contract's
+    keys on the same workload configuration as the GPU arm, with its own
+    cpu_baseline and a copy-free e2e."""
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1",
+                                      "--warmup", "0"])
+    args = bench.parse()
+    line = bench.run_reference(args)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    cfg = dict(line["config"])
+    cfg.pop("step")
+    assert cfg == bench.headline_config(args)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
