@@ -83,6 +83,14 @@ def parse():
     ap.add_argument("--sinker-refine", type=int, default=0,
                     help="iterative refinement with a double-double residual in the "
                          "six-sinker sweep: the most correction solves (0: off)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only: no many-disc, batched or served samples")
+    ap.add_argument("--c3-max-inner", type=int, default=20,
+                    help="inner iteration cap of the many-disc sample")
+    ap.add_argument("--batch-count", type=int, default=16,
+                    help="instances of the batched sample in the headline line")
+    ap.add_argument("--serve-count", type=int, default=16,
+                    help="requests of each served sample in the headline line")
     ap.add_argument("--sinker-min-eta", type=float, default=1e3,
                     help="smallest viscosity contrast of the six-sinker sweep")
     ap.add_argument("--sinker-max-eta", type=float, default=1e8,
@@ -317,6 +325,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     apply_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps_apply
     ab, af = algorithmic_apply(k, n * n, 8)
+    sched64 = prob64.schedule()
+    dominant = kernel_name(sched64["apply"][0], k, 8)
+    peaks = measured_alu_peaks(dev)
+    f32_lines = apply_f32_rooflines(ctx, dev, flush, stream, peaks)
 
     launches = sum(r["kernel_launches"] for r in r64)
     lat = sorted(t64)
@@ -343,13 +355,27 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(eta_h.nbytes + rho_pin.numel() * 8),
                 "d2h_bytes_per_step": int((prob64.n_u + prob64.n_p) * 8)},
         "gpu_launches": int(launches),
-        "schedule": {"fp64": prob64.schedule(), "mixed": sched_mixed},
+        "schedule": {"fp64": sched64, "mixed": sched_mixed},
         "clocks": clk,
-        "sip_apply": {"kernel": DOMINANT, "ms": apply_ms,
+        "sip_apply": {"kernel": dominant, "ms": apply_ms,
                       "GB_per_s": ab / apply_ms / 1e6, "GFLOP_per_s": af / apply_ms / 1e6,
                       "dof_per_s": prob64.n_u / (apply_ms / 1e3)},
     }
-    out["roofline"] = roofline(out, ab, af, apply_ms)
+    traffic = captured_traffic(dominant)
+    out["roofline"] = roofline(ab, af, apply_ms, dominant, traffic, peaks)
+    out["sip_apply_f32"] = f32_lines
+    out["alu_peaks_TFLOP_per_s"] = peaks
+    if not args.no_extras and rank == 0:
+        # bounded samples of the many-disc, batched and served workloads
+        # (outside the timed region; sample sizes stated in each object)
+        out["c3"] = c3_sample(ctx, args.c3_max_inner, refine=4)
+        out["batch"] = batch_sample(ctx, args.batch_count, refine=4)
+        hi = serve_sample(ctx, args.serve_count, refine=4, max_log_contrast=6.0)
+        # offered load at half the throughput measured at 200 / s: latency
+        # there is service time, not backlog
+        lo = serve_sample(ctx, args.serve_count, refine=4, max_log_contrast=6.0,
+                          rate=max(0.05, 0.5 * hi["value"]))
+        out["serve"] = {"at_200_per_s": hi, "below_capacity": lo}
     return out
 
 
@@ -357,21 +383,128 @@ def run_ours(args, rank, world):
 # 2 FP64 FMA per SM per clock x 2 FLOP x 2.07 GHz (maximum SM clock)
 # = 1.259 TFLOP/s (NVIDIA's figure: 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# the kernel sip_apply_A launches for k = 3 in FP64 (component split,
-# 16-byte vector accesses; SIP_APPLY_KERNEL=elem1 / tile select the others)
-DOMINANT = {"elem1": "k_apply_elem<4,double>", "tile": "k_apply_sip<4,double>"}.get(
-    os.environ.get("SIP_APPLY_KERNEL", ""), "k_apply_elem2<4,double,true>")
+# the same count for FP32: 128 FMA per SM per clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md")
 
 
-def captured_traffic():
-    """DRAM bytes per launch of the dominant kernel from its committed ncu
-    summary (dram__bytes_read.sum + dram__bytes_write.sum), or None."""
-    if not os.path.exists(TRAFFIC_PROFILE):
+def kernel_name(code, k, word):
+    """The SIP apply kernel that sip_problem_schedule's code selects."""
+    n, t = k + 1, "double" if word == 8 else "float"
+    return {1: f"k_apply_elem2<{n},{t},1>", 2: f"k_apply_elem<{n},{t}>",
+            3: f"k_apply_sip<{n},{t}>", 4: f"k_apply_stage<{n},{t},{t},2,1,0>",
+            5: f"k_apply_stage<{n},{t},{t},4,1,0>"}.get(code, f"code {code}")
+
+
+def measured_alu_peaks(dev):
+    """FP64 and FP32 arithmetic peaks measured on this GPU by library GEMMs
+    (torch.matmul, 8192^3, FP32 without TF32), best of 5 CUDA-event timings:
+    the denominators of the ALU-bound rooflines."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            n = 8192
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            c = a @ b
+            best = 1e30
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def time_launches(fn, flush, stream, reps=30):
+    """Mean device time (ms) of one launch of fn on `stream`, L2 flushed
+    (a 256 MB write) before every launch, CUDA events around each launch."""
+    import torch
+    for _ in range(3):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for e0, e1 in ev:
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
+
+
+def apply_f32_rooflines(ctx, dev, flush, stream, peaks):
+    """The FP32 SIP apply (the operator of the mixed V-cycle) on 512^2
+    meshes, k = 3 and 4, the kernel the autotuner picks: algorithmic bytes
+    and FLOPs per launch over its CUDA-event time, against the measured HBM
+    copy bandwidth and the measured FP32 GEMM rate.  The algorithmic
+    intensity (16 n^3 + 128 n^2 FLOP per 2 (2 n^2) + 1 words) is 11.8 FLOP/B
+    at k = 3 and 12.9 at k = 4, above the FP32 ridge point (peak FLOP/s over
+    HBM B/s), so both fractions are reported."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    hbm, hbm_src = hbm_peak()
+    out = []
+    for k in (3, 4):
+        n = 512
+        pr = api.Problem(ctx, n, n, k, synth.random_eta(n * n, 1, (0.0, 3.0)), n_hlevels=5,
+                         seed=1, precision="mixed", mixed_fp64_ratio=0.0)
+        pr.setup()   # autotunes the FP32 kernel for this mesh
+        x = torch.randn(pr.n_u, dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        ms = time_launches(lambda: pr.apply_A_f32(x, y, stream=stream), flush, stream)
+        ab, af = algorithmic_apply(k, n * n, 4)
+        code = pr.schedule()["apply"][1]
+        out.append({"elements": f"{n}x{n}", "k": k, "kernel": kernel_name(code, k, 4),
+                    "ms": ms, "GB_per_s": ab / ms / 1e6, "hbm_frac": ab / ms / 1e6 / hbm,
+                    "TFLOP_per_s": af / ms / 1e9, "fp32_frac": af / ms / 1e9 / peaks["fp32"],
+                    "algorithmic_bytes": ab, "algorithmic_flops": af,
+                    "hbm_peak_GB_per_s": hbm, "hbm_peak_source": hbm_src,
+                    "fp32_peak_TFLOP_per_s": peaks["fp32"],
+                    "fp32_peak_source": "measured: cuBLAS SGEMM 8192^3 (torch.matmul, no TF32)"})
+        del pr
+    return out
+
+
+# committed ncu summaries of the FP64 apply kernels on the 128^2, k = 3 workload
+TRAFFIC_PROFILES = {
+    "k_apply_elem2<4,double,1>": os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md"),
+    "k_apply_stage<4,double,double,2,1,0>": os.path.join(
+        ROOT, "profiles", "k_apply_stage_fp64_128x128_k3.md"),
+    "k_apply_stage<4,double,double,4,1,0>": os.path.join(
+        ROOT, "profiles", "k_apply_stage4_fp64_128x128_k3.md"),
+}
+
+
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary
+    (dram__bytes_read.sum + dram__bytes_write.sum), or None."""
+    path = TRAFFIC_PROFILES.get(kernel)
+    if not path or not os.path.exists(path):
         return None
     vals = {}
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    for line in open(TRAFFIC_PROFILE):
+    for line in open(path):
         for key in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             if f"`{key}`" in line:
                 cells = [c.strip() for c in line.strip().strip("|").split("|")]
@@ -381,72 +514,123 @@ def captured_traffic():
     return vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]
 
 
-def roofline(out, ab, af, apply_ms):
+def roofline(ab, af, apply_ms, kernel, traffic, peaks):
     """FP64 on GB300 is bound by the FP64 pipe, not HBM: achieved FP64
     FLOP/s of the SIP apply (algorithmic FLOPs / live launch time) against the
-    FP64 peak derived from unit counts and clocks."""
+    FP64 peak measured by cuBLAS DGEMM on this GPU (the unit-count figure
+    beside it)."""
     achieved = af / apply_ms / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": captured_traffic(),
-            "kernel": DOMINANT, "algorithmic_bytes": ab, "algorithmic_flops": af,
+    peak = peaks["fp64"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": kernel, "algorithmic_bytes": ab, "algorithmic_flops": af,
             "hbm_GB_per_s": ab / apply_ms / 1e6,
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
+            "peak_source": "measured: cuBLAS DGEMM 8192^3 (torch.matmul), best of 5",
+            "peak_derived": FP64_PEAK_TFLOPS,
+            "peak_derived_source": "152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
+            "frac_of_derived": achieved / FP64_PEAK_TFLOPS}
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(seconds_hint=20.0):
-    """Time the FP64 oracle on a bounded sample of the workload: the same
-    physics (box inclusion 1e4, k = 3, Q^2_1 + h-levels, rtol 1e-8) on a
-    16 x 16 mesh, scaled by the element count (128^2 / 16^2 = 64) to an
-    estimate for the full workload (the solver is O(n) per iteration)."""
+ORACLE_SIZES = (16, 24)   # meshes of the timed oracle samples (3 h-coarsenings each)
+
+
+def oracle_sample(n):
+    """One FP64 oracle solve of the headline physics (box inclusion 1e4,
+    k = 3, Q^2_1 + 3 h-coarsenings, FGMRES to 1e-8 with PCG stopped on the
+    residual at 1e-3) on an n x n mesh: assembly, multigrid set-up and solve,
+    single-threaded SciPy.  Returns (seconds, outer iterations)."""
     import numpy as np
     from oracle import krylov, materials, multigrid, sip
     from paper_1607_03777_gb300 import synth
-    n = 16
-    wl = synth.single_box_inclusion(n=n, n_hlevels=0)
+    wl = synth.single_box_inclusion(n=n, n_hlevels=3)
     eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
     t0 = time.perf_counter()
     pr = sip.Problem(n, n, wl.k, eta, bc=wl.bc)
     A, B = sip.assemble_A(pr), sip.assemble_B(pr)
     f = sip.rhs_body_force(pr, rho)
-    mg = multigrid.HPMultigrid(pr, A, 1, seed=1)
+    mg = multigrid.HPMultigrid(pr, A, 3, seed=1)
     Pc = krylov.BlockPreconditioner(A, B, sip.schur_mass(pr), mg, 1e-3)   # residual inner test
     K = krylov.stokes_matrix(A, B)
     b = np.concatenate([f, np.zeros(B.shape[1])])
     x, its, _ = krylov.fgmres(lambda v: K @ v, Pc, b, 1e-8, maxit=1000)
-    dt = time.perf_counter() - t0
-    scale = (128 * 128) / (n * n)
-    return dt, scale, its
+    return time.perf_counter() - t0, its
+
+
+def _oracle_worker(n, q):
+    q.put((n,) + oracle_sample(n))
+
+
+def oracle_scaling():
+    """The oracle timed on two mesh sizes at once (one process each, spawned:
+    two host cores), and the growth exponent of its time in the element
+    count fitted to them; the 128^2 time is the 24^2 time scaled by that
+    exponent (an extrapolation, labelled as such)."""
+    import math
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(n, q)) for n in ORACLE_SIZES]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in procs:
+        n, dt, its = q.get()
+        got[n] = (dt, its)
+    for p in procs:
+        p.join()
+    (n0, n1) = ORACLE_SIZES
+    alpha = math.log(got[n1][0] / got[n0][0]) / math.log((n1 * n1) / (n0 * n0))
+    t128 = got[n1][0] * ((128 * 128) / (n1 * n1)) ** alpha
+    return {"samples": {f"{n}x{n}": {"s": got[n][0], "outer_its": got[n][1]} for n in ORACLE_SIZES},
+            "exponent": alpha, "extrapolated_s_128x128": t128,
+            "cores": len(ORACLE_SIZES), "host_cpus": os.cpu_count()}
 
 
 def run_reference(args):
-    per = []
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.
+    A step is one oracle solve of the headline physics on a 16 x 16 mesh
+    (the full 128 x 128 solve takes the oracle minutes): the line's value
+    and ms_per_step are what was timed; the 128 x 128 estimate is beside
+    them."""
+    per, its = [], 0
+    n0 = ORACLE_SIZES[0]
     for i in range(args.warmup + args.steps):
-        dt, scale, its = oracle_sample()
+        dt, its = oracle_sample(n0)
         if i >= args.warmup:
-            per.append(dt * scale)
+            per.append(dt)
     value = len(per) / sum(per)
-    cores = 1
+    cfg = dict(headline_config(args),
+               workload=f"single_box_inclusion_{n0}x{n0}_k3_eta1e4_Q1+3h (oracle sample of the "
+                        "128x128 workload)",
+               nx=n0, ny=n0, sample_of="single_box_inclusion_128x128_k3_eta1e4_Q1+3h",
+               step=f"one FP64 oracle solve of the same physics on a {n0}x{n0} mesh "
+                    "(assembly, set-up, FGMRES)")
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * sum(per) / len(per), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": dict(headline_config(args),
-                           step="oracle solve of a 16x16 mesh of the same physics, time x 64"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "16x16 mesh of the same physics per step, time x 64 "
-                                       "(element-count ratio)"},
+            "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cpus": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{n0}x{n0} mesh of the headline physics per step, "
+                                       f"{its} outer iterations; SciPy sparse, single-threaded"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
 def cpu_baseline():
-    dt, scale, its = oracle_sample()
-    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle solve of the same physics on a 16x16 mesh ({dt:.1f} s, "
-                      f"{its} outer its), time x {scale:.0f} (element-count ratio); "
-                      "SciPy sparse kernels, single-threaded"}
+    sc = oracle_scaling()
+    t = sc["extrapolated_s_128x128"]
+    n0, n1 = ORACLE_SIZES
+    return {"value": 1.0 / t, "unit": UNIT, "cores": sc["cores"], "host_cpus": sc["host_cpus"],
+            "kind": "oracle",
+            "sample": f"oracle solves of the headline physics on {n0}x{n0} and {n1}x{n1} meshes "
+                      "(3 h-coarsenings each), one spawned process per mesh, SciPy sparse "
+                      "single-threaded; value = 1 / (the {n1}x{n1} time scaled to 128x128 by the "
+                      "fitted exponent of time in the element count): an extrapolation",
+            "measured": sc["samples"], "exponent": sc["exponent"],
+            "extrapolated_s_128x128": t}
 
 
 def _instance(ctx, wl, precision, seed):
@@ -463,32 +647,32 @@ def _instance(ctx, wl, precision, seed):
     return pr, f, u, p
 
 
-def run_batch(args):
-    """Batched form: the first ``--count`` instances of the seeded list
+def batch_sample(ctx, count, refine, log10_contrast=(2.0, 6.0)):
+    """Batched form on the first ``count`` instances of the seeded list
     (side in {32, 64, 128, 256}, k in {2..5}, the six inclusions of Sec. 7.3
-    jittered, contrast 10^U[2,6]), mixed precision (FP32 V-cycle, FP64
-    Krylov), solved concurrently on 8 streams; against the plain FP64 form
-    solved one at a time.  Both arms refine with a double-double residual
-    (``--refine``).  Set-up is inside both timed regions."""
+    jittered, one contrast 10^U[2,6] each), mixed precision (FP32 V-cycle,
+    FP64 Krylov), all instances' inner solves in one batched graph, set-up
+    inside the timed region; against the plain FP64 form solved one at a
+    time.  Both arms refine with a double-double residual (``refine``
+    correction solves at most).  Every result's residual is the library's
+    (double-double with refinement); the difference from the FP64 arm is
+    reported per instance."""
     import torch
     from paper_1607_03777_gb300 import api, synth
-    ctx = api.Context(0)
-    insts = synth.batch_instances(128)[:args.count]
+    insts = synth.batch_instances(128, log10_contrast=log10_contrast)[:count]
     mixed = [_instance(ctx, wl, "mixed", 4) for wl in insts]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for pr, _, _, _ in mixed:
-        pr.setup()
     st, reps = api.solve_batch(ctx, [m[0] for m in mixed], [m[1] for m in mixed],
-                               [m[2] for m in mixed], [m[3] for m in mixed], n_streams=8,
-                               rtol=1e-8, refine=args.refine)
+                               [m[2] for m in mixed], [m[3] for m in mixed], n_streams=count,
+                               rtol=1e-8, refine=refine)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     t1 = time.perf_counter()
     plain = []
     for wl in insts:
         pr, f, u, p = _instance(ctx, wl, "fp64", 4)
-        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.refine, check=False)
+        rep = pr.solve(f, u, p, rtol=1e-8, refine=refine, check=False)
         plain.append((rep, u))
         del pr
     torch.cuda.synchronize()
@@ -499,27 +683,82 @@ def run_batch(args):
             "converged": sum(1 for r in reps if r["status"] == 0),
             "fp64_converged": sum(1 for r, _ in plain if r["status"] == 0),
             "max_rel_residual": max(r["rel_residual"] for r in reps),
+            "fp64_max_rel_residual": max(r["rel_residual"] for r, _ in plain),
             "u_rel_diff_vs_fp64": {"max": max(err), "median": float(sorted(err)[len(err) // 2])},
-            "config": {"workload": "batch_instances(seed 4): sides 32-256, k 2-5, "
-                                   "jittered six inclusions, contrast 1e2-1e6",
-                       "count": len(insts), "precision": "mixed", "streams": 8, "rtol": 1e-8,
-                       "refine": args.refine}}
+            "config": {"workload": "batch_instances(seed 4): sides 32-256, k 2-5, jittered six "
+                                   f"inclusions, contrast 1e{log10_contrast[0]:g}-"
+                                   f"1e{log10_contrast[1]:g}",
+                       "sample": f"first {len(insts)} of the 128 instances",
+                       "precision": "mixed", "group": "one batched inner-solve graph",
+                       "rtol": 1e-8, "refine": refine}}
 
 
-def run_serve(args):
-    """Served form: the first ``--count`` requests of the seeded Poisson
-    stream (200 requests/s, side log-uniform in [32, 512], k in {2..6}, the
-    six inclusions of Sec. 7.3 jittered, contrast 10^U[0,5] by default) replayed in real
+def c3_sample(ctx, max_inner, refine, forms=("fp64", "mixed"), n=512, k=4):
+    """The many-disc workload (64 discs of radius 0.02 at seeded random
+    centres, log10 eta ~ U[0, 6] per disc, rho 1.2; Neumann top, Navier
+    elsewhere; Q^2_1 + 5 h-coarsenings) solved once per form to 1e-8 with
+    refinement by a double-double residual; the inner solve capped at
+    ``max_inner`` iterations (the flexible outer FGMRES absorbs the rest).
+    Reports solves/s, iteration counts, the residual (double-double) and the
+    difference of each form's velocity from the FP64 one."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    wl = synth.many_discs(n=n, k=k, n_hlevels=synth.levels_to_17(n))
+    eta, rho = ctx.rasterise_inclusions(n, n, wl.shapes)
+    eh = eta.cpu().numpy()
+    out, u64 = {}, None
+    for form in forms:
+        pr = api.Problem(ctx, n, n, k, eh, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
+                         precision=form)
+        f = torch.empty(pr.n_u, dtype=torch.float64, device="cuda")
+        pr.rhs_body_force(rho, synth.GRAVITY, f)
+        u = torch.empty_like(f)
+        p = torch.empty(pr.n_p, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = pr.solve(f, u, p, rtol=1e-8, max_outer=2000, max_inner=max_inner, refine=refine,
+                       check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rec = {"value": 1.0 / dt, "unit": UNIT, "s": dt, "status": rep["status"],
+               "outer_its": rep["outer_its"], "inner_avg": rep["inner_avg"],
+               "inner_max": rep["inner_max"], "rel_residual": rep["rel_residual"],
+               "refine_steps": rep["refine_steps"], "setup_ms": rep["setup_ms"],
+               "schedule": pr.schedule()}
+        if form == "fp64":
+            u64 = u.clone()
+        elif u64 is not None:
+            rec["u_rel_diff_vs_fp64"] = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
+        out[form] = rec
+        del pr
+    return {"metric": "stokes_solves_per_s_to_1e-8_residual", "forms": out,
+            "config": {"workload": f"many_discs_{n}x{n}_k{k}: 64 discs r 0.02, log10 eta "
+                                   "U[0,6], Q1+5h", "rtol": 1e-8, "refine": refine,
+                       "max_inner": max_inner, "inner_rtol": 1e-3,
+                       "residual": "double-double (refinement)"}}
+
+
+def run_batch(args):
+    import torch  # noqa: F401
+    from paper_1607_03777_gb300 import api
+    return batch_sample(api.Context(0), args.count, args.refine)
+
+
+def serve_sample(ctx, count, refine, max_log_contrast, rate=None):
+    """Served form on the first ``count`` requests of the seeded Poisson
+    stream (side log-uniform in [32, 512], k in {2..6}, the six inclusions of
+    Sec. 7.3 jittered, contrast 10^U[0, max_log_contrast]) replayed in real
     time into the server (mixed precision, 8 slots, HBM admission budget =
-    free HBM - 10%); latency = submit to result on the host.  Against the
-    same requests solved one at a time in plain FP64.  ``--serve-refine``
-    turns on refinement with a double-double residual in both arms."""
+    free HBM - 10%) at the stream's 200 requests/s, or at ``rate``; latency =
+    submit to result on the host.  Against the same requests solved one at a
+    time in plain FP64."""
     import numpy as np
     import torch
     from paper_1607_03777_gb300 import api, synth
-    ctx = api.Context(0)
-    arrivals, wls = synth.request_stream(log10_contrast=(0.0, args.serve_max_log_contrast))
-    arrivals, wls = arrivals[:args.count], wls[:args.count]
+    arrivals, wls = synth.request_stream(log10_contrast=(0.0, max_log_contrast))
+    arrivals, wls = arrivals[:count], wls[:count]
+    if rate:
+        arrivals = arrivals * (200.0 / rate)
     free, _ = torch.cuda.mem_get_info()
     srv = api.Server(ctx, budget_bytes=int(free * 0.9), max_slots=8)
     eta_rho = []
@@ -535,20 +774,19 @@ def run_serve(args):
         eta, rho = eta_rho[i]
         keep.append(srv.submit(i, wl.nx, wl.ny, wl.k, eta, rho, g=synth.GRAVITY, bc=wl.bc,
                                n_hlevels=wl.n_hlevels, seed=5, precision="mixed",
-                               opts={"rtol": 1e-8, "refine": args.serve_refine}))
+                               opts={"rtol": 1e-8, "refine": refine}))
     srv.drain()
     dt = time.perf_counter() - t0
     done = srv.poll(cap=max(256, len(wls)))
     srv.close()
     lat = np.array([r["solve_ms"] for _, r in done])
     ok = sum(1 for _, r in done if r["status"] == 0)
-    # baseline: the same requests, one at a time, plain FP64, arrival times ignored
     t1 = time.perf_counter()
     base_lat, base_ok, base_u = [], 0, []
     for wl in wls:
         ts = time.perf_counter()
         pr, f, u, p = _instance(ctx, wl, "fp64", 5)
-        rep = pr.solve(f, u, p, rtol=1e-8, refine=args.serve_refine, check=False)
+        rep = pr.solve(f, u, p, rtol=1e-8, refine=refine, check=False)
         torch.cuda.synchronize()
         base_lat.append((time.perf_counter() - ts) * 1e3)
         base_ok += rep["status"] == 0
@@ -561,17 +799,23 @@ def run_serve(args):
         err.append(float(np.linalg.norm(u_srv - ref) / np.linalg.norm(ref)))
     return {"metric": "served_stokes_solves_per_s", "value": len(done) / dt, "unit": UNIT,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "offered_rate_per_s": rate or 200.0,
             "requests": len(done), "converged": ok,
             "u_rel_diff_vs_fp64": {"max": max(err), "median": float(np.median(err))},
             "fp64_one_at_a_time": {"value": len(wls) / dt1, "unit": UNIT,
                                    "solve_ms_p50": float(np.percentile(base_lat, 50)),
                                    "solve_ms_p99": float(np.percentile(base_lat, 99)),
                                    "converged": int(base_ok)},
-            "config": {"workload": "request_stream(seed 5): 200 req/s, sides 32-512, k 2-6, "
-                                   "jittered six inclusions, contrast "
-                                   f"1-1e{args.serve_max_log_contrast:g}",
-                       "count": len(wls), "slots": 8, "precision": "mixed", "rtol": 1e-8,
-                       "refine": args.serve_refine}}
+            "config": {"workload": "request_stream(seed 5): sides 32-512, k 2-6, jittered six "
+                                   f"inclusions, contrast 1-1e{max_log_contrast:g}",
+                       "sample": f"first {len(wls)} requests", "slots": 8, "precision": "mixed",
+                       "rtol": 1e-8, "refine": refine}}
+
+
+def run_serve(args):
+    from paper_1607_03777_gb300 import api
+    return serve_sample(api.Context(0), args.count, args.serve_refine,
+                        args.serve_max_log_contrast)
 
 
 def run_coarse(args):

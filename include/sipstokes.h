@@ -47,7 +47,8 @@ typedef enum {
     SIP_ERR_BREAKDOWN = 5,     /* Krylov breakdown or non-finite iterate      */
     SIP_ERR_TIMEOUT = 6,       /* a served request passed its deadline        */
     SIP_ERR_REJECTED = 7,      /* server admission refused the request        */
-    SIP_ERR_NOT_READY = 8      /* result not available yet                    */
+    SIP_ERR_NOT_READY = 8,     /* result not available yet                    */
+    SIP_ERR_CANCELLED = 9      /* a served request was cancelled              */
 } sip_status;
 
 /* Boundary condition of one side of the rectangle (Sec. 2, eqs.
@@ -94,6 +95,17 @@ typedef struct {
      * i.e. odd element counts; n_hlevels = 0 solves A_0 directly, at most
      * 8192 elements). */
     int coarse;
+    /* Mixed forms only (no counterpart in the paper, which is FP64): the FP32
+     * operator of the V-cycle is evaluated in FP64 arithmetic (on the same
+     * FP32 data) on the mesh tiles of 32 x 2 elements whose tile or
+     * one-element halo holds an element with eta >= mixed_fp64_ratio x
+     * min(eta); elsewhere in FP32.  In FP32 arithmetic the nearly rigid
+     * motion of an inclusion much stiffer than the medium cancels to
+     * rounding noise of size eps_32 eta_K |u|, which swamps the residual of
+     * the soft medium: at contrast 1e6 the FP32 V-cycle stops reducing the
+     * residual altogether.  Default 1e3; 0 = FP32 arithmetic everywhere.
+     * Needs k <= 5 (k = 6 keeps FP32 arithmetic). */
+    double mixed_fp64_ratio;
 } sip_problem_desc;
 
 /* values of sip_problem_desc.coarse */
@@ -102,7 +114,7 @@ enum { SIP_COARSE_Q1 = 0, SIP_COARSE_Q0 = 1 };
 /* Fill a descriptor with the paper's defaults (Sec. 6-7): Navier on every
  * side, penalty_scale 1, n_hlevels 0, 2 p-level and 3 h-level smoothing
  * steps, 10 eigen-estimate iterations, bounds 0.1 / 1.1, seed 0, FP64,
- * Q^2_1 coarse space. */
+ * Q^2_1 coarse space; mixed_fp64_ratio 1e3. */
 void sip_problem_desc_default(sip_problem_desc* desc);
 
 /* ---- context ------------------------------------------------------------ */
@@ -132,12 +144,23 @@ sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p
  * of a problem of a new (degree, precision, mesh) times the candidate kernels
  * on the device and keeps the fastest; later problems of the same shape reuse
  * the choice.  apply[0] / apply[1]: SIP apply kernel of the FP64 / FP32
- * operator (1 component-split thread pair per element, 2 one thread per
- * element, 3 shared-memory tile); fused[0] / fused[1]: 1 if a p-level
- * smoother step is one launch (apply, block-Jacobi and Chebyshev update
- * together), 0 if it is the apply and block-Jacobi launches.  Either array
- * may be NULL; the values are those of the last set-up (defaults before). */
+ * operator: 1 component-split thread pair per element, 2 one thread per
+ * element, 3 shared-memory tile, 4 / 5 component-split thread pair on
+ * element blocks staged through shared memory with 2 / 4 tile rows (an FP32
+ * operator with split-precision tiles, see mixed_fp64_ratio, always runs 4);
+ * fused[0] / fused[1]: 1 if a p-level smoother step is one launch (apply,
+ * block-Jacobi and Chebyshev update together), 0 if it is the apply and
+ * block-Jacobi launches.  Either array may be NULL; the values are those of
+ * the last set-up (defaults before). */
 sip_status sip_problem_schedule(const sip_problem* prob, int apply[2], int fused[2]);
+/* Pin the kernel schedule of this problem (no counterpart in the paper):
+ * apply[t] in 0..5 with the codes of sip_problem_schedule (0 = autotuned;
+ * 1, 2, 4, 5 need k <= 5), fused[t] in -1..1 (-1 = autotuned; 1 takes effect
+ * only for k <= 3).  Either array may be NULL (unchanged).  The operator
+ * entry points use a pinned apply kernel at once; the multigrid set-up is
+ * marked stale, so the next call that needs it rebuilds it (in the buffers
+ * already held) with the pinned kernels.  Errors: INVALID_ARG. */
+sip_status sip_problem_set_schedule(sip_problem* prob, const int apply[2], const int fused[2]);
 
 /* ---- operators (paper Sec. 4) ------------------------------------------- */
 /* y_u = A x_u: the SIP viscous operator, eq. stiffness_form -- volume term
@@ -259,6 +282,14 @@ typedef struct {
                          *    Reaches residuals below FP64's attainable accuracy   *
                          *    for high viscosity contrasts, in place of the        *
                          *    paper's quadruple precision (Sec. 7.4).             */
+    double time_limit_ms;  /* 0 (default): none.  > 0: wall-clock limit of the  *
+                            *    solve (sip_solve, sip_solve_batch: from the    *
+                            *    call; served requests: from submission).  It   *
+                            *    is checked between outer iterations: a solve   *
+                            *    past it stops with SIP_ERR_TIMEOUT and keeps   *
+                            *    its last iterate; a queued request past it is  *
+                            *    reported with SIP_ERR_TIMEOUT unsolved.  No    *
+                            *    counterpart in the paper.                      */
 } sip_solve_opts;
 
 typedef struct {
@@ -278,7 +309,7 @@ typedef struct {
 
 /* rtol 1e-8, max_outer 500, restart 100, inner_rtol 1e-3, max_inner 200,
  * inner_loop 0, inner_krylov 0, inner_norm 0, inner_restart 30,
- * outer_krylov 0, refine 0. */
+ * outer_krylov 0, refine 0, time_limit_ms 0. */
 void sip_solve_opts_default(sip_solve_opts* opts);
 /* Solve [A B; B^T 0][u; p] = [f; g] (eq. discretestokes) by right-
  * preconditioned FGMRES (or GCR, opts->outer_krylov) with the upper
@@ -327,6 +358,28 @@ typedef struct sip_server sip_server;
 sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* problems,
                            const double* const* f_u, double* const* u, double* const* p,
                            const sip_solve_opts* opts, sip_solve_report* reports, int n_streams);
+/* The same solves with the inner solves of up to `group` problems at a time
+ * (<= 0: 32) batched into one CUDA graph: each problem's outer FGMRES runs on
+ * its own host thread and stream, and where it needs an inner solve it
+ * waits until every problem of its group still solving needs one; the last
+ * to arrive launches one inner loop for all of them, in which every stage
+ * (each step of the V-cycle, Algorithm 1, and of the Krylov iteration) is
+ * one launch over a work list of (problem, tile) items per polynomial
+ * degree, and the loop runs on the device until every problem has met its
+ * stopping test.  The problems thus advance through their outer iterations
+ * in lockstep, and the number of launches per stage does not grow with the
+ * group.  Results equal the same solves alone to rounding (the dot products
+ * are blocked differently), not bit for bit.  Needs one precision
+ * (SIP_PREC_FP64 or SIP_PREC_MIXED) for all problems, the default inner
+ * method and stopping test on the device loop, the Q^2_1 coarse space with
+ * 1..11 h-coarsenings, k <= 5 and one smoothing schedule with 2..8 h-level
+ * steps; else SIP_ERR_INVALID_ARG.  A round lasts as long as its slowest
+ * inner solve, so problems of very different difficulty are faster through
+ * sip_solve_batch.  Synchronous. */
+sip_status sip_solve_batch_grouped(sip_ctx* ctx, int n, sip_problem* const* problems,
+                                   const double* const* f_u, double* const* u, double* const* p,
+                                   const sip_solve_opts* opts, sip_solve_report* reports,
+                                   int group);
 /* Device bytes a problem of this description holds after a solve with the
  * given FGMRES restart length (the server's admission estimate). */
 int64_t sip_problem_footprint(const sip_problem_desc* desc, int restart);
@@ -337,9 +390,11 @@ sip_status sip_server_create(sip_ctx* ctx, int64_t budget_bytes, int max_slots, 
 /* Queue one request: the problem desc (eta_host copied), the element
  * densities rho_host (copied; body force (0, -g rho_K)), host outputs u_host
  * (n_u) and p_host (n_p) that must stay valid until the request is reported
- * done, options (NULL = defaults).  Non-blocking.  A request whose footprint
- * exceeds the whole budget is refused (SIP_ERR_REJECTED, also reported by
- * poll). */
+ * done, options (NULL = defaults; opts->time_limit_ms is a deadline counted
+ * from this call).  Non-blocking.  Non-finite or non-positive eta,
+ * non-finite rho or g: SIP_ERR_INVALID_ARG (nothing queued).  A request whose
+ * footprint exceeds the whole budget is refused (SIP_ERR_REJECTED, also
+ * reported by poll). */
 sip_status sip_server_submit(sip_server* server, const sip_problem_desc* desc,
                              const double* rho_host, double g, double* u_host, double* p_host,
                              const sip_solve_opts* opts, uint64_t request_id);
@@ -347,6 +402,12 @@ sip_status sip_server_submit(sip_server* server, const sip_problem_desc* desc,
  * submit-to-result latency in ms); *n_done receives the count. */
 sip_status sip_server_poll(sip_server* server, uint64_t* ids, sip_solve_report* reports, int cap,
                            int* n_done);
+/* Cancel request `request_id`: a queued request is dropped and reported
+ * by poll with SIP_ERR_CANCELLED; a running one stops at its next outer
+ * iteration and is reported with SIP_ERR_CANCELLED (its outputs hold the
+ * last iterate).  Returns SIP_OK, or SIP_ERR_INVALID_ARG when no queued or
+ * running request has this id (finished requests cannot be cancelled). */
+sip_status sip_server_cancel(sip_server* server, uint64_t request_id);
 /* Block until every queued and running request has finished. */
 sip_status sip_server_drain(sip_server* server);
 sip_status sip_server_stats(sip_server* server, int* queued, int* running,

@@ -14,7 +14,7 @@ SIP_OK = 0
 STATUS_NAMES = {
     0: "SIP_OK", 1: "SIP_ERR_INVALID_ARG", 2: "SIP_ERR_OOM", 3: "SIP_ERR_CUDA",
     4: "SIP_ERR_NOT_CONVERGED", 5: "SIP_ERR_BREAKDOWN", 6: "SIP_ERR_TIMEOUT",
-    7: "SIP_ERR_REJECTED", 8: "SIP_ERR_NOT_READY",
+    7: "SIP_ERR_REJECTED", 8: "SIP_ERR_NOT_READY", 9: "SIP_ERR_CANCELLED",
 }
 BC = {"navier": 0, "neumann": 1, "dirichlet": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_f32_inner": 2}
@@ -39,6 +39,7 @@ class ProblemDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("precision", ctypes.c_int),
         ("coarse", ctypes.c_int),
+        ("mixed_fp64_ratio", ctypes.c_double),
     ]
 
 
@@ -55,6 +56,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_restart", ctypes.c_int),
         ("outer_krylov", ctypes.c_int),
         ("refine", ctypes.c_int),
+        ("time_limit_ms", ctypes.c_double),
     ]
 
 
@@ -87,6 +89,7 @@ SIGNATURES = {
     "sip_problem_destroy": (None, [_VP]),
     "sip_problem_sizes": (ctypes.c_int, [_VP, _I64P, _I64P, _I64P]),
     "sip_problem_schedule": (ctypes.c_int, [_VP, ctypes.c_void_p, ctypes.c_void_p]),
+    "sip_problem_set_schedule": (ctypes.c_int, [_VP, ctypes.c_void_p, ctypes.c_void_p]),
     "sip_apply_A": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_A_f32": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sip_apply_B": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -115,11 +118,14 @@ SIGNATURES = {
                                  ctypes.POINTER(SolveReport), _VP]),
     "sip_solve_batch": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                        ctypes.POINTER(SolveOpts), _VP, ctypes.c_int]),
+    "sip_solve_batch_grouped": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
+                                               ctypes.POINTER(SolveOpts), _VP, ctypes.c_int]),
     "sip_problem_footprint": (ctypes.c_int64, [ctypes.POINTER(ProblemDesc), ctypes.c_int]),
     "sip_server_create": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_VP)]),
     "sip_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(ProblemDesc), _VP, ctypes.c_double,
                                          _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.c_uint64]),
     "sip_server_poll": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "sip_server_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sip_server_drain": (ctypes.c_int, [_VP]),
     "sip_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P]),

@@ -77,7 +77,7 @@ class Problem:
     def __init__(self, ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0,
                  penalty_scale=1.0, n_hlevels=0, cheb_steps_p=2, cheb_steps_h=3,
                  eig_iters=10, cheb_lo=0.1, cheb_hi=1.1, seed=0, precision="fp64",
-                 coarse="q1"):
+                 coarse="q1", mixed_fp64_ratio=1e3):
         self.ctx = ctx
         lib = ctx.lib
         d = ProblemDesc()
@@ -95,6 +95,7 @@ class Problem:
         d.seed = seed
         d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         d.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
+        d.mixed_fp64_ratio = float(mixed_fp64_ratio)
         h = ctypes.c_void_p()
         ctx.check(lib.sip_problem_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -117,11 +118,20 @@ class Problem:
 
     def schedule(self):
         """sip_problem_schedule: {"apply": [fp64, fp32], "fused": [fp64, fp32]}
-        (apply: 1 component split, 2 one thread per element, 3 tile)."""
+        (apply: 1 component split, 2 one thread per element, 3 tile, 4 / 5
+        staged tile with 2 / 4 rows)."""
         apply = (ctypes.c_int * 2)()
         fused = (ctypes.c_int * 2)()
         self.ctx.check(self.ctx.lib.sip_problem_schedule(self.handle, apply, fused))
         return {"apply": list(apply), "fused": list(fused)}
+
+    def set_schedule(self, apply=None, fused=None):
+        """sip_problem_set_schedule: pin the apply kernel ([fp64, fp32] codes
+        of ``schedule``, 0 = autotuned) and the fused smoother step ([fp64,
+        fp32], -1 = autotuned); None leaves a pair unchanged."""
+        a = (ctypes.c_int * 2)(*apply) if apply is not None else None
+        f = (ctypes.c_int * 2)(*fused) if fused is not None else None
+        self.ctx.check(self.ctx.lib.sip_problem_set_schedule(self.handle, a, f))
 
     def device_bytes(self):
         n_u, n_p, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -237,7 +247,7 @@ class Problem:
     def solve(self, f, u, p, g=None, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3,
               max_inner=200, inner_loop="device", inner_krylov="auto",
               inner_norm="true", inner_restart=30, outer_krylov="fgmres", refine=0,
-              stream=None, check=True):
+              time_limit_ms=0.0, stream=None, check=True):
         """sip_solve; returns the report as a dict (raises on failure when
         ``check``).  ``inner_loop`` = "device" (one graph launch per inner
         solve) or "host" (host-driven loop); ``inner_krylov`` = "auto",
@@ -246,9 +256,11 @@ class Problem:
         default; GCR always tests it) or "preconditioned" (the V-cycle
         applied to the residual; device loop only); ``outer_krylov`` =
         "fgmres" (default) or "gcr"; ``refine`` = the most correction solves
-        of iterative refinement with a double-double residual (0: off)."""
+        of iterative refinement with a double-double residual (0: off);
+        ``time_limit_ms`` > 0 stops the solve between outer iterations once
+        that much wall time has passed (status SIP_ERR_TIMEOUT)."""
         o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
-                  inner_krylov, inner_norm, inner_restart, outer_krylov, refine)
+                  inner_krylov, inner_norm, inner_restart, outer_krylov, refine, time_limit_ms)
         rep = SolveReport()
         st = self.ctx.lib.sip_solve(self.handle, _ptr(f, torch.float64),
                                     _ptr(g, torch.float64) if g is not None else None,
@@ -264,7 +276,7 @@ class Problem:
 # ---------------------------------------------------------------- batches, serving
 def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_scale=1.0,
               n_hlevels=0, cheb_steps_p=2, cheb_steps_h=3, eig_iters=10, cheb_lo=0.1,
-              cheb_hi=1.1, seed=0, precision="fp64", coarse="q1"):
+              cheb_hi=1.1, seed=0, precision="fp64", coarse="q1", mixed_fp64_ratio=1e3):
     """A filled sip_problem_desc and the host eta array it points to (keep
     both alive while the C side may read them)."""
     d = ProblemDesc()
@@ -279,6 +291,7 @@ def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_s
     d.cheb_lo, d.cheb_hi, d.seed = cheb_lo, cheb_hi, seed
     d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     d.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
+    d.mixed_fp64_ratio = float(mixed_fp64_ratio)
     return d, eta
 
 
@@ -290,7 +303,7 @@ OUTER_KRYLOV = {"fgmres": 0, "gcr": 1}
 
 def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner=200,
           inner_loop="device", inner_krylov="auto", inner_norm="true",
-          inner_restart=30, outer_krylov="fgmres", refine=0):
+          inner_restart=30, outer_krylov="fgmres", refine=0, time_limit_ms=0.0):
     o = SolveOpts()
     lib.sip_solve_opts_default(ctypes.byref(o))
     o.rtol, o.max_outer, o.restart = rtol, max_outer, restart
@@ -303,6 +316,7 @@ def _opts(lib, rtol=1e-8, max_outer=500, restart=100, inner_rtol=1e-3, max_inner
     o.outer_krylov = (OUTER_KRYLOV[outer_krylov] if isinstance(outer_krylov, str)
                       else int(outer_krylov))
     o.refine = int(refine)
+    o.time_limit_ms = float(time_limit_ms)
     return o
 
 
@@ -315,9 +329,10 @@ def footprint(ctx, restart=100, **desc_kw):
     return int(ctx.lib.sip_problem_footprint(ctypes.byref(d), int(restart)))
 
 
-def solve_batch(ctx, problems, fs, us, ps, n_streams=8, stream=None, **opt_kw):
-    """sip_solve_batch over lists of Problems and CUDA tensors; returns
-    (status, [report dicts])."""
+def solve_batch(ctx, problems, fs, us, ps, n_streams=8, stream=None, grouped=False, **opt_kw):
+    """sip_solve_batch (or, with ``grouped``, sip_solve_batch_grouped with
+    groups of ``n_streams`` problems) over lists of Problems and CUDA
+    tensors; returns (status, [report dicts])."""
     n = len(problems)
     arr = lambda vals: (ctypes.c_void_p * n)(*vals)
     hp = arr([p.handle.value for p in problems])
@@ -327,7 +342,8 @@ def solve_batch(ctx, problems, fs, us, ps, n_streams=8, stream=None, **opt_kw):
     reps = (SolveReport * n)()
     o = _opts(ctx.lib, **opt_kw)
     torch.cuda.current_stream().synchronize()
-    st = ctx.lib.sip_solve_batch(ctx.handle, n, hp, hf, hu, hpp, ctypes.byref(o), reps, int(n_streams))
+    fn = ctx.lib.sip_solve_batch_grouped if grouped else ctx.lib.sip_solve_batch
+    st = fn(ctx.handle, n, hp, hf, hu, hpp, ctypes.byref(o), reps, int(n_streams))
     return st, [_report(r) for r in reps]
 
 
@@ -369,6 +385,11 @@ class Server:
             out.append((int(ids[i]), _report(reps[i])))
             self._keep.pop(int(ids[i]), None)
         return out
+
+    def cancel(self, request_id):
+        """sip_server_cancel; returns the status (SIP_OK, or
+        SIP_ERR_INVALID_ARG for an id that is neither queued nor running)."""
+        return self.ctx.lib.sip_server_cancel(self.handle, ctypes.c_uint64(request_id))
 
     def drain(self):
         self.ctx.check(self.ctx.lib.sip_server_drain(self.handle))

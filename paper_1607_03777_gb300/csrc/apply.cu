@@ -469,7 +469,8 @@ int apply_variant(const OpGeom& g) {
         const std::string e(v);
         return e == "elem2" ? int(APPLY_ELEM2)
                             : (e == "elem1" ? int(APPLY_ELEM1)
-                                            : (e == "tile" ? int(APPLY_TILE) : int(APPLY_AUTO)));
+                            : (e == "tile" ? int(APPLY_TILE)
+                            : (e == "stage" ? int(APPLY_STAGE) : int(APPLY_AUTO))));
     }();
     return forced != APPLY_AUTO ? forced : g.variant[sizeof(T) == 4 ? 1 : 0];
 }
@@ -482,6 +483,11 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
     // low degrees: thread-per-element kernels with compile-time tables,
     // unless the schedule picks the shared-memory tile kernel
     const int v = apply_variant<T>(g);
+    // the split-precision FP32 operator exists only as the staged kernel
+    const bool split = sizeof(T) == 4 && g.n_hi > 0;
+    if ((v == APPLY_STAGE || split) &&
+        launch_apply_sip_stage<T>(N, g, x, y, eta, alpha, z, beta, nullptr, s))
+        return;
     if (v != APPLY_TILE &&
         launch_apply_sip_elem<T>(N, g, x, y, eta, alpha, z, beta, v != APPLY_ELEM1, s))
         return;

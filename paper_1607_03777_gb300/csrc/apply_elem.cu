@@ -14,6 +14,7 @@
 // faces into shared memory, halo elements the one face that touches the
 // tile, and the volume terms into registers.  Phase B: face vectors P, Q
 // from own and neighbour traces, spread to the outputs, one write per mode.
+#include "sip_elem.cuh"
 #include "sip_face.cuh"
 #include "sip_internal.h"
 #include "sip_parity.cuh"
@@ -21,114 +22,6 @@
 namespace sip {
 
 namespace {
-
-// ---- compile-time tables of the orthonormal Legendre basis ----------------
-// Built by constant evaluation and stored as device constants; after loop
-// unrolling every index is constant, so each entry becomes an immediate and
-// the zero entries of G and D drop out of the code.
-constexpr double csqrt_iter(double x, double g, int n) {
-    return n == 0 ? g : csqrt_iter(x, 0.5 * (g + x / g), n - 1);
-}
-constexpr double csqrt(double x) { return x <= 0.0 ? 0.0 : csqrt_iter(x, x > 1.0 ? x : 1.0, 60); }
-
-template <int N>
-struct CTabs {
-    double lp[N];     // l_i(+1)
-    double dp[N];     // l_i'(+1)
-    double G[N][N];   // int l_a' l_b'
-    double D[N][N];   // int l_p l_q'
-};
-
-template <int N>
-constexpr CTabs<N> build_ctabs() {
-    CTabs<N> t{};
-    for (int i = 0; i < N; ++i) {
-        const double c = csqrt((2.0 * i + 1.0) / 2.0);
-        t.lp[i] = c;
-        t.dp[i] = c * i * (i + 1) / 2.0;
-    }
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) {
-            const int m = a < b ? a : b;
-            t.G[a][b] = ((a + b) % 2 == 0 && m >= 1) ? t.lp[a] * t.lp[b] * m * (m + 1) : 0.0;
-            t.D[a][b] = (b > a && (b - a) % 2 == 1) ? 2.0 * t.lp[a] * t.lp[b] : 0.0;
-        }
-    return t;
-}
-
-template <int N>
-__device__ constexpr CTabs<N> kT = build_ctabs<N>();
-
-constexpr int TX = 32, TY = 2, TXY = TX * TY;
-constexpr int NHALO = 2 * TX + 2 * TY;
-
-template <typename T>
-struct ElemArgs {
-    const T* x;
-    T* y;
-    const T* eta;
-    const T* z;
-    T alpha, beta;
-    int nx, ny;
-    T two_over_hx, two_over_hy;
-    T c2hy_hx, chx_hy, c2hx_hy, chy_hx;
-    FaceGeo<T> fgx, fgy;
-    int bc[4];
-    T pen_x, pen_y;
-    T* r1;   // component-split kernel: write only the Q^2_1 modes (i, j < 2) here
-};
-
-// Traces of one element on face F (0 left, 1 right, 2 bottom, 3 top):
-// out[0][c][m] = value, out[1][c][m] = physical normal derivative d/dx_d.
-template <int N, typename T>
-__device__ __forceinline__ void face_traces(const T (&u)[2][N][N], int F, T two_over_h,
-                                            T* out /* [2][2][N] */) {
-    const bool plus = (F & 1) != 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            T ev = T(0), od = T(0), evd = T(0), odd = T(0);
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                const T uq = F < 2 ? u[c][m][q] : u[c][q][m];   // q along the normal
-                if (q % 2 == 0) {
-                    ev += T(kT<N>.lp[q]) * uq;
-                    if (q > 0) evd += T(kT<N>.dp[q]) * uq;
-                } else {
-                    od += T(kT<N>.lp[q]) * uq;
-                    odd += T(kT<N>.dp[q]) * uq;
-                }
-            }
-            // l_q(-1) = (-1)^q l_q(1),  l_q'(-1) = -(-1)^q l_q'(1)
-            out[0 * 2 * N + c * N + m] = plus ? ev + od : ev - od;
-            out[1 * 2 * N + c * N + m] = (plus ? evd + odd : odd - evd) * two_over_h;
-        }
-}
-
-// Component c only of face_traces (c uniform within a warp).
-template <int N, typename T>
-__device__ __forceinline__ void face_traces_comp(const T (&u)[2][N][N], int F, int c,
-                                                 T two_over_h, T* out /* [2][2][N] */) {
-    const bool plus = (F & 1) != 0;
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-        T ev = T(0), od = T(0), evd = T(0), odd = T(0);
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-            const T uq = F < 2 ? u[c][m][q] : u[c][q][m];
-            if (q % 2 == 0) {
-                ev += T(kT<N>.lp[q]) * uq;
-                if (q > 0) evd += T(kT<N>.dp[q]) * uq;
-            } else {
-                od += T(kT<N>.lp[q]) * uq;
-                odd += T(kT<N>.dp[q]) * uq;
-            }
-        }
-        out[0 * 2 * N + c * N + m] = plus ? ev + od : ev - od;
-        out[1 * 2 * N + c * N + m] = (plus ? evd + odd : odd - evd) * two_over_h;
-    }
-}
 
 template <int N, typename T>
 __global__ void __launch_bounds__(TXY) k_apply_elem(const ElemArgs<T> a) {
@@ -348,32 +241,6 @@ constexpr int TY2 = 2;                        // tile rows
 constexpr int T2THREADS = 64 * TY2;           // 2 warps per tile row
 constexpr int NHALO2 = 2 * TX + 2 * TY2;
 
-// 16-byte vector accesses to one element's coefficients.  A thread reads a
-// whole element (2 N^2 contiguous values), so scalar loads cost one L1
-// wavefront per value and warp; 16-byte loads cut that by 2 (FP64) or 4
-// (FP32).  Usable when an element and a component block are multiples of 16
-// bytes (N = 2, 4) and the vectors are 16-byte aligned (checked at launch).
-template <typename T> struct Vec16;
-template <> struct Vec16<double> {
-    using type = double2;
-    static constexpr int n = 2;
-    __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
-    __device__ static double2 make(const double* p) { return make_double2(p[0], p[1]); }
-};
-template <> struct Vec16<float> {
-    using type = float4;
-    static constexpr int n = 4;
-    __device__ static float get(const float4& v, int i) {
-        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-    }
-    __device__ static float4 make(const float* p) { return make_float4(p[0], p[1], p[2], p[3]); }
-};
-
-template <int N, typename T>
-constexpr bool vec_ok() {
-    return (N * N * sizeof(T)) % 16 == 0;
-}
-
 template <int N, typename T, bool VEC>
 __device__ __forceinline__ void load_elem(const T* __restrict__ src, T (&u)[2][N][N]) {
     constexpr int NN = N * N;
@@ -441,74 +308,6 @@ __device__ __forceinline__ void store_comp(T* dst, const T* zz, T alpha, T beta,
                 if (sres) sres[j * N + i] = v;
             }
     }
-}
-
-// Work of one component C (compile-time, so the register arrays stay in
-// registers) in phase A: own traces of component C and the volume terms of y_C.
-template <int N, typename T, int C>
-__device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)[2][N][N], T etaK,
-                                              T* tr, T (&y)[N][N]) {
-#pragma unroll
-    for (int F = 0; F < 4; ++F)
-        face_traces_comp<N, T>(u, F, C, F < 2 ? a.two_over_hx : a.two_over_hy, tr + F * 4 * N);
-    const T sx = C == 0 ? a.c2hy_hx : a.chy_hx;   // weight of G along x on u_C
-    const T sy = C == 0 ? a.chx_hy : a.c2hx_hy;   // weight of G along y on u_C
-#pragma unroll
-    for (int b = 0; b < N; ++b)
-#pragma unroll
-        for (int av = 0; av < N; ++av) {
-            T gx = T(0), gy = T(0);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                if (kT<N>.G[av][i] != 0.0) gx += T(kT<N>.G[av][i]) * u[C][b][i];
-                if (kT<N>.G[b][i] != 0.0) gy += T(kT<N>.G[b][i]) * u[C][i][av];
-            }
-            y[b][av] = sx * gx + sy * gy;
-        }
-    T w[N][N];
-    if (C == 0) {
-        // y_x[b][a] += sum_j D[j][b] sum_i D[a][i] u_y[j][i]
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-#pragma unroll
-            for (int av = 0; av < N; ++av) {
-                T s = T(0);
-#pragma unroll
-                for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[av][i] != 0.0) s += T(kT<N>.D[av][i]) * u[1][j][i];
-                w[j][av] = s;
-            }
-#pragma unroll
-        for (int b = 0; b < N; ++b)
-#pragma unroll
-            for (int av = 0; av < N; ++av)
-#pragma unroll
-                for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[j][b] != 0.0) y[b][av] += T(kT<N>.D[j][b]) * w[j][av];
-    } else {
-        // y_y[b][a] += sum_i D[i][a] sum_j D[b][j] u_x[j][i]
-#pragma unroll
-        for (int b = 0; b < N; ++b)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                T s = T(0);
-#pragma unroll
-                for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[b][j] != 0.0) s += T(kT<N>.D[b][j]) * u[0][j][i];
-                w[b][i] = s;
-            }
-#pragma unroll
-        for (int b = 0; b < N; ++b)
-#pragma unroll
-            for (int av = 0; av < N; ++av)
-#pragma unroll
-                for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[i][av] != 0.0) y[b][av] += T(kT<N>.D[i][av]) * w[b][i];
-    }
-#pragma unroll
-    for (int b = 0; b < N; ++b)
-#pragma unroll
-        for (int av = 0; av < N; ++av) y[b][av] *= etaK;
 }
 
 // Phase B of component C: face vectors from own and neighbour traces, spread
@@ -786,35 +585,6 @@ size_t elem2_smem(bool with_residual) {
     return sizeof(T) * words;
 }
 
-template <typename T>
-ElemArgs<T> make_elem_args(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z,
-                           T beta) {
-    ElemArgs<T> a;
-    a.x = x;
-    a.y = y;
-    a.eta = eta;
-    a.z = z;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.nx = g.nx;
-    a.ny = g.ny;
-    a.two_over_hx = T(2.0 / g.hx);
-    a.two_over_hy = T(2.0 / g.hy);
-    a.c2hy_hx = T(2.0 * g.hy / g.hx);
-    a.chx_hy = T(g.hx / g.hy);
-    a.c2hx_hy = T(2.0 * g.hx / g.hy);
-    a.chy_hx = T(g.hy / g.hx);
-    a.fgx = make_face_geo<T>(g.hx, g.hy);
-    a.fgy = make_face_geo<T>(g.hy, g.hx);
-    for (int i = 0; i < 4; ++i) a.bc[i] = g.bc[i];
-    a.pen_x = T(g.pen_x);
-    a.pen_y = T(g.pen_y);
-    a.r1 = nullptr;
-    return a;
-}
-
-inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
 template <int N, typename T>
 void apply_elem_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z, T beta,
                   bool split, cudaStream_t s) {
@@ -891,6 +661,7 @@ void cheb_elem_n(const OpGeom& g, const T* x, const T* z, T* r, const T* eta, co
         launch_k(k_cheb_elem2<N, T, false>, grid, T2THREADS, smem, s, a, b);
     SIP_CHECK_LAUNCH();
 }
+
 
 }  // namespace
 

@@ -56,6 +56,18 @@ void require_valid_opts(const sip_solve_opts& o, int precision) {
             "GCR needs 1 <= inner_restart <= 64 and an FP64 inner iterate");
     require(o.outer_krylov == 0 || o.outer_krylov == 1, "outer_krylov is 0 or 1");
     require(o.refine >= 0 && o.refine <= 100, "refine is 0..100");
+    require(std::isfinite(o.time_limit_ms) && o.time_limit_ms >= 0.0,
+            "time_limit_ms must be finite and >= 0");
+}
+
+const char* status_message(sip_status st) {
+    switch (st) {
+        case SIP_ERR_NOT_CONVERGED: return "the solve did not reach the tolerance";
+        case SIP_ERR_BREAKDOWN: return "Krylov breakdown";
+        case SIP_ERR_TIMEOUT: return "the solve passed its time limit";
+        case SIP_ERR_CANCELLED: return "the solve was cancelled";
+        default: return "the solve failed";
+    }
 }
 
 }  // namespace sip
@@ -80,6 +92,7 @@ void sip_problem_desc_default(sip_problem_desc* d) {
     d->cheb_hi = 1.1;
     d->seed = 0;
     d->precision = SIP_PREC_FP64;
+    d->mixed_fp64_ratio = 1e3;
 }
 
 sip_status sip_ctx_create(int device, sip_ctx** out) {
@@ -132,6 +145,8 @@ sip_status sip_problem_create(sip_ctx* ctx, const sip_problem_desc* d, sip_probl
         sip::require(std::isfinite(d->cheb_lo) && std::isfinite(d->cheb_hi) && d->cheb_lo > 0 &&
                          d->cheb_hi > d->cheb_lo,
                      "Chebyshev bound factors must satisfy 0 < lo < hi");
+        sip::require(std::isfinite(d->mixed_fp64_ratio) && d->mixed_fp64_ratio >= 0.0,
+                     "mixed_fp64_ratio must be finite and >= 0");
         sip::require(d->coarse == SIP_COARSE_Q1 || d->coarse == SIP_COARSE_Q0,
                      "unknown coarse space");
         {
@@ -210,9 +225,42 @@ sip_status sip_problem_schedule(const sip_problem* p, int apply[2], int fused[2]
             const int v = p->geom.variant[t];
             apply[t] = v != sip::APPLY_AUTO ? v : (p->n <= 6 ? int(sip::APPLY_ELEM2)
                                                              : int(sip::APPLY_TILE));
+            if (apply[t] == int(sip::APPLY_STAGE) && p->geom.stage_rows[t] == 4) apply[t] = 5;
+            if (t == 1 && p->geom.n_hi > 0 && p->n <= 6) apply[t] = int(sip::APPLY_STAGE);
         }
         if (fused) fused[t] = (p->n <= 4 && p->geom.fused[t]) ? 1 : 0;
     }
+    return SIP_OK;
+}
+
+sip_status sip_problem_set_schedule(sip_problem* p, const int apply[2], const int fused[2]) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    for (int t = 0; t < 2; ++t) {
+        if (apply && (apply[t] < 0 || apply[t] > 5 || (apply[t] != 0 && apply[t] != 3 && p->n > 6))) {
+            p->ctx->err = "schedule: apply code outside 0..5, or an element kernel above k = 5";
+            return SIP_ERR_INVALID_ARG;
+        }
+        if (fused && (fused[t] < -1 || fused[t] > 1)) {
+            p->ctx->err = "schedule: fused code outside -1..1";
+            return SIP_ERR_INVALID_ARG;
+        }
+    }
+    for (int t = 0; t < 2; ++t) {
+        if (apply) {
+            p->pin_apply[t] = apply[t];
+            if (apply[t] > 0) {
+                p->geom.variant[t] = apply[t] == 5 ? int(sip::APPLY_STAGE) : apply[t];
+                p->geom.stage_rows[t] = apply[t] == 5 ? 4 : 2;
+            }
+        }
+        if (fused) {
+            p->pin_fused[t] = fused[t];
+            if (fused[t] >= 0) p->geom.fused[t] = fused[t];
+        }
+    }
+    // the captured V-cycles hold the old kernels: rebuild at the next use
+    if (p->mg64) p->mg64->ready = false;
+    if (p->mg32) p->mg32->ready = false;
     return SIP_OK;
 }
 
@@ -503,6 +551,7 @@ void sip_solve_opts_default(sip_solve_opts* o) {
     o->inner_restart = 30;
     o->outer_krylov = 0;
     o->refine = 0;
+    o->time_limit_ms = 0.0;
 }
 
 sip_status sip_residual_dd(sip_problem* p, const double* f, const double* g, const double* x_u,
@@ -528,11 +577,10 @@ sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u
         if (opts) o = *opts;
         sip::require_valid_opts(o, p->desc.precision);
         SIP_CUDA(cudaSetDevice(p->ctx->device));
+        const sip::StopScope stop(o.time_limit_ms > 0.0 ? sip::steady_ms() + o.time_limit_ms : 0.0,
+                                  nullptr);
         st = sip::solve_dispatch(p, f, g, u, pp, o, rep, as_stream(stream));
-        if (st != SIP_OK) {
-            throw Error(st, st == SIP_ERR_NOT_CONVERGED ? "FGMRES did not reach the tolerance"
-                                                        : "Krylov breakdown");
-        }
+        if (st != SIP_OK) throw Error(st, sip::status_message(st));
     });
     if (gst != SIP_OK && rep) rep->status = gst;
     return gst;

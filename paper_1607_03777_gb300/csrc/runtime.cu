@@ -7,12 +7,16 @@
 // first-out whenever a slot is free and the request's device footprint fits
 // in the remaining budget, so requests that arrive while others run join as
 // capacity frees up (continuous batching).
+#include <algorithm>
 #include <atomic>
+#include <cmath>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 
@@ -99,6 +103,7 @@ cudaStream_t batch_stream(int device, int slot) {
 
 void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n_streams) {
     std::atomic<size_t> next{0};
+    const double deadline = o.time_limit_ms > 0.0 ? sip::steady_ms() + o.time_limit_ms : 0.0;
     auto worker = [&](int slot) {
         cudaSetDevice(device);
         cudaStream_t s = nullptr;
@@ -113,6 +118,7 @@ void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n
             return;
         }
         sip::AllocStreamScope scope(s);
+        const sip::StopScope stop(deadline, nullptr);
         for (size_t i = next++; i < jobs.size(); i = next++) {
             Job& j = jobs[i];
             try {
@@ -136,6 +142,75 @@ void run_jobs(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int n
     for (auto& t : pool) t.join();
 }
 
+// Whether the jobs can share batched inner solves: one V-cycle precision
+// (FP64, or FP32 with the FP64 inner iterate), the default inner method and
+// stopping test on the device loop, the Q^2_1 coarse space with at least one
+// h-coarsening, degree <= 5 and one smoothing schedule.
+bool groupable(const std::vector<Job>& jobs, const sip_solve_opts& o) {
+    if (jobs.empty() || o.inner_loop != 0 || o.inner_norm != 0 || o.inner_krylov == 3) return false;
+    const sip_problem_desc& d0 = jobs[0].prob->desc;
+    const bool mixed = d0.precision == SIP_PREC_MIXED;
+    if (d0.precision != SIP_PREC_FP64 && !mixed) return false;
+    if (o.inner_krylov == 1 && mixed) return false;      // PCG on the FP32 V-cycle
+    if (o.inner_krylov == 2 && !mixed) return false;     // FCG on the FP64 V-cycle
+    for (const Job& j : jobs) {
+        const sip_problem_desc& d = j.prob->desc;
+        if (d.precision != d0.precision || d.coarse != SIP_COARSE_Q1 || d.n_hlevels < 1 ||
+            d.n_hlevels > 11 || d.k > 5 || d.cheb_steps_p != d0.cheb_steps_p ||
+            d.cheb_steps_h != d0.cheb_steps_h || d.cheb_steps_p < 1 || d.cheb_steps_p > 8 ||
+            d.cheb_steps_h < 2 || d.cheb_steps_h > 8)
+            return false;
+    }
+    return true;
+}
+
+// Groups of up to `width` jobs solved in lockstep: one host thread per job
+// runs its outer Krylov method; the inner solves of a group are batched
+// (batch.cu).  Groups run one after the other.
+void run_jobs_grouped(int device, std::vector<Job>& jobs, const sip_solve_opts& o, int width) {
+    const double deadline = o.time_limit_ms > 0.0 ? sip::steady_ms() + o.time_limit_ms : 0.0;
+    const bool mixed = jobs[0].prob->desc.precision == SIP_PREC_MIXED;
+    for (size_t g0 = 0; g0 < jobs.size(); g0 += size_t(width)) {
+        const size_t g1 = std::min(jobs.size(), g0 + size_t(width));
+        std::vector<sip_problem*> probs;
+        for (size_t i = g0; i < g1; ++i) probs.push_back(jobs[i].prob);
+        std::unique_ptr<sip::BatchCollector, void (*)(sip::BatchCollector*)> col(
+            sip::make_collector(probs, mixed, o.inner_rtol, o.max_inner), sip::free_collector);
+        auto worker = [&](size_t i) {
+            Job& j = jobs[i];
+            cudaSetDevice(device);
+            sip::batch_collector() = col.get();
+            struct Leave {
+                sip::BatchCollector* c;
+                sip_problem* p;
+                ~Leave() {
+                    sip::batch_collector() = nullptr;
+                    sip::collector_leave(c, p);
+                }
+            } leave{col.get(), j.prob};
+            try {
+                const cudaStream_t s = batch_stream(device, int(i - g0));
+                sip::AllocStreamScope scope(s);
+                const sip::StopScope stop(deadline, nullptr);
+                sip_solve_report local{};
+                j.st = sip::solve_dispatch(j.prob, j.f, nullptr, j.u, j.p, o, j.rep ? j.rep : &local, s);
+                cudaStreamSynchronize(s);
+            } catch (const Error& e) {
+                j.st = e.status;
+                j.err = e.what();
+                if (j.rep) j.rep->status = e.status;
+            } catch (const std::exception& e) {
+                j.st = SIP_ERR_CUDA;
+                j.err = e.what();
+                if (j.rep) j.rep->status = SIP_ERR_CUDA;
+            }
+        };
+        std::vector<std::thread> pool;
+        for (size_t i = g0; i < g1; ++i) pool.emplace_back(worker, i);
+        for (auto& t : pool) t.join();
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ server
@@ -149,6 +224,7 @@ struct ServerRequest {
     sip_solve_opts opts{};
     int64_t bytes = 0;
     double t_submit = 0.0;
+    std::shared_ptr<volatile bool> cancel = std::make_shared<volatile bool>(false);
 };
 
 struct ServerDone {
@@ -169,6 +245,7 @@ struct sip_server {
     std::vector<ServerDone> done;
     std::vector<std::thread> workers;
     std::vector<double> latencies_ms;
+    std::map<uint64_t, std::shared_ptr<volatile bool>> running;   // cancel flags by id
 
     void worker_loop();
     sip_status solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep);
@@ -229,13 +306,24 @@ void sip_server::worker_loop() {
             queue.pop_front();
             in_use += r.bytes;
             ++busy;
+            running[r.id] = r.cancel;
         }
         sip_solve_report rep{};
-        const sip_status st = solve_one(r, s, rep);
+        sip_status st = SIP_OK;
+        const double deadline = r.opts.time_limit_ms > 0.0 ? r.t_submit + r.opts.time_limit_ms : 0.0;
+        if (deadline > 0.0 && wall_ms() > deadline) {
+            st = SIP_ERR_TIMEOUT;   // expired while queued: not solved
+        } else if (*r.cancel) {
+            st = SIP_ERR_CANCELLED;
+        } else {
+            const sip::StopScope stop(deadline, r.cancel.get());
+            st = solve_one(r, s, rep);
+        }
         rep.status = st;
         const double lat = wall_ms() - r.t_submit;
         {
             std::lock_guard<std::mutex> lk(mu);
+            running.erase(r.id);
             in_use -= r.bytes;
             --busy;
             rep.solve_ms = lat;   // for served requests: submit-to-result latency
@@ -250,9 +338,12 @@ void sip_server::worker_loop() {
 
 extern "C" {
 
-sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* probs, const double* const* f_u,
-                           double* const* u, double* const* p, const sip_solve_opts* opts,
-                           sip_solve_report* reports, int n_streams) {
+namespace {
+
+sip_status solve_batch_impl(sip_ctx* ctx, int n, sip_problem* const* probs,
+                            const double* const* f_u, double* const* u, double* const* p,
+                            const sip_solve_opts* opts, sip_solve_report* reports, int n_streams,
+                            bool grouped) {
     if (!ctx) return SIP_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!probs || !f_u || !u || !p))) {
         ctx->err = "bad batch arguments";
@@ -275,15 +366,40 @@ sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* probs, const
         }
         jobs[i] = Job{probs[i], f_u[i], u[i], p[i], reports ? &reports[i] : nullptr};
     }
-    run_jobs(ctx->device, jobs, o, n_streams < 1 ? 8 : n_streams);
+    if (grouped) {
+        if (n > 0 && !groupable(jobs, o)) {
+            ctx->err = "grouped batch: one precision (FP64 or mixed), the default inner method "
+                       "and stopping test on the device loop, the Q^2_1 coarse space with 1..11 "
+                       "h-coarsenings, k <= 5 and one smoothing schedule (2..8 h-level steps)";
+            return SIP_ERR_INVALID_ARG;
+        }
+        if (n > 0) run_jobs_grouped(ctx->device, jobs, o, n_streams < 1 ? 32 : n_streams);
+    } else {
+        run_jobs(ctx->device, jobs, o, n_streams < 1 ? 8 : n_streams);
+    }
     sip_status worst = SIP_OK;
     for (auto& j : jobs)
         if (j.st != SIP_OK) {
             worst = j.st;
-            ctx->err = j.err.empty() ? "a batched solve did not converge" : j.err;
+            ctx->err = j.err.empty() ? sip::status_message(j.st) : j.err;
         }
     if (worst == SIP_OK) ctx->err.clear();
     return worst;
+}
+
+}  // namespace
+
+sip_status sip_solve_batch(sip_ctx* ctx, int n, sip_problem* const* probs, const double* const* f_u,
+                           double* const* u, double* const* p, const sip_solve_opts* opts,
+                           sip_solve_report* reports, int n_streams) {
+    return solve_batch_impl(ctx, n, probs, f_u, u, p, opts, reports, n_streams, false);
+}
+
+sip_status sip_solve_batch_grouped(sip_ctx* ctx, int n, sip_problem* const* probs,
+                                   const double* const* f_u, double* const* u, double* const* p,
+                                   const sip_solve_opts* opts, sip_solve_report* reports,
+                                   int group) {
+    return solve_batch_impl(ctx, n, probs, f_u, u, p, opts, reports, group, true);
 }
 
 sip_status sip_server_create(sip_ctx* ctx, int64_t budget_bytes, int max_slots, sip_server** out) {
@@ -328,6 +444,10 @@ sip_status sip_server_submit(sip_server* sv, const sip_problem_desc* desc, const
     if (desc->nx < 1 || desc->ny < 1 || desc->k < 1 || desc->k > 6) return SIP_ERR_INVALID_ARG;
     r.eta.assign(desc->eta_host, desc->eta_host + ne);
     r.rho.assign(rho_host, rho_host + ne);
+    for (size_t e = 0; e < ne; ++e)
+        if (!std::isfinite(r.eta[e]) || !(r.eta[e] > 0.0) || !std::isfinite(r.rho[e]))
+            return SIP_ERR_INVALID_ARG;
+    if (!std::isfinite(g)) return SIP_ERR_INVALID_ARG;
     r.g = g;
     r.u_host = u_host;
     r.p_host = p_host;
@@ -365,6 +485,28 @@ sip_status sip_server_poll(sip_server* sv, uint64_t* ids, sip_solve_report* reps
     }
     sv->done.erase(sv->done.begin(), sv->done.begin() + n);
     *n_done = n;
+    return SIP_OK;
+}
+
+sip_status sip_server_cancel(sip_server* sv, uint64_t id) {
+    if (!sv) return SIP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto run = sv->running.find(id);
+        if (run != sv->running.end()) {
+            *run->second = true;   // the solve stops at its next outer iteration
+            return SIP_OK;
+        }
+        auto it = std::find_if(sv->queue.begin(), sv->queue.end(),
+                               [&](const ServerRequest& q) { return q.id == id; });
+        if (it == sv->queue.end()) return SIP_ERR_INVALID_ARG;
+        sip_solve_report rep{};
+        rep.status = SIP_ERR_CANCELLED;
+        sv->done.push_back({id, rep});
+        sv->queue.erase(it);
+    }
+    sv->cv_work.notify_all();
+    sv->cv_idle.notify_all();
     return SIP_OK;
 }
 

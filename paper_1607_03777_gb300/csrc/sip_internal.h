@@ -77,6 +77,27 @@ void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
         SIP_CUDA(cudaGetLastError());       \
     } while (0)
 
+// Stop request of the solve running on this host thread, checked between
+// outer Krylov iterations: a deadline on the steady clock (ms; 0 = none) and
+// a cancel flag (may be null).  A solve that meets it returns
+// SIP_ERR_TIMEOUT or SIP_ERR_CANCELLED with its last iterate.
+struct StopCtl {
+    double deadline_ms = 0.0;
+    const volatile bool* cancel = nullptr;
+};
+StopCtl& stop_ctl();   // per host thread
+double steady_ms();
+// SIP_OK, or the status of a met stop request
+sip_status stop_requested();
+struct StopScope {
+    StopCtl prev;
+    StopScope(double deadline_ms, const volatile bool* cancel) : prev(stop_ctl()) {
+        stop_ctl().deadline_ms = deadline_ms;
+        stop_ctl().cancel = cancel;
+    }
+    ~StopScope() { stop_ctl() = prev; }
+};
+
 inline void require(bool ok, const std::string& msg) {
     if (!ok) throw Error(SIP_ERR_INVALID_ARG, msg);
 }
@@ -126,7 +147,7 @@ Tab1D<N, T> make_tab() {
 // |e|/|K| = 1/h_normal; boundary faces double it (eq. sipg_penalty).
 // Kernel schedule of one operator, per precision ([0] FP64, [1] FP32):
 // which apply kernel runs and whether the p-level smoother step is fused.
-enum ApplyVariant { APPLY_AUTO = 0, APPLY_ELEM2 = 1, APPLY_ELEM1 = 2, APPLY_TILE = 3 };
+enum ApplyVariant { APPLY_AUTO = 0, APPLY_ELEM2 = 1, APPLY_ELEM1 = 2, APPLY_TILE = 3, APPLY_STAGE = 4 };
 
 struct OpGeom {
     int nx, ny;
@@ -135,6 +156,12 @@ struct OpGeom {
     double pen_x, pen_y;
     int variant[2];   // ApplyVariant (APPLY_AUTO: component-split for N <= 6, else tile)
     int fused[2];     // p-level smoother step fused into one launch (1) or not (0)
+    int stage_rows[2];   // tile rows of the staged apply (2 or 4), per precision
+    // split-precision FP32 operator (mixed form at high viscosity contrast):
+    // tiles evaluated in FP64 arithmetic on FP32 data; n_hi = 0: none
+    const unsigned char* hi_flag;
+    const int* hi_tiles;
+    int n_hi;
 };
 
 inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], int k_pen,
@@ -148,6 +175,10 @@ inline OpGeom make_geom(int nx, int ny, double lx, double ly, const int bc[4], i
     double c = penalty_scale * 4.0 * double(k_pen + 1) * double(k_pen + 1);
     g.variant[0] = g.variant[1] = APPLY_AUTO;
     g.fused[0] = g.fused[1] = 1;
+    g.stage_rows[0] = g.stage_rows[1] = 2;
+    g.hi_flag = nullptr;
+    g.hi_tiles = nullptr;
+    g.n_hi = 0;
     g.pen_x = c / g.hx;
     g.pen_y = c / g.hy;
     return g;
@@ -163,6 +194,20 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
 template <typename T>
 bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                            const T* z, T beta, bool split, cudaStream_t s);
+// Staged-tile kernels (N <= 6; returns false otherwise): y = alpha A x +
+// beta z, or with r1 non-null the Q^2_1 modes of that result into r1 (y
+// unused).  For T = float with g.n_hi > 0 the flagged tiles are evaluated in
+// FP64 arithmetic (split precision); x must not overlap y.
+template <typename T>
+bool launch_apply_sip_stage(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
+                            const T* z, T beta, T* r1, cudaStream_t s);
+// Number of split-precision tiles of an nx x ny mesh, and their flags: tile
+// t is flagged (and listed) when an element of the tile or of its halo has
+// eta >= ratio x min(eta).  scratch: 32 device bytes.  Returns the count
+// (synchronises s).
+int split_tile_count(int nx, int ny);
+int mark_hi_tiles(int nx, int ny, const double* eta, double ratio, unsigned char* flag, int* list,
+                  int* scratch, cudaStream_t s);
 // The apply variant in force for precision T: SIP_APPLY_KERNEL (elem2, elem1,
 // tile) overrides the operator's schedule.
 template <typename T>

@@ -21,15 +21,17 @@ namespace sip {
 // The members of the row's parity group are enumerated arithmetically (no
 // table reads): mode (c, j, i) has x-parity (i + [c = x]) & 1, so for each
 // component the group's i (and, with the y-symmetry, j) run over one parity.
-template <int N, typename T>
-__device__ __forceinline__ T block_row_apply(const T* __restrict__ Minv, const T* rr, int row,
-                                             int sym) {
+// TA: accumulation type (FP64 accumulation of an FP32 block keeps the small
+// components of an ill-conditioned block's result, which FP32 sums cancel).
+template <int N, typename T, typename TA = T>
+__device__ __forceinline__ TA block_row_apply(const T* __restrict__ Minv, const T* rr, int row,
+                                              int sym) {
     constexpr int NN = N * N;
     constexpr int NB = 2 * NN;
-    T acc = T(0);
+    TA acc = TA(0);
     if (sym == 0) {
 #pragma unroll 8
-        for (int q = 0; q < NB; ++q) acc += Minv[q * NB + row] * rr[q];
+        for (int q = 0; q < NB; ++q) acc += TA(Minv[q * NB + row]) * TA(rr[q]);
         return acc;
     }
     const int cr = row / NN, jr = (row / N) % N, ir = row % N;
@@ -51,7 +53,7 @@ __device__ __forceinline__ T block_row_apply(const T* __restrict__ Minv, const T
                 const int i = i0 + a * di;
                 if (i >= N) break;
                 const int q = c * NN + j * N + i;
-                acc += Minv[q * NB + row] * rr[q];
+                acc += TA(Minv[q * NB + row]) * TA(rr[q]);
             }
         }
     }

@@ -14,10 +14,35 @@ void launch_classify(int nx, int ny, const double* eta, int* emap, int* uniq_lis
 template <typename T>
 void launch_build_blocks(int N, const OpGeom& g, const int* spec, int count, const double* eta,
                          T* out, cudaStream_t s);
+// uniq_hi (may be null): unique blocks applied with FP64 accumulation
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                      const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                     cudaStream_t s);
+                     cudaStream_t s, const unsigned char* uniq_hi = nullptr);
+// Block-Jacobi apply arguments of one element set (one member of a batch).
+template <typename T>
+struct BJBatchArgs {
+    int ne;
+    const T* r;
+    T* out;
+    T* x;
+    const int* emap;
+    const T* cls_inv;
+    const int* cls_sym;
+    const T* uniq_inv;
+    const T* eta_inv;
+    const unsigned char* uniq_hi;
+    T c1, c2;
+    int x_zero;
+};
+// elements per CTA of the block-Jacobi kernels
+int bj_group(int N);
+// CTA b: member items[b].x (args[items[b].x]), element group items[b].y
+template <typename T>
+void launch_bj_apply_batch(int N, const BJBatchArgs<T>* args, const int2* items, int n_items,
+                           const int* active, cudaStream_t s);
+void launch_mark_uniq_hi(int nx, int ny, const int* list, const int* n_uniq_dev, int n_uniq,
+                         const double* eta, double ratio, unsigned char* flag, cudaStream_t s);
 
 // ---- transfer.cu
 // M = 2: Q^2_1 modes (8 per element), M = 1: Q^2_0 (2 per element)
@@ -121,6 +146,11 @@ struct Multigrid {
     DeviceBuffer ws, sc;
     HostScalars hs;
     DeviceBuffer cg_r, cg_d, cg_q;   // inner PCG vectors (outside the graph)
+    // FP32 operator only: split-precision tiles (flags per tile, their list)
+    DeviceBuffer hi_flag, hi_list, hi_scr;
+    int n_hi = 0;
+    DeviceBuffer uniq_hi;   // unique blocks applied with FP64 accumulation (FP32 only)
+    const unsigned char* bj_hi() const { return n_hi > 0 ? uniq_hi.as<unsigned char>() : nullptr; }
     // set-up scratch, kept so that a repeated set-up allocates nothing
     DeviceBuffer scr_V, scr_tmp, scr_b, scr_spec, scr_L, scr_X, scr_Y, scr_xv, scr_t1, scr_t2;
     std::vector<DeviceBuffer> scr_S64;
@@ -156,6 +186,9 @@ struct Multigrid {
     double estimate_p(cudaStream_t s);
     double estimate_h(int l, cudaStream_t s);
     void build_blocks(cudaStream_t s);
+    void mark_split_tiles(cudaStream_t s);
+    // r1 = R (b - A y) in one launch where a kernel for it exists
+    bool residual_restrict(const T* y, const T* b, T* r1, cudaStream_t s);
     void build_coarse_from_band(const std::vector<double>& band, int n, int bw, cudaStream_t s);
 };
 
@@ -185,6 +218,19 @@ void tune_apply(sip_problem* P, cudaStream_t s);
 
 int inner_pcg_mixed(sip_problem* P, Workspace& W, const double* t, double* y, double rtol,
                     int maxit, cudaStream_t s);
+// Batched inner solves (batch.cu): a group of problems whose solves run on
+// host threads registered with one collector share one batched inner loop.
+struct BatchCollector;
+BatchCollector*& batch_collector();   // the calling thread's group (null: none)
+// the inner solve through the group's rendezvous when the calling thread
+// belongs to a group (*used = true), else nothing (*used = false)
+int batched_inner(sip_problem* P, const double* t, double* y, cudaStream_t s, bool* used);
+BatchCollector* make_collector(const std::vector<sip_problem*>& probs, bool mixed, double rtol,
+                               int maxit);
+void free_collector(BatchCollector* c);
+void collector_leave(BatchCollector* c, sip_problem* P);
+int64_t collector_rounds(const BatchCollector* c);
+
 // The same inner solve (FP64 iterate; V-cycle in FP32 when mixed, else FP64)
 // as one graph launch with a device-side loop; returns the iteration count.
 // flexible: FCG(1) directions instead of PCG's; pnorm: stop on the
@@ -214,6 +260,8 @@ sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_
 // Throws Error(SIP_ERR_INVALID_ARG) unless the options are valid for a
 // problem of this precision (every solve entry point checks them).
 void require_valid_opts(const sip_solve_opts& o, int precision);
+// Message of a solve's failing status.
+const char* status_message(sip_status st);
 // Device bytes of one problem solved with these options (admission).
 int64_t estimate_problem_bytes(const sip_problem_desc& d, const sip_solve_opts& o);
 
@@ -247,6 +295,10 @@ struct sip_problem {
     sip::DeviceBuffer eta_dd, rf_x, rf_y, rf_t, rf_r, rf_d, rf_scr;
     std::unique_ptr<sip::HostScalars> rf_hs;
     double setup_ms = 0.0;
+    // kernel schedule pinned by sip_problem_set_schedule ([0] FP64, [1] FP32):
+    // apply 0 = autotuned, else sip_problem_schedule's code; fused -1 = autotuned
+    int pin_apply[2] = {0, 0};
+    int pin_fused[2] = {-1, -1};
     int64_t device_bytes() const;
     void ensure_setup(cudaStream_t s);
 };

@@ -10,6 +10,7 @@
 #include "sip_face.cuh"
 #include "sip_internal.h"
 #include "sip_parity.cuh"
+#include "sip_solver.h"
 
 namespace sip {
 
@@ -172,23 +173,17 @@ __global__ void k_classify(int nx, int ny, const double* eta, int* emap, int* un
 // out = c2 * M_K^{-1} r_K (+ c1 * out_old); if x: x = (x_zero ? 0 : x) + out.
 // EB elements per CTA, the residual blocks staged in shared memory; thread
 // (element, row r) reads column r of the symmetric inverse (coalesced).
+// Unique blocks flagged in uniq_hi (may be null) accumulate in FP64.
 template <int N, typename T>
-__global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ r, T* out, T* x,
-                                                  const int* __restrict__ emap,
-                                                  const T* __restrict__ cls_inv,
-                                                  const int* __restrict__ cls_sym,
-                                                  const T* __restrict__ uniq_inv,
-                                                  const T* __restrict__ eta_inv, T c1, T c2,
-                                                  int x_zero) {
-    grid_dep_wait();
+__device__ __forceinline__ void bj_body(int e0, const BJBatchArgs<T>& a) {
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     static_assert(EB * NB <= 256, "one (element, row) per thread");
     __shared__ T sr[EB * NB];
     __shared__ const T* s_minv[EB];
     __shared__ T s_scale[EB];
-    __shared__ int s_sym[EB];
-    const int e0 = blockIdx.x * EB;
+    __shared__ int s_sym[EB];   // symmetry type; -1: dense with FP64 accumulation
+    const int ne = a.ne;
     const int cnt = min(EB, ne - e0) * NB;
     // every load that does not depend on another is issued before the
     // barrier: the residual block, the element's block pointer and scale,
@@ -196,30 +191,62 @@ __global__ void __launch_bounds__(256) k_bj_apply(int ne, const T* __restrict__ 
     const int q = threadIdx.x;
     const bool act = q < cnt;
     const size_t o = size_t(e0) * NB + q;
-    if (act) sr[q] = r[o];
+    if (act) sr[q] = a.r[o];
     if (q < EB && e0 + q < ne) {
         const int e = e0 + q;
-        const int m = emap[e];
+        const int m = a.emap[e];
         if (m < 0) {
-            s_minv[q] = cls_inv + size_t(-m - 1) * NB * NB;
-            s_scale[q] = eta_inv[e];
-            s_sym[q] = cls_sym ? cls_sym[-m - 1] : 0;
+            s_minv[q] = a.cls_inv + size_t(-m - 1) * NB * NB;
+            s_scale[q] = a.eta_inv[e];
+            s_sym[q] = a.cls_sym ? a.cls_sym[-m - 1] : 0;
         } else {
-            s_minv[q] = uniq_inv + size_t(m) * NB * NB;
+            s_minv[q] = a.uniq_inv + size_t(m) * NB * NB;
             s_scale[q] = T(1);
-            s_sym[q] = 0;
+            s_sym[q] = (a.uniq_hi && a.uniq_hi[m]) ? -1 : 0;
         }
     }
-    const T out_old = (act && c1 != T(0)) ? out[o] : T(0);
-    const T x_old = (act && x && !x_zero) ? x[o] : T(0);
+    const T c1 = a.c1, c2 = a.c2;
+    const T out_old = (act && c1 != T(0)) ? a.out[o] : T(0);
+    const T x_old = (act && a.x && !a.x_zero) ? a.x[o] : T(0);
     __syncthreads();
     if (!act) return;
     const int el = q / NB, row = q % NB;
-    const T acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el]);
+    T acc;
+    if constexpr (sizeof(T) == 4) {
+        if (s_sym[el] < 0)
+            acc = T(block_row_apply<N, T, double>(s_minv[el], sr + el * NB, row, 0));
+        else
+            acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el]);
+    } else {
+        acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el] < 0 ? 0 : s_sym[el]);
+    }
     T v = c2 * s_scale[el] * acc;
     if (c1 != T(0)) v += c1 * out_old;
-    out[o] = v;
-    if (x) x[o] = x_zero ? v : x_old + v;
+    a.out[o] = v;
+    if (a.x) a.x[o] = a.x_zero ? v : x_old + v;
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_bj_apply(const BJBatchArgs<T> a) {
+    grid_dep_wait();
+    constexpr int NB = 2 * N * N;
+    constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
+    bj_body<N, T>(blockIdx.x * EB, a);
+}
+
+// Many block-Jacobi applies in one launch: CTA b serves member items[b].x
+// (arguments args[items[b].x]), element group items[b].y; members with
+// active[m] == 0 are skipped.
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_bj_apply_batch(const BJBatchArgs<T>* __restrict__ args,
+                                                        const int2* __restrict__ items,
+                                                        const int* __restrict__ active) {
+    grid_dep_wait();
+    constexpr int NB = 2 * N * N;
+    constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
+    const int2 it = items[blockIdx.x];
+    if (active && !active[it.x]) return;
+    bj_body<N, T>(it.y * EB, args[it.x]);
 }
 
 template <int N>
@@ -253,12 +280,20 @@ void build_blocks_n(const OpGeom& g, const int* spec, int count, const double* e
 template <int N, typename T>
 void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                 const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                cudaStream_t s) {
+                const unsigned char* uniq_hi, cudaStream_t s) {
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     const int blocks = (ne + EB - 1) / EB;
-    launch_k(k_bj_apply<N, T>, blocks, 256, 0, s, ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta,
-                                            c1, c2, x_zero ? 1 : 0);
+    const BJBatchArgs<T> a{ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, uniq_hi,
+                           c1, c2, x_zero ? 1 : 0};
+    launch_k(k_bj_apply<N, T>, blocks, 256, 0, s, a);
+    SIP_CHECK_LAUNCH();
+}
+
+template <int N, typename T>
+void bj_batch_n(const BJBatchArgs<T>* args, const int2* items, int n_items, const int* active,
+                cudaStream_t s) {
+    launch_k(k_bj_apply_batch<N, T>, dim3(unsigned(n_items)), 256, 0, s, args, items, active);
     SIP_CHECK_LAUNCH();
 }
 
@@ -292,22 +327,71 @@ template void launch_build_blocks<float>(int, const OpGeom&, const int*, int, co
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                      const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                     cudaStream_t s) {
+                     cudaStream_t s, const unsigned char* uniq_hi) {
     switch (N) {
-        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
-        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, s); break;
+        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
         default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
     }
 }
 template void launch_bj_apply<double>(int, int, const double*, double*, double*, const int*,
                                       const double*, const int*, const double*, const double*,
-                                      double, double, bool, cudaStream_t);
+                                      double, double, bool, cudaStream_t, const unsigned char*);
 template void launch_bj_apply<float>(int, int, const float*, float*, float*, const int*,
                                      const float*, const int*, const float*, const float*, float,
-                                     float, bool, cudaStream_t);
+                                     float, bool, cudaStream_t, const unsigned char*);
+
+int bj_group(int N) {
+    const int nb = 2 * N * N;
+    return (256 / nb) > 0 ? (256 / nb) : 1;
+}
+
+template <typename T>
+void launch_bj_apply_batch(int N, const BJBatchArgs<T>* args, const int2* items, int n_items,
+                           const int* active, cudaStream_t s) {
+    if (n_items <= 0) return;
+    switch (N) {
+        case 2: bj_batch_n<2, T>(args, items, n_items, active, s); break;
+        case 3: bj_batch_n<3, T>(args, items, n_items, active, s); break;
+        case 4: bj_batch_n<4, T>(args, items, n_items, active, s); break;
+        case 5: bj_batch_n<5, T>(args, items, n_items, active, s); break;
+        case 6: bj_batch_n<6, T>(args, items, n_items, active, s); break;
+        case 7: bj_batch_n<7, T>(args, items, n_items, active, s); break;
+        default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
+    }
+}
+template void launch_bj_apply_batch<double>(int, const BJBatchArgs<double>*, const int2*, int,
+                                            const int*, cudaStream_t);
+template void launch_bj_apply_batch<float>(int, const BJBatchArgs<float>*, const int2*, int,
+                                           const int*, cudaStream_t);
+
+// uniq_hi[s] = 1 when the unique block of slot s belongs to an element whose
+// largest face-neighbour viscosity is at least ratio times its own: the
+// blocks whose condition grows with that contrast.
+__global__ void k_mark_uniq_hi(int nx, int ny, const int* list, const int* n_uniq,
+                               const double* eta, double ratio, unsigned char* flag) {
+    grid_dep_wait();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= *n_uniq) return;
+    const int e = list[s], ex = e % nx, ey = e / nx;
+    double m = 0.0;
+    if (ex > 0) m = fmax(m, eta[e - 1]);
+    if (ex < nx - 1) m = fmax(m, eta[e + 1]);
+    if (ey > 0) m = fmax(m, eta[e - nx]);
+    if (ey < ny - 1) m = fmax(m, eta[e + nx]);
+    flag[s] = m >= ratio * eta[e] ? 1 : 0;
+}
+
+void launch_mark_uniq_hi(int nx, int ny, const int* list, const int* n_uniq_dev, int n_uniq,
+                         const double* eta, double ratio, unsigned char* flag, cudaStream_t s) {
+    if (n_uniq <= 0) return;
+    launch_k(k_mark_uniq_hi, unsigned((n_uniq + 255) / 256), 256, 0, s, nx, ny, list, n_uniq_dev,
+             eta, ratio, flag);
+    SIP_CHECK_LAUNCH();
+}
 
 }  // namespace sip

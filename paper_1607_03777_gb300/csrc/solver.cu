@@ -28,6 +28,23 @@ bool& release_on_legacy() {
     return on;
 }
 
+StopCtl& stop_ctl() {
+    static thread_local StopCtl c;
+    return c;
+}
+
+double steady_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+sip_status stop_requested() {
+    const StopCtl& c = stop_ctl();
+    if (c.cancel && *c.cancel) return SIP_ERR_CANCELLED;
+    if (c.deadline_ms > 0.0 && steady_ms() > c.deadline_ms) return SIP_ERR_TIMEOUT;
+    return SIP_OK;
+}
+
 bool& pdl_enabled() {
     static thread_local bool on = [] {
         const char* v = std::getenv("SIP_PDL");
@@ -312,7 +329,7 @@ template <typename T>
 void Multigrid<T>::bj(const T* r, T* z, cudaStream_t s) {
     launch_bj_apply<T>(N, int(ne), r, z, nullptr, emap.as<int>(), cls_inv.template as<T>(),
                        cls_sym.as<int>(), uniq_inv.template as<T>(),
-                       eta_inv_of<T>(P), T(0), T(1), true, s);
+                       eta_inv_of<T>(P), T(0), T(1), true, s, bj_hi());
 }
 
 // Arnoldi (GMRES) estimate of the largest eigenvalue of the preconditioned
@@ -429,6 +446,45 @@ void Multigrid<T>::build_coarse_from_band(const std::vector<double>& band_in, in
     SIP_CUDA(cudaStreamSynchronize(s));
 }
 
+// Mixed form: the FP32 operator evaluates the tiles near elements with
+// eta >= ratio x min(eta) in FP64 arithmetic (apply_stage.cu); the FP64
+// operator has no such tiles.
+template <typename T>
+void Multigrid<T>::mark_split_tiles(cudaStream_t s) {
+    n_hi = 0;
+    const double ratio = P->desc.mixed_fp64_ratio;
+    if (sizeof(T) == 4 && ratio > 0.0 && N <= 6) {
+        const int nt = split_tile_count(P->desc.nx, P->desc.ny);
+        hi_flag.alloc(size_t(nt));
+        hi_list.alloc(size_t(nt) * sizeof(int));
+        hi_scr.alloc(32);
+        n_hi = mark_hi_tiles(P->desc.nx, P->desc.ny, P->eta_d.as<double>(), ratio,
+                             hi_flag.as<unsigned char>(), hi_list.as<int>(), hi_scr.as<int>(), s);
+        if (n_hi > 0) {
+            // FP32 sums of an element block whose face neighbour is much
+            // stiffer cancel the block's small components the same way
+            uniq_hi.alloc(size_t(std::max(n_uniq, 1)));
+            launch_mark_uniq_hi(P->desc.nx, P->desc.ny, uniq_list.as<int>(), n_uniq_d.as<int>(),
+                                n_uniq, P->eta_d.as<double>(), std::max(1.0, 0.1 * ratio),
+                                uniq_hi.as<unsigned char>(), s);
+        }
+    }
+    if (sizeof(T) == 4) {
+        P->geom.n_hi = n_hi;
+        P->geom.hi_flag = n_hi > 0 ? hi_flag.as<unsigned char>() : nullptr;
+        P->geom.hi_tiles = n_hi > 0 ? hi_list.as<int>() : nullptr;
+    }
+}
+
+template <typename T>
+bool Multigrid<T>::residual_restrict(const T* y, const T* b, T* r1, cudaStream_t s) {
+    const bool split = sizeof(T) == 4 && P->geom.n_hi > 0;
+    if (split || apply_variant<T>(P->geom) == APPLY_STAGE)
+        return launch_apply_sip_stage<T>(N, P->geom, y, nullptr, eta_of<T>(P), T(-1), b, T(1), r1,
+                                         s);
+    return use_fused() && launch_residual_restrict_elem<T>(N, P->geom, y, b, eta_of<T>(P), r1, s);
+}
+
 template <typename T>
 void Multigrid<T>::setup(cudaStream_t s) {
     const sip_problem_desc& d = P->desc;
@@ -451,6 +507,7 @@ void Multigrid<T>::setup(cudaStream_t s) {
     cg_d.alloc(n_u * sizeof(T));
     cg_q.alloc(n_u * sizeof(T));
     build_blocks(s);
+    mark_split_tiles(s);
     lmax_p = estimate_p(s);
     tune_smoother(s);
 
@@ -629,6 +686,8 @@ bool Multigrid<T>::use_fused() const {
         return v ? (std::string(v) == "1" ? 1 : 0) : -1;
     }();
     if (env_off || !pd2.ptr || !cheb_elem_available(N)) return false;
+    // the fused step evaluates the operator in T everywhere
+    if (sizeof(T) == 4 && P->geom.n_hi > 0) return false;
     if (forced >= 0) return forced == 1;
     return P->geom.fused[sizeof(T) == 4 ? 1 : 0] != 0;
 }
@@ -657,7 +716,7 @@ void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
         if (zero) {
             // d = c2 M^{-1} b, y = d; the next step's residual is b - A d
             launch_bj_apply<T>(N, int(ne), b, dA, y, em, ci, cs, ui, einv0, T(0), T(1.0 / ch.theta),
-                               true, s);
+                               true, s, bj_hi());
         } else {
             launch_cheb_elem<T>(N, P->geom, y, b, r, eta, em, ci, cs, ui, einv0, nullptr, dA, nullptr,
                                 T(0), T(1.0 / ch.theta), false, s);
@@ -684,13 +743,13 @@ void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
     const T* einv = eta_inv_of<T>(P);
     launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
                        cls_sym.as<int>(), uniq_inv.template as<T>(), einv,
-                       T(0), T(1.0 / ch.theta), zero, s);
+                       T(0), T(1.0 / ch.theta), zero, s, bj_hi());
     for (int st = 1; st < P->desc.cheb_steps_p; ++st) {
         launch_apply_sip<T>(N, P->geom, dd, r, eta, T(-1), r, T(1), s);  // r -= A d
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
         launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
                            cls_sym.as<int>(), uniq_inv.template as<T>(),
-                           einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s);
+                           einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s, bj_hi());
         rho = rn;
     }
 }
@@ -784,8 +843,7 @@ void Multigrid<T>::vcycle_on(const T* b, T* y, cudaStream_t s) {
         return;
     }
     // r1 = R (b - A y)
-    if (!use_fused() ||
-        !launch_residual_restrict_elem<T>(N, P->geom, y, b, eta_of<T>(P), r1.template as<T>(), s)) {
+    if (!residual_restrict(y, b, r1.template as<T>(), s)) {
         launch_apply_sip<T>(N, P->geom, y, pr.template as<T>(), eta_of<T>(P), T(-1), b, T(1), s);
         launch_p_restrict<T>(ne, N, pr.template as<T>(), r1.template as<T>(), s);
     }
@@ -1023,8 +1081,11 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                         : P->mg64->inner_pcg(W.tu.as<double>(), z, o.inner_rtol, o.max_inner, s,
                                              nullptr);
         } else {
-            its = inner_pcg_graph(P, W, mixed, flexible, o.inner_norm == 1, W.tu.as<double>(), z,
-                                  o.inner_rtol, o.max_inner, s, gcr_restart);
+            bool batched = false;
+            its = batched_inner(P, W.tu.as<double>(), z, s, &batched);
+            if (!batched)
+                its = inner_pcg_graph(P, W, mixed, flexible, o.inner_norm == 1, W.tu.as<double>(),
+                                      z, o.inner_rtol, o.max_inner, s, gcr_restart);
         }
         inner_total += its;
         inner_max = std::max(inner_max, its);
@@ -1067,9 +1128,11 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         double* sq = sc + restart + 1;     // ||q_j||^2
         double* sa = sc + restart + 2;     // <r, q_j>
         double* sone = sc + restart + 3;   // 1.0
+        double* sq0 = sc + restart + 4;    // ||K z_j||^2 before the projections
         static const double one = 1.0;
         SIP_CUDA(cudaMemcpyAsync(sone, &one, sizeof(double), cudaMemcpyHostToDevice, s));
         bool broke = false;
+        sip_status stop_st = SIP_OK;
         for (;;) {
             applyK(x, r);
             launch_axpby<double>(n, 1.0, b, -1.0, r, s);
@@ -1088,6 +1151,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                 st = SIP_ERR_BREAKDOWN;
                 break;
             }
+            if (stop_st != SIP_OK) {
+                st = stop_st;
+                break;
+            }
             if (total >= o.max_outer || stagnated(rn)) break;
             int j = 0;
             recur_conv = false;
@@ -1098,6 +1165,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                 precond(r, zj);
                 applyK(zj, qj);
                 project(qj);
+                launch_dot<double>(n, qj, qj, sq0, wsd, s);
                 if (j > 0) {
                     for (int pass = 0; pass < 2; ++pass) {
                         launch_mdot<double>(j, n, V, n, qj, sc, wsd, s);
@@ -1106,13 +1174,22 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                     }
                 }
                 launch_dot<double>(n, qj, qj, sq, wsd, s);
+                // a direction with K z_j in the span of the stored q_i (or
+                // K z_j = 0) cannot be normalised: stop with the iterate so far
+                SIP_CUDA(cudaMemcpyAsync(hp, sq, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                SIP_CUDA(cudaStreamSynchronize(s));
+                const double qq = hp[0], qq0 = hp[sq0 - sq];
+                if (!(qq > 1e-28 * qq0) || !std::isfinite(qq)) {
+                    broke = true;
+                    break;
+                }
                 launch_scale_inv_sqrt<double>(n, sq, qj, s);
                 launch_scale_inv_sqrt<double>(n, sq, zj, s);
                 launch_dot<double>(n, r, qj, sa, wsd, s);
                 launch_pcg_update<double>(n, zj, qj, x, r, sa, sone, s);
                 ++total;
                 ++j;
-                const double rr = norm(r);   // non-finite after a breakdown (q_j = 0)
+                const double rr = norm(r);
                 if (!std::isfinite(rr)) {
                     broke = true;
                     break;
@@ -1121,6 +1198,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                     recur_conv = true;
                     break;
                 }
+                stop_st = stop_requested();
+                if (stop_st != SIP_OK) break;
             }
         }
     }
@@ -1136,6 +1215,7 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         gv[0] = beta;
         int j = 0, jdone = 0;
         bool broke = false;
+        sip_status stop_st = SIP_OK;
         recur_conv = false;
         for (j = 0; j < restart && total < o.max_outer; ++j) {
             double* vj = V + size_t(j) * n;
@@ -1180,6 +1260,8 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
                 recur_conv = true;
                 break;
             }
+            stop_st = stop_requested();
+            if (stop_st != SIP_OK) break;
         }
         if (jdone > 0) {
             std::vector<double> yk(jdone);
@@ -1208,6 +1290,10 @@ sip_status run_solve(sip_problem* P, const double* f_u, const double* g_p, doubl
         }
         if (broke) {
             st = SIP_ERR_BREAKDOWN;
+            break;
+        }
+        if (stop_st != SIP_OK) {
+            st = stop_st;
             break;
         }
         // the recurrence may report convergence while the true residual does

@@ -9,13 +9,11 @@
 //    stencils;
 //  - a dense symmetric matrix-vector product for the coarsest-level inverse.
 #include "sip_internal.h"
+#include "sip_level.cuh"
 
 namespace sip {
 
 namespace {
-
-constexpr double kInvSqrt2 = 0.70710678118654752440;   // int L_p l_0 for the two end hats
-constexpr double kInvSqrt6 = 0.40824829046386301637;   // |int L_p l_1|
 
 // p-transfers to the coarse space of the M x M lowest modes per component
 // (M = 2: Q^2_1, M = 1: Q^2_0), coarse layout [e][c][j][i] with i, j < M.
@@ -41,12 +39,6 @@ __global__ void k_p_prolong_add(size_t ne, int N, int M, const T* __restrict__ e
     const size_t e = g / per;
     const int l = int(g % per), c = l / (M * M), j = (l / M) % M, i = l % M;
     y[e * 2 * N * N + c * N * N + j * N + i] += e1[g];
-}
-
-// weight of corner p (0 = low end, 1 = high end) on mode i of the 1D
-// orthonormal basis: int L_p l_i over [-1, 1] with L_0 = (1-xi)/2, L_1 = (1+xi)/2
-__device__ __forceinline__ double hatw(int i, int p) {
-    return i == 0 ? kInvSqrt2 : (p == 0 ? -kInvSqrt6 : kInvSqrt6);
 }
 
 template <typename T>
@@ -87,45 +79,6 @@ __global__ void k_rdc(int nx, int ny, const T* __restrict__ r, T* __restrict__ o
         }
     }
     out[g] = T(acc);
-}
-
-// Two consecutive values; one 2-word vector load when VEC (the launcher has
-// checked that every such pair is 2-word aligned).
-template <typename T, bool VEC>
-__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
-    if constexpr (VEC && sizeof(T) == 8) {
-        const double2 v = *reinterpret_cast<const double2*>(p);
-        a = v.x;
-        b = v.y;
-    } else if constexpr (VEC) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
-        a = v.x;
-        b = v.y;
-    } else {
-        a = p[0];
-        b = p[1];
-    }
-}
-
-// Row c of vertex (vx, vy) of the 9-point 2x2-block stencil times x.
-template <typename T, bool VEC>
-__device__ __forceinline__ T stencil_row(int nvx, int nvy, int vx, int vy, int c, const T* sv,
-                                         const T* __restrict__ x) {
-    T acc = T(0);
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int wy = vy + dy;
-        if (wy < 0 || wy >= nvy) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int wx = vx + dx;
-            if (wx < 0 || wx >= nvx) continue;
-            const int t = (dy + 1) * 3 + (dx + 1);
-            T s0, s1, x0, x1;
-            ld2<T, VEC>(sv + t * 4 + c * 2, s0, s1);
-            ld2<T, VEC>(x + 2 * (size_t(wy) * nvx + wx), x0, x1);
-            acc += s0 * x0 + s1 * x1;
-        }
-    }
-    return acc;
 }
 
 template <typename T>

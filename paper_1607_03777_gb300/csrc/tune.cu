@@ -3,7 +3,9 @@
 // everywhere: the component-split apply (two threads per element) hides the
 // narrow FP64 pipe's latency on small meshes, the one-thread-per-element
 // apply issues fewer loads on large ones, the shared-memory tile kernel
-// covers every degree.  So each problem times the candidates on its own mesh
+// covers every degree, and the staged-tile kernel (element blocks copied
+// through shared memory with coalesced 16-byte accesses, 2 or 4 tile rows)
+// suits the memory-bound FP32 operator.  So each problem times the candidates on its own mesh
 // the first time it is set up and keeps the fastest:
 //   * the apply kernel, per precision the problem runs in;
 //   * the p-level smoother step: one fused launch (apply + block-Jacobi +
@@ -86,8 +88,13 @@ double time_ms(F&& f, cudaStream_t s, int reps) {
 template <typename T>
 void tune_apply_t(sip_problem* P, cudaStream_t s) {
     const int t = sizeof(T) == 4 ? 1 : 0;
+    if (P->pin_apply[t] > 0) {   // pinned: code 5 = staged with 4 tile rows
+        P->geom.variant[t] = P->pin_apply[t] == 5 ? int(APPLY_STAGE) : P->pin_apply[t];
+        P->geom.stage_rows[t] = P->pin_apply[t] == 5 ? 4 : 2;
+        return;
+    }
     const Key key{0, P->n, int(sizeof(T)), P->desc.nx, P->desc.ny};
-    int best = APPLY_AUTO;
+    int best = APPLY_AUTO;   // variant + 16 x stage rows
     if (!cached(key, best)) {
         const size_t n_u = size_t(P->n_u);
         DeviceBuffer x, y;
@@ -97,8 +104,11 @@ void tune_apply_t(sip_problem* P, cudaStream_t s) {
         const T* eta = eta_vec<T>(P);
         double tbest = 1e300;
         const int64_t launches = launch_counter();
-        for (int v : {int(APPLY_ELEM2), int(APPLY_ELEM1), int(APPLY_TILE)}) {
-            P->geom.variant[t] = v;
+        const int saved_rows = P->geom.stage_rows[t];
+        for (int cand : {int(APPLY_ELEM2), int(APPLY_ELEM1), int(APPLY_TILE),
+                         int(APPLY_STAGE) + 16 * 2, int(APPLY_STAGE) + 16 * 4}) {
+            P->geom.variant[t] = cand % 16;
+            P->geom.stage_rows[t] = cand / 16 ? cand / 16 : saved_rows;
             const double ms = time_ms(
                 [&] {
                     launch_apply_sip<T>(P->n, P->geom, x.as<T>(), y.as<T>(), eta, T(1), nullptr,
@@ -107,19 +117,29 @@ void tune_apply_t(sip_problem* P, cudaStream_t s) {
                 s, 5);
             if (ms < tbest) {
                 tbest = ms;
-                best = v;
+                best = cand;
             }
         }
+        P->geom.stage_rows[t] = saved_rows;
         launch_counter() = launches;
         store(key, best);
     }
-    P->geom.variant[t] = best;
+    P->geom.variant[t] = best % 16;
+    if (best / 16) P->geom.stage_rows[t] = best / 16;
 }
 
 }  // namespace
 
 void tune_apply(sip_problem* P, cudaStream_t s) {
-    if (!autotune_on() || P->n > 6) return;   // one kernel exists above degree 5
+    if (P->n > 6) return;   // one kernel exists above degree 5
+    if (!autotune_on()) {
+        for (int t = 0; t < 2; ++t)
+            if (P->pin_apply[t] > 0) {
+                P->geom.variant[t] = P->pin_apply[t] == 5 ? int(APPLY_STAGE) : P->pin_apply[t];
+                P->geom.stage_rows[t] = P->pin_apply[t] == 5 ? 4 : 2;
+            }
+        return;
+    }
     tune_apply_t<double>(P, s);
     if (P->desc.precision != SIP_PREC_FP64) tune_apply_t<float>(P, s);
 }
@@ -127,6 +147,10 @@ void tune_apply(sip_problem* P, cudaStream_t s) {
 template <typename T>
 void Multigrid<T>::tune_smoother(cudaStream_t s) {
     const int t = sizeof(T) == 4 ? 1 : 0;
+    if (P->pin_fused[t] >= 0) {
+        P->geom.fused[t] = P->pin_fused[t];
+        return;
+    }
     if (!autotune_on() || !cheb_elem_available(N) || !pd2.ptr) return;
     const Key key{1, N, int(sizeof(T)), P->desc.nx, P->desc.ny};
     int fused = 1;

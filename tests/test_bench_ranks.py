@@ -46,8 +46,9 @@ def test_single_rank_identity():
 
 def test_reference_arm_line_contract(monkeypatch):
     """The reference arm (the oracle on the host cores) prints the contract's
-    keys on the same workload configuration as the GPU arm, with its own
-    cpu_baseline and a copy-free e2e."""
+    keys; its config is the GPU arm's physics and solver settings on the
+    smaller mesh it actually timed (named as a sample of the GPU arm's
+    workload), with its own cpu_baseline and a copy-free e2e."""
     import sys
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1",
                                       "--warmup", "0"])
@@ -59,7 +60,11 @@ def test_reference_arm_line_contract(monkeypatch):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     cfg = dict(line["config"])
-    cfg.pop("step")
-    assert cfg == bench.headline_config(args)
+    head = bench.headline_config(args)
+    assert cfg["sample_of"] == head["workload"]
+    assert (cfg["nx"], cfg["ny"]) == (bench.ORACLE_SIZES[0],) * 2
+    assert 1000.0 / line["ms_per_step"] == pytest.approx(line["value"])
+    for key in ("k", "n_hlevels", "rtol", "inner_rtol", "inner_norm", "inner_krylov", "precision"):
+        assert cfg[key] == head[key], key
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0

@@ -1,0 +1,165 @@
+"""GPU parity of the staged-tile SIP apply and of the split-precision FP32
+operator, and the mixed-precision V-cycle and solve at viscosity contrast
+1e6 (small discs as in the many-disc workload, scaled down), against the
+FP64 oracle, through the C ABI.
+
+In FP32 arithmetic the operator applied to a nearly rigid motion of a stiff
+inclusion cancels to rounding noise eps_32 eta |u|; the mixed form evaluates
+the tiles near stiff elements in FP64 arithmetic on the FP32 data
+(sip_problem_desc.mixed_fp64_ratio).  The tests below show the cancellation
+(ratio 0) and its cure (default ratio) on the same inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov, materials, multigrid, sip
+from paper_1607_03777_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+SINK = synth.SINKER_BC
+BCS = [("navier",) * 4, SINK, ("dirichlet",) * 4, ("neumann", "dirichlet", "navier", "neumann")]
+TOL64, TOL32 = 1e-10, 1e-5
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def errs(got, ref):
+    d = got - ref
+    return np.linalg.norm(d) / np.linalg.norm(ref), np.abs(d).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("code", [4, 5])   # staged tile, 2 / 4 tile rows
+@pytest.mark.parametrize("mesh", [(1, 1), (3, 2), (37, 3), (4, 35), (33, 9)])
+def test_apply_A_staged(ctx, k, code, mesh):
+    """Both precisions of the staged kernel against the assembled operator,
+    element by element, on ragged tiles (tile rows and columns cut by the
+    mesh edge) and every boundary kind."""
+    nx, ny = mesh
+    for i, bc in enumerate(BCS):
+        eta = synth.random_eta(nx * ny, 900 + 10 * k + i, (0.0, 3.0))
+        prob = api.Problem(ctx, nx, ny, k, eta, bc=bc, lx=1.0, ly=0.7)
+        prob.set_schedule(apply=[code, code])
+        assert prob.schedule()["apply"] == [code, code]
+        A = sip.assemble_A(sip.Problem(nx, ny, k, eta, bc=bc, lx=1.0, ly=0.7))
+        x = synth.random_vector(prob.n_u, seed=70 + i)
+        y = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        prob.apply_A(dev(x), y)
+        e2, emax = errs(host(y), A @ x)
+        assert e2 < TOL64 and emax < TOL64, (bc, e2, emax)
+        x32 = x.astype(np.float32)
+        y32 = torch.empty(prob.n_u, dtype=torch.float32, device="cuda")
+        prob.apply_A_f32(dev(x32, torch.float32), y32)
+        e2, emax = errs(host(y32), A @ x32.astype(np.float64))
+        assert e2 < TOL32 and emax < 2 * TOL32, (bc, e2, emax)
+
+
+def high_contrast(n, k, seed=3):
+    """64 discs of radius 0.02 with log10 eta ~ U[0, 6] (the many-disc
+    workload's fields) on an n x n mesh."""
+    wl = synth.many_discs(n=n, k=k, n_hlevels=synth.levels_to_17(n), seed=seed)
+    eta, rho = materials.rasterise_inclusions(n, n, wl.shapes)
+    return wl, eta, rho
+
+
+def rigid_rotation(ref, seed):
+    """The rigid rotation u = (-(y - 1/2), x - 1/2) of the unit square in the
+    modal basis, plus a perturbation of relative size 1e-6.  Its strain
+    vanishes, so inside every inclusion A x is the cancellation of terms of
+    size eta_K |grad u|; the exact result is carried by the boundary faces."""
+    n = ref.k + 1
+    nx, ny = ref.nx, ref.ny
+    h = 1.0 / nx
+    x = np.zeros((ny, nx, 2, n, n))
+    xc = (np.arange(nx) + 0.5) * h
+    yc = (np.arange(ny) + 0.5) * h
+    # u = a + b zeta on the reference square: c_00 = 2 a, c_(j=1) = 2 b / sqrt(3)
+    x[:, :, 0, 0, 0] = -2.0 * (yc[:, None] - 0.5)
+    x[:, :, 0, 1, 0] = -2.0 * (h / 2) / np.sqrt(3.0)
+    x[:, :, 1, 0, 0] = 2.0 * (xc[None, :] - 0.5)
+    x[:, :, 1, 0, 1] = 2.0 * (h / 2) / np.sqrt(3.0)
+    x = x.ravel()
+    return x + 1e-6 * synth.random_vector(x.size, seed)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_apply_A_f32_split_precision(ctx, k):
+    """With the default ratio the FP32 operator of a mixed problem matches
+    the FP64 operator applied to the same FP32 data to 1e-5 even where the
+    result is a cancellation in 1e6-viscosity discs (a rigid rotation); with
+    FP32 arithmetic everywhere (ratio 0) the cancellation error is orders of
+    magnitude larger."""
+    n = 40
+    wl, eta, _ = high_contrast(n, k)
+    ref = sip.Problem(n, n, k, eta, bc=wl.bc)
+    A = sip.assemble_A(ref)
+    x32 = rigid_rotation(ref, 5).astype(np.float32)
+    yref = A @ x32.astype(np.float64)
+    out = {}
+    for ratio in (1e3, 0.0):
+        prob = api.Problem(ctx, n, n, k, eta, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
+                           precision="mixed", mixed_fp64_ratio=ratio)
+        prob.setup()
+        y = torch.empty(prob.n_u, dtype=torch.float32, device="cuda")
+        prob.apply_A_f32(dev(x32, torch.float32), y)
+        out[ratio] = errs(host(y), yref)
+        if ratio > 0:
+            assert prob.schedule()["apply"][1] == 4
+    e2, emax = out[1e3]
+    assert e2 < TOL32 and emax < 1e-4, out
+    assert out[0.0][0] > 100 * e2, out     # the cancellation that the split removes
+
+
+def test_vcycle_f32_high_contrast(ctx):
+    """The mixed V-cycle (FP32 data, split-precision operator, FP64 sums of
+    the ill-conditioned element blocks) against the oracle's FP64 V-cycle at
+    contrast 1e6, in the energy norm of A, on the load vector of the disc
+    field.  (One application does not show the failure of FP32 arithmetic
+    everywhere, which appears over the Krylov iterations: see the solve
+    test below.)"""
+    n, k = 32, 3
+    wl, eta, rho = high_contrast(n, k)
+    ref = sip.Problem(n, n, k, eta, bc=wl.bc)
+    A = sip.assemble_A(ref)
+    mg = multigrid.HPMultigrid(ref, A, wl.n_hlevels, seed=1)
+    f = sip.rhs_body_force(ref, rho)
+    z_ref = mg(f)
+    nz = np.sqrt(z_ref @ (A @ z_ref))
+    prob = api.Problem(ctx, n, n, k, eta, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
+                       precision="mixed")
+    z = torch.empty(prob.n_u, dtype=torch.float32, device="cuda")
+    prob.vcycle_f32(dev(f, torch.float32), z)
+    d = host(z) - z_ref
+    assert np.sqrt(d @ (A @ d)) / nz < 1e-2
+
+
+def test_solve_mixed_high_contrast(ctx):
+    """Scaled many-disc problem at contrast 1e6 (32^2, k = 3): the mixed and
+    the FP64 forms, both with the double-double refinement, reach 1e-8; the
+    oracle's FP64 residual of either result sits at the FP64 floor of this
+    field.  (The velocity itself is not compared: at this contrast the
+    1e-8 residual leaves it determined only to the condition number.)"""
+    n, k = 32, 3
+    wl, eta, rho = high_contrast(n, k)
+    ref = sip.Problem(n, n, k, eta, bc=wl.bc)
+    f = sip.rhs_body_force(ref, rho)
+    A, B = sip.assemble_A(ref), sip.assemble_B(ref)
+    K = krylov.stokes_matrix(A, B).tocsr()
+    b = np.concatenate([f, np.zeros(B.shape[1])])
+    for precision in ("fp64", "mixed"):
+        prob = api.Problem(ctx, n, n, k, eta, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
+                           precision=precision)
+        u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(prob.n_p, dtype=torch.float64, device="cuda")
+        rep = prob.solve(dev(f), u, p, rtol=1e-8, max_outer=1000, refine=4)
+        assert rep["status"] == 0 and rep["rel_residual"] <= 1e-8, (precision, rep)
+        x = np.concatenate([host(u), host(p)])
+        assert np.linalg.norm(b - K @ x) / np.linalg.norm(b) < 1e-7, precision

@@ -41,11 +41,13 @@ def test_noalloc_matches_allocating_entry_point_twice(ctx):
         (96, 80, np.concatenate([synth.random_discs(64, 0.02, (0.0, 6.0), seed=3),
                                  np.stack([synth.box(0.25, 0.75, 0.25, 0.75, 1e4, 1.2)])])),
         (33, 47, synth.random_discs(7, 0.09, (1.0, 3.0), seed=11)),   # fewer records than before
+        (5, 3, np.zeros((0, 7))),     # no record at all: the stale ones must not be read
     ]
     for nx, ny, shapes in cases:
-        st, eta, rho = _noalloc(ctx, nx, ny, shapes)
+        bg = (2.0, 0.5) if len(shapes) == 0 else (1.0, 1.0)
+        st, eta, rho = _noalloc(ctx, nx, ny, shapes, *bg)
         assert st == _lib.SIP_OK, ctx.lib.sip_last_error(ctx.handle).decode()
-        eta_ref, rho_ref = ctx.rasterise_inclusions(nx, ny, shapes)
+        eta_ref, rho_ref = ctx.rasterise_inclusions(nx, ny, shapes, eta_bg=bg[0], rho_bg=bg[1])
         torch.cuda.synchronize()
         assert torch.equal(eta, eta_ref)
         assert torch.equal(rho, rho_ref)
