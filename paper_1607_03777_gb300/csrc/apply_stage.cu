@@ -82,8 +82,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TS, TC>& a, int ex0, 
 #pragma unroll 1
     for (int q0 = 0; q0 < QT; q0 += BATCH * L::NT) {
         TS v[BATCH][V];
-        long long gfirst[BATCH], glo[BATCH], ghi[BATCH], gbase[BATCH];
-        int srow[BATCH];
+        // per chunk: its first entry and the staged row's valid range, as
+        // offsets from the row's stage origin (element ex0 - 1): 32-bit
+        int rel0[BATCH], rlo[BATCH], rhi[BATCH], srow[BATCH];
         bool ok[BATCH];
 #pragma unroll
         for (int b = 0; b < BATCH; ++b) {
@@ -91,44 +92,46 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TS, TC>& a, int ex0, 
             const int r = q / CPR, c = q % CPR;
             const int ey = ey0 - 1 + r;
             ok[b] = false;
-            gfirst[b] = glo[b] = ghi[b] = gbase[b] = 0;
-            srow[b] = 0;
+            rel0[b] = rlo[b] = rhi[b] = srow[b] = 0;
+            long long gfirst = 0;
             if (q < QT && ey >= 0 && ey < ny) {
                 const bool edge = r == 0 || r == L::XH - 1;
                 const int elo = edge ? ex0 : max(ex0 - 1, 0);
                 const int ehi = edge ? min(ex0 + STX, nx) : min(ex0 + STX + 1, nx);
                 const long long row = (long long)ey * nx;
-                glo[b] = (row + elo) * NB;
-                ghi[b] = (row + ehi) * NB;
-                gbase[b] = (row + ex0 - 1) * NB;
-                gfirst[b] = (glo[b] / V + c) * V;
+                const long long gbase = (row + ex0 - 1) * NB;
+                const long long glo = (row + elo) * NB;
+                gfirst = (glo / V + c) * V;
+                rel0[b] = int(gfirst - gbase);
+                rlo[b] = (elo - (ex0 - 1)) * NB;
+                rhi[b] = (ehi - (ex0 - 1)) * NB;
                 srow[b] = r;
-                ok[b] = elo < ehi && gfirst[b] < ghi[b];
+                ok[b] = elo < ehi && rel0[b] < rhi[b];
             }
             if (!ok[b]) continue;
             if constexpr (VEC) {
-                if (gfirst[b] + V <= a.n_total) {
+                if (gfirst + V <= a.n_total) {
                     using VV = Vec16<TS>;
                     const typename VV::type w =
-                        __ldg(reinterpret_cast<const typename VV::type*>(a.x + gfirst[b]));
+                        __ldg(reinterpret_cast<const typename VV::type*>(a.x + gfirst));
 #pragma unroll
                     for (int t = 0; t < V; ++t) v[b][t] = VV::get(w, t);
                     continue;
                 }
             }
 #pragma unroll
-            for (int t = 0; t < V; ++t)
-                v[b][t] = gfirst[b] + t < a.n_total ? a.x[gfirst[b] + t] : TS(0);
+            for (int t = 0; t < V; ++t) v[b][t] = gfirst + t < a.n_total ? a.x[gfirst + t] : TS(0);
         }
 #pragma unroll
         for (int b = 0; b < BATCH; ++b) {
             if (!ok[b]) continue;
+            TS* row = sx + srow[b] * L::XW * L::XS;
 #pragma unroll
             for (int t = 0; t < V; ++t) {
-                const long long g = gfirst[b] + t;
-                if (g >= glo[b] && g < ghi[b]) {
-                    const int rel = int(g - gbase[b]);
-                    sx[(srow[b] * L::XW + rel / NB) * L::XS + rel % NB] = v[b][t];
+                const int rel = rel0[b] + t;
+                if (rel >= rlo[b] && rel < rhi[b]) {
+                    const int el = rel / NB;   // rel >= 0 here
+                    row[el * L::XS + (rel - el * NB)] = v[b][t];
                 }
             }
         }
@@ -249,11 +252,13 @@ __device__ __forceinline__ void stage_store(const StageArgs<TS, TC>& a, int ex0,
         const int ey = ey0 + r;
         if (ey >= ny) continue;
         const long long g0 = ((long long)ey * nx + ex0) * NB;
-        const long long g1 = ((long long)ey * nx + ehi) * NB;
+        const int span = (ehi - ex0) * NB;            // entries of this tile row
         const long long gf = (g0 / V + c) * V;
-        if (gf >= g1) continue;
+        const int rel0 = int(gf - g0);                 // may be negative (before the span)
+        if (rel0 >= span) continue;
+        const TC* srow = sy + r * STX * L::XS;
         if constexpr (VEC) {
-            if (gf >= g0 && gf + V <= g1) {
+            if (rel0 >= 0 && rel0 + V <= span) {
                 using VV = Vec16<TS>;
                 TS w[V];
                 if (a.z) {
@@ -261,15 +266,15 @@ __device__ __forceinline__ void stage_store(const StageArgs<TS, TC>& a, int ex0,
                         __ldg(reinterpret_cast<const typename VV::type*>(a.z + gf));
 #pragma unroll
                     for (int t = 0; t < V; ++t) {
-                        const int rel = int(gf + t - g0);
-                        w[t] = TS(alpha * sy[(r * STX + rel / NB) * L::XS + rel % NB] +
+                        const int rel = rel0 + t, el = rel / NB;
+                        w[t] = TS(alpha * srow[el * L::XS + (rel - el * NB)] +
                                   beta * TC(VV::get(zv, t)));
                     }
                 } else {
 #pragma unroll
                     for (int t = 0; t < V; ++t) {
-                        const int rel = int(gf + t - g0);
-                        w[t] = TS(alpha * sy[(r * STX + rel / NB) * L::XS + rel % NB]);
+                        const int rel = rel0 + t, el = rel / NB;
+                        w[t] = TS(alpha * srow[el * L::XS + (rel - el * NB)]);
                     }
                 }
                 *reinterpret_cast<typename VV::type*>(a.y + gf) = VV::make(w);
@@ -278,12 +283,12 @@ __device__ __forceinline__ void stage_store(const StageArgs<TS, TC>& a, int ex0,
         }
 #pragma unroll
         for (int t = 0; t < V; ++t) {
-            const long long g = gf + t;
-            if (g < g0 || g >= g1) continue;
-            const int rel = int(g - g0);
-            TC w = alpha * sy[(r * STX + rel / NB) * L::XS + rel % NB];
-            if (a.z) w += beta * TC(a.z[g]);
-            a.y[g] = TS(w);
+            const int rel = rel0 + t;
+            if (rel < 0 || rel >= span) continue;
+            const int el = rel / NB;
+            TC w = alpha * srow[el * L::XS + (rel - el * NB)];
+            if (a.z) w += beta * TC(a.z[gf + t]);
+            a.y[gf + t] = TS(w);
         }
     }
 }

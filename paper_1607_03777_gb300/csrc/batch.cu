@@ -821,6 +821,7 @@ void BatchEngine<T>::build(cudaStream_t s) {
                 a.uniq_inv = G.uniq_inv.template as<T>();
                 a.eta_inv = eta_inv;
                 a.uniq_hi = G.bj_hi();
+                a.uniq_inv64 = G.bj_inv64();
                 a.c1 = T(c1[st]);
                 a.c2 = T(c2[st]);
                 a.x_zero = k == 0 ? 1 : 0;

@@ -14,11 +14,12 @@ void launch_classify(int nx, int ny, const double* eta, int* emap, int* uniq_lis
 template <typename T>
 void launch_build_blocks(int N, const OpGeom& g, const int* spec, int count, const double* eta,
                          T* out, cudaStream_t s);
-// uniq_hi (may be null): unique blocks applied with FP64 accumulation
+// uniq_hi (may be null): unique blocks applied in FP64 from uniq_inv64
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                      const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                     cudaStream_t s, const unsigned char* uniq_hi = nullptr);
+                     cudaStream_t s, const unsigned char* uniq_hi = nullptr,
+                     const double* uniq_inv64 = nullptr);
 // Block-Jacobi apply arguments of one element set (one member of a batch).
 template <typename T>
 struct BJBatchArgs {
@@ -32,6 +33,7 @@ struct BJBatchArgs {
     const T* uniq_inv;
     const T* eta_inv;
     const unsigned char* uniq_hi;
+    const double* uniq_inv64;   // FP64 inverses of the unique blocks (flagged ones read)
     T c1, c2;
     int x_zero;
 };
@@ -149,8 +151,11 @@ struct Multigrid {
     // FP32 operator only: split-precision tiles (flags per tile, their list)
     DeviceBuffer hi_flag, hi_list, hi_scr;
     int n_hi = 0;
-    DeviceBuffer uniq_hi;   // unique blocks applied with FP64 accumulation (FP32 only)
+    // unique blocks whose face neighbour is much stiffer: applied in FP64 from
+    // FP64 inverses (FP32 operator only)
+    DeviceBuffer uniq_hi, uniq_inv64;
     const unsigned char* bj_hi() const { return n_hi > 0 ? uniq_hi.as<unsigned char>() : nullptr; }
+    const double* bj_inv64() const { return n_hi > 0 ? uniq_inv64.as<double>() : nullptr; }
     // set-up scratch, kept so that a repeated set-up allocates nothing
     DeviceBuffer scr_V, scr_tmp, scr_b, scr_spec, scr_L, scr_X, scr_Y, scr_xv, scr_t1, scr_t2;
     std::vector<DeviceBuffer> scr_S64;

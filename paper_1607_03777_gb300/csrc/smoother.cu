@@ -173,7 +173,10 @@ __global__ void k_classify(int nx, int ny, const double* eta, int* emap, int* un
 // out = c2 * M_K^{-1} r_K (+ c1 * out_old); if x: x = (x_zero ? 0 : x) + out.
 // EB elements per CTA, the residual blocks staged in shared memory; thread
 // (element, row r) reads column r of the symmetric inverse (coalesced).
-// Unique blocks flagged in uniq_hi (may be null) accumulate in FP64.
+// Unique blocks flagged in uniq_hi (may be null) are applied in FP64 from
+// their FP64 inverses (uniq_inv64): rounding an ill-conditioned inverse to
+// FP32, or summing its products in FP32, loses the small components of the
+// result.
 template <int N, typename T>
 __device__ __forceinline__ void bj_body(int e0, const BJBatchArgs<T>& a) {
     constexpr int NB = 2 * N * N;
@@ -182,7 +185,8 @@ __device__ __forceinline__ void bj_body(int e0, const BJBatchArgs<T>& a) {
     __shared__ T sr[EB * NB];
     __shared__ const T* s_minv[EB];
     __shared__ T s_scale[EB];
-    __shared__ int s_sym[EB];   // symmetry type; -1: dense with FP64 accumulation
+    __shared__ int s_sym[EB];   // symmetry type; -1: dense, FP64 inverse
+    __shared__ const double* s_m64[EB];
     const int ne = a.ne;
     const int cnt = min(EB, ne - e0) * NB;
     // every load that does not depend on another is issued before the
@@ -202,7 +206,9 @@ __device__ __forceinline__ void bj_body(int e0, const BJBatchArgs<T>& a) {
         } else {
             s_minv[q] = a.uniq_inv + size_t(m) * NB * NB;
             s_scale[q] = T(1);
-            s_sym[q] = (a.uniq_hi && a.uniq_hi[m]) ? -1 : 0;
+            const bool hi = a.uniq_hi && a.uniq_hi[m] && a.uniq_inv64;
+            s_sym[q] = hi ? -1 : 0;
+            s_m64[q] = hi ? a.uniq_inv64 + size_t(m) * NB * NB : nullptr;
         }
     }
     const T c1 = a.c1, c2 = a.c2;
@@ -213,10 +219,16 @@ __device__ __forceinline__ void bj_body(int e0, const BJBatchArgs<T>& a) {
     const int el = q / NB, row = q % NB;
     T acc;
     if constexpr (sizeof(T) == 4) {
-        if (s_sym[el] < 0)
-            acc = T(block_row_apply<N, T, double>(s_minv[el], sr + el * NB, row, 0));
-        else
+        if (s_sym[el] < 0) {
+            const double* M = s_m64[el];
+            const T* rr = sr + el * NB;
+            double a64 = 0.0;
+#pragma unroll 8
+            for (int q2 = 0; q2 < NB; ++q2) a64 += M[q2 * NB + row] * double(rr[q2]);
+            acc = T(a64);
+        } else {
             acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el]);
+        }
     } else {
         acc = block_row_apply<N, T>(s_minv[el], sr + el * NB, row, s_sym[el] < 0 ? 0 : s_sym[el]);
     }
@@ -280,12 +292,12 @@ void build_blocks_n(const OpGeom& g, const int* spec, int count, const double* e
 template <int N, typename T>
 void bj_apply_n(int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                 const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                const unsigned char* uniq_hi, cudaStream_t s) {
+                const unsigned char* uniq_hi, const double* uniq_inv64, cudaStream_t s) {
     constexpr int NB = 2 * N * N;
     constexpr int EB = (256 / NB) > 0 ? (256 / NB) : 1;
     const int blocks = (ne + EB - 1) / EB;
     const BJBatchArgs<T> a{ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, uniq_hi,
-                           c1, c2, x_zero ? 1 : 0};
+                           uniq_inv64, c1, c2, x_zero ? 1 : 0};
     launch_k(k_bj_apply<N, T>, blocks, 256, 0, s, a);
     SIP_CHECK_LAUNCH();
 }
@@ -327,23 +339,25 @@ template void launch_build_blocks<float>(int, const OpGeom&, const int*, int, co
 template <typename T>
 void launch_bj_apply(int N, int ne, const T* r, T* out, T* x, const int* emap, const T* cls_inv,
                      const int* cls_sym, const T* uniq_inv, const T* eta, T c1, T c2, bool x_zero,
-                     cudaStream_t s, const unsigned char* uniq_hi) {
+                     cudaStream_t s, const unsigned char* uniq_hi, const double* uniq_inv64) {
     switch (N) {
-        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
-        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
-        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
-        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
-        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
-        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, s); break;
+        case 2: bj_apply_n<2, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
+        case 3: bj_apply_n<3, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
+        case 4: bj_apply_n<4, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
+        case 5: bj_apply_n<5, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
+        case 6: bj_apply_n<6, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
+        case 7: bj_apply_n<7, T>(ne, r, out, x, emap, cls_inv, cls_sym, uniq_inv, eta, c1, c2, x_zero, uniq_hi, uniq_inv64, s); break;
         default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
     }
 }
 template void launch_bj_apply<double>(int, int, const double*, double*, double*, const int*,
                                       const double*, const int*, const double*, const double*,
-                                      double, double, bool, cudaStream_t, const unsigned char*);
+                                      double, double, bool, cudaStream_t, const unsigned char*,
+                                      const double*);
 template void launch_bj_apply<float>(int, int, const float*, float*, float*, const int*,
                                      const float*, const int*, const float*, const float*, float,
-                                     float, bool, cudaStream_t, const unsigned char*);
+                                     float, bool, cudaStream_t, const unsigned char*,
+                                     const double*);
 
 int bj_group(int N) {
     const int nb = 2 * N * N;

@@ -256,7 +256,8 @@ Multigrid<T>::~Multigrid() {
 
 template <typename T>
 int64_t Multigrid<T>::bytes() const {
-    int64_t b = int64_t(emap.bytes + uniq_list.bytes + n_uniq_d.bytes + cls_inv.bytes +
+    int64_t b = int64_t(uniq_hi.bytes + uniq_inv64.bytes + hi_flag.bytes + hi_list.bytes +
+                        emap.bytes + uniq_list.bytes + n_uniq_d.bytes + cls_inv.bytes +
                         uniq_inv.bytes + cls_sym.bytes + pb.bytes + pr.bytes + pd.bytes + pd2.bytes + r1.bytes + e1.bytes +
                         vin.bytes + vout.bytes + cinv.bytes + ws.bytes + sc.bytes + cg_r.bytes +
                         cg_d.bytes + cg_q.bytes);
@@ -329,7 +330,7 @@ template <typename T>
 void Multigrid<T>::bj(const T* r, T* z, cudaStream_t s) {
     launch_bj_apply<T>(N, int(ne), r, z, nullptr, emap.as<int>(), cls_inv.template as<T>(),
                        cls_sym.as<int>(), uniq_inv.template as<T>(),
-                       eta_inv_of<T>(P), T(0), T(1), true, s, bj_hi());
+                       eta_inv_of<T>(P), T(0), T(1), true, s, bj_hi(), bj_inv64());
 }
 
 // Arnoldi (GMRES) estimate of the largest eigenvalue of the preconditioned
@@ -467,6 +468,11 @@ void Multigrid<T>::mark_split_tiles(cudaStream_t s) {
             launch_mark_uniq_hi(P->desc.nx, P->desc.ny, uniq_list.as<int>(), n_uniq_d.as<int>(),
                                 n_uniq, P->eta_d.as<double>(), std::max(1.0, 0.1 * ratio),
                                 uniq_hi.as<unsigned char>(), s);
+            // their inverses are also kept in FP64 (an ill-conditioned inverse
+            // rounded to FP32 is wrong along its stiff directions)
+            uniq_inv64.alloc(size_t(std::max(n_uniq, 1)) * nb * nb * sizeof(double));
+            launch_build_blocks<double>(N, P->geom, uniq_list.as<int>(), n_uniq,
+                                        P->eta_d.as<double>(), uniq_inv64.as<double>(), s);
         }
     }
     if (sizeof(T) == 4) {
@@ -716,7 +722,7 @@ void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
         if (zero) {
             // d = c2 M^{-1} b, y = d; the next step's residual is b - A d
             launch_bj_apply<T>(N, int(ne), b, dA, y, em, ci, cs, ui, einv0, T(0), T(1.0 / ch.theta),
-                               true, s, bj_hi());
+                               true, s, bj_hi(), bj_inv64());
         } else {
             launch_cheb_elem<T>(N, P->geom, y, b, r, eta, em, ci, cs, ui, einv0, nullptr, dA, nullptr,
                                 T(0), T(1.0 / ch.theta), false, s);
@@ -743,13 +749,14 @@ void Multigrid<T>::smooth_p(const T* b, T* y, bool zero, cudaStream_t s) {
     const T* einv = eta_inv_of<T>(P);
     launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
                        cls_sym.as<int>(), uniq_inv.template as<T>(), einv,
-                       T(0), T(1.0 / ch.theta), zero, s, bj_hi());
+                       T(0), T(1.0 / ch.theta), zero, s, bj_hi(), bj_inv64());
     for (int st = 1; st < P->desc.cheb_steps_p; ++st) {
         launch_apply_sip<T>(N, P->geom, dd, r, eta, T(-1), r, T(1), s);  // r -= A d
         const double rn = 1.0 / (2.0 * ch.sigma - rho);
         launch_bj_apply<T>(N, int(ne), r, dd, y, emap.as<int>(), cls_inv.template as<T>(),
                            cls_sym.as<int>(), uniq_inv.template as<T>(),
-                           einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s, bj_hi());
+                           einv, T(rn * rho), T(2.0 * rn / ch.delta), false, s, bj_hi(),
+                           bj_inv64());
         rho = rn;
     }
 }
