@@ -57,11 +57,23 @@ def parse():
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the warm-up and timed FP64 steps (for ncu launch lists)")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "batch", "serve", "coarse", "sinkers", "checkerboard"],
+                    choices=["solve", "batch", "serve", "coarse", "sinkers", "checkerboard",
+                             "kernel"],
                     help="solve: the headline line; batch / serve: the batched and served "
                          "forms on bounded samples of their workloads; coarse: the four "
                          "coarse-space preconditioners; sinkers / checkerboard: the "
-                         "six-sinker and checkerboard iteration sweeps (extra lines)")
+                         "six-sinker and checkerboard iteration sweeps (extra lines); "
+                         "kernel: a few launches of one operator on a small case, the "
+                         "command the ncu captures under profiles/ run")
+    ap.add_argument("--kernel", default="apply_f64",
+                    choices=["apply_f64", "apply_f32", "vcycle_f32"],
+                    help="operator run by --mode kernel: the FP64 or FP32 SIP apply on a "
+                         "random viscosity field, or one FP32 V-cycle of the many-discs field")
+    ap.add_argument("--apply-code", default="",
+                    help="--mode kernel and --profile-only: pinned SIP apply schedule codes "
+                         "'FP64[,FP32]' (1 elem2, 2 elem1, 3 tile, 4 staged 2 rows, 5 staged "
+                         "4 rows; empty leaves the tuner's choice, which timings taken "
+                         "under a profiler can mislead)")
     ap.add_argument("--count", type=int, default=32,
                     help="instances (batch) or requests (serve) in the bounded sample")
     ap.add_argument("--sinker-inner", default="gcr",
@@ -218,6 +230,8 @@ def run_ours(args, rank, world):
     def make(precision):
         prob = api.Problem(ctx, n, n, k, eta_h, bc=wl.bc, n_hlevels=wl.n_hlevels, seed=1,
                            precision=precision)
+        if args.profile_only and apply_codes(args):
+            prob.set_schedule(apply=apply_codes(args))
         f = torch.empty(prob.n_u, dtype=torch.float64, device=dev)
         u = torch.empty_like(f)
         p = torch.empty(prob.n_p, dtype=torch.float64, device=dev)
@@ -236,7 +250,7 @@ def run_ours(args, rank, world):
                           inner_loop=args.inner_loop, inner_norm=inner_norm,
                           check=not args.profile_only)
 
-    def timed(precision, steps, warmup, clocks=None, inner_norm=head_norm):
+    def timed(precision, steps, warmup, clocks=None, inner_norm=head_norm, profiler_range=False):
         prob, f, u, p = make(precision)
         for _ in range(warmup):
             step(prob, f, u, p, inner_norm)
@@ -246,6 +260,8 @@ def run_ours(args, rank, world):
         times, reps = [], []
         if clocks:
             clocks.start()
+        if profiler_range:
+            torch.cuda.profiler.start()
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -257,11 +273,15 @@ def run_ours(args, rank, world):
             times.append(e0.elapsed_time(e1))
         clocks_out = clocks.stop() if clocks else None
         torch.cuda.synchronize()
+        if profiler_range:
+            torch.cuda.profiler.stop()
         return prob, f, u, p, times, reps, clocks_out
 
     clocks = ClockSampler(dev.index)
     if args.profile_only:   # one form only, for profiler launch lists
-        _, _, _, _, tp, rp, _ = timed(args.profile_precision, args.steps, args.warmup)
+        # (the timed steps are the CUDA profiler range: ncu --profile-from-start off)
+        _, _, _, _, tp, rp, _ = timed(args.profile_precision, args.steps, args.warmup,
+                                      profiler_range=True)
         return {"metric": METRIC, "value": whole_job_rate(args.steps, 1, sum(tp)), "unit": UNIT,
                 "profile_only": True, "precision": args.profile_precision,
                 "solve_report": rp[-1]}
@@ -490,8 +510,6 @@ def apply_f32_rooflines(ctx, dev, flush, stream, peaks):
 # committed ncu summaries of the FP64 apply kernels on the 128^2, k = 3 workload
 TRAFFIC_PROFILES = {
     "k_apply_elem2<4,double,1>": os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md"),
-    "k_apply_stage<4,double,double,2,1,0>": os.path.join(
-        ROOT, "profiles", "k_apply_stage_fp64_128x128_k3.md"),
     "k_apply_stage<4,double,double,4,1,0>": os.path.join(
         ROOT, "profiles", "k_apply_stage4_fp64_128x128_k3.md"),
 }
@@ -628,7 +646,7 @@ def cpu_baseline():
             "kind": "oracle",
             "sample": f"oracle solves of the headline physics on {n0}x{n0} and {n1}x{n1} meshes "
                       "(3 h-coarsenings each), one spawned process per mesh, SciPy sparse "
-                      "single-threaded; value = 1 / (the {n1}x{n1} time scaled to 128x128 by the "
+                      f"single-threaded; value = 1 / (the {n1}x{n1} time scaled to 128x128 by the "
                       "fitted exponent of time in the element count): an extrapolation",
             "measured": sc["samples"], "exponent": sc["exponent"],
             "extrapolated_s_128x128": t}
@@ -1004,6 +1022,59 @@ def run_checkerboard(args):
                        "precision": "fp64", "outer": "fgmres", "inner": args.checker_inner}}
 
 
+def apply_codes(args):
+    """--apply-code 'a[,b]' as the [FP64, FP32] pair set_schedule takes."""
+    if not args.apply_code:
+        return None
+    c = [int(v) for v in args.apply_code.split(",")]
+    return [c[0], c[-1]]
+
+
+def run_kernel(args):
+    """A few launches of one operator on a small case (--profile-n, --profile-k),
+    timed with CUDA events: the command behind the ncu captures of single
+    kernels. apply_f64 / apply_f32: y = A x (Eq. 6 form) on a random viscosity
+    field log-uniform over three decades; vcycle_f32: one FP32 V-cycle of the
+    many-discs field (the high-contrast workload, split-precision parts
+    included) with the fused smoother step off, so the block-Jacobi kernel
+    launches on its own."""
+    import torch
+    from paper_1607_03777_gb300 import api, synth
+    ctx = api.Context(0)
+    n, k = args.profile_n, args.profile_k
+    if args.kernel == "vcycle_f32":
+        wl = synth.many_discs(n=n, k=k, n_hlevels=synth.levels_to_17(n))
+        eta, _ = ctx.rasterise_inclusions(n, n, wl.shapes)
+        pr = api.Problem(ctx, n, n, k, eta.cpu().numpy(), bc=wl.bc, n_hlevels=wl.n_hlevels,
+                         seed=1, precision="mixed")
+        pr.set_schedule(fused=[0, 0])
+        pr.setup()
+        x = torch.randn(pr.n_u, dtype=torch.float32, device="cuda")
+        fn = pr.vcycle_f32
+    else:
+        dt = torch.float32 if args.kernel == "apply_f32" else torch.float64
+        pr = api.Problem(ctx, n, n, k, synth.random_eta(n * n, 1, (0.0, 3.0)))
+        x = torch.randn(pr.n_u, dtype=dt, device="cuda")
+        fn = pr.apply_A_f32 if dt == torch.float32 else pr.apply_A
+    if apply_codes(args):
+        pr.set_schedule(apply=apply_codes(args))
+    y = torch.empty_like(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(max(args.warmup, 1)):
+        fn(x, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()   # ncu --profile-from-start off captures from here
+    ev[0].record()
+    for _ in range(args.steps):
+        fn(x, y)
+    ev[1].record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return {"mode": "kernel", "kernel": args.kernel, "n": n, "k": k,
+            "schedule": pr.schedule(), "ms_per_call": ev[0].elapsed_time(ev[1]) / args.steps,
+            "finite": bool(torch.isfinite(y).all().item())}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1012,7 +1083,8 @@ def main():
     if args.mode != "solve":
         if rank == 0:
             out = {"batch": run_batch, "serve": run_serve, "coarse": run_coarse,
-                   "sinkers": run_sinkers, "checkerboard": run_checkerboard}[args.mode](args)
+                   "sinkers": run_sinkers, "checkerboard": run_checkerboard,
+                   "kernel": run_kernel}[args.mode](args)
             print(json.dumps(out), flush=True)
         return 0
     if args.impl == "reference":

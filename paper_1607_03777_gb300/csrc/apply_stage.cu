@@ -48,15 +48,29 @@ struct StageLayout {
     static constexpr int NHALO = 2 * STX + 2 * TYS;
     static constexpr int TRW = 16 * N + 1;  // own traces of one element, all four faces
     static constexpr int HW = 4 * N + 1;    // the one face of a halo element
+    // Region 0 holds in turn the staged input blocks, the own traces and the
+    // output blocks (each phase ends at a barrier with its data read or in
+    // registers): one region instead of three, so more CTAs fit an SM.
     static constexpr size_t X_BYTES = size_t(XH) * XW * XS * sizeof(TS);
-    static constexpr size_t ETA_OFF = (X_BYTES + 15) / 16 * 16;
-    static constexpr size_t TR_OFF = ETA_OFF + (size_t(XH) * XW * sizeof(TC) + 15) / 16 * 16;
-    static constexpr size_t H_OFF = TR_OFF + size_t(STX) * TYS * TRW * sizeof(TC);
+    static constexpr size_t TR_BYTES = size_t(STX) * TYS * TRW * sizeof(TC);
+    static constexpr size_t OUT_BYTES = size_t(TYS) * STX * XS * sizeof(TC);
+    static constexpr size_t R0_BYTES =
+        X_BYTES > TR_BYTES ? (X_BYTES > OUT_BYTES ? X_BYTES : OUT_BYTES)
+                           : (TR_BYTES > OUT_BYTES ? TR_BYTES : OUT_BYTES);
+    static constexpr size_t ETA_OFF = (R0_BYTES + 15) / 16 * 16;
+    static constexpr size_t H_OFF = ETA_OFF + (size_t(XH) * XW * sizeof(TC) + 15) / 16 * 16;
     static constexpr size_t BYTES = H_OFF + size_t(NHALO) * HW * sizeof(TC);
-    static_assert(size_t(TYS) * STX * XS * sizeof(TC) <= X_BYTES,
-                  "the output blocks fit the staged input region");
+    // CTAs per SM asked of the register allocator: as many as the shared
+    // memory admits (1 KB reserved per CTA), unless that leaves a thread
+    // fewer registers than the element's arrays need without spilling
+    static constexpr int REG_FLOOR =
+        sizeof(TC) == 8 ? (N <= 4 ? 128 : (N == 5 ? 168 : 255)) : (N <= 5 ? 80 : 128);
+    static constexpr int SMEM_FIT = int((228 * 1024) / (BYTES + 1024));
+    static constexpr int REG_FIT = 65536 / (NT * REG_FLOOR);
+    static constexpr int MIN_BLOCKS =
+        (SMEM_FIT < REG_FIT ? SMEM_FIT : REG_FIT) > 1 ? (SMEM_FIT < REG_FIT ? SMEM_FIT : REG_FIT)
+                                                      : 1;
 };
-
 
 // Copy the tile's staged element blocks and viscosities into shared memory.
 // Stage row r is mesh row ey0 - 1 + r, stage column c mesh column ex0 - 1 + c.
@@ -140,12 +154,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TS, TC>& a, int ex0, 
 
 // Phase B of component C on the staged tile: face vectors from own and
 // neighbour traces (neighbour viscosities from the stage), spread into y_C;
-// the block goes to sy (shared memory), or, with a.r1, alpha y + beta z of
-// its Q^2_1 modes straight to r1.
+// with a.r1, alpha y + beta z of its Q^2_1 modes go straight to r1.
 template <int N, typename TS, typename TC, int C, int TYS>
 __device__ __forceinline__ void stage_phase_b(const StageArgs<TS, TC>& a, int ex, int ey, int tx,
                                               int ty, TC etaK, const TC* seta, const TC* s_tr,
-                                              const TC* s_halo, TC (&y)[N][N], TC* sy) {
+                                              const TC* s_halo, TC (&y)[N][N]) {
     using L = StageLayout<N, TS, TC, TYS>;
     constexpr int NB = L::NB;
     const int nx = a.c.nx, ny = a.c.ny;
@@ -224,13 +237,7 @@ __device__ __forceinline__ void stage_phase_b(const StageArgs<TS, TC>& a, int ex
                 if (zz) v += a.c.beta * TC(zz[j * N + i]);
                 d1[j * 2 + i] = TS(v);
             }
-        return;
     }
-    TC* dst = sy + el * L::XS + C * N * N;
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-#pragma unroll
-        for (int i = 0; i < N; ++i) dst[j * N + i] = y[j][i];
 }
 
 // Write the tile's output blocks from shared memory: y = alpha (A x) + beta z
@@ -298,9 +305,10 @@ template <int N, typename TS, typename TC, int TYS, bool VEC>
 __device__ __forceinline__ void stage_body(const StageArgs<TS, TC>& a, int bx, int by) {
     using L = StageLayout<N, TS, TC, TYS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TS* sx = reinterpret_cast<TS*>(smem_raw);
+    TS* sx = reinterpret_cast<TS*>(smem_raw);       // region 0: staged inputs,
+    TC* s_tr = reinterpret_cast<TC*>(smem_raw);     // then own traces,
+    TC* sy = reinterpret_cast<TC*>(smem_raw);       // then output blocks
     TC* seta = reinterpret_cast<TC*>(smem_raw + L::ETA_OFF);
-    TC* s_tr = reinterpret_cast<TC*>(smem_raw + L::TR_OFF);
     TC* s_halo = reinterpret_cast<TC*>(smem_raw + L::H_OFF);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ty = warp / 2, c = warp % 2, tx = lane;
@@ -331,10 +339,9 @@ __device__ __forceinline__ void stage_body(const StageArgs<TS, TC>& a, int bx, i
                                s_halo + h * L::HW);
         }
     }
-    TC y[N][N];
+    TC u[2][N][N];
     TC etaK = TC(0);
     if (active) {
-        TC u[2][N][N];
         const TS* src = sx + ((ty + 1) * L::XW + tx + 1) * L::XS;
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc)
@@ -343,21 +350,32 @@ __device__ __forceinline__ void stage_body(const StageArgs<TS, TC>& a, int bx, i
 #pragma unroll
                 for (int i = 0; i < N; ++i) u[cc][j][i] = TC(src[cc * N * N + j * N + i]);
         etaK = seta[(ty + 1) * L::XW + tx + 1];
+    }
+    __syncthreads();   // staged blocks read: region 0 takes the traces
+    TC y[N][N];
+    if (active) {
         TC* tr = s_tr + (ty * STX + tx) * L::TRW;
         if (c == 0)
             elem2_phase_a<N, TC, 0>(a.c, u, etaK, tr, y);
         else
             elem2_phase_a<N, TC, 1>(a.c, u, etaK, tr, y);
     }
-    __syncthreads();   // from here on the stage region receives the outputs
-    TC* sy = reinterpret_cast<TC*>(smem_raw);
+    __syncthreads();
     if (active) {
         if (c == 0)
-            stage_phase_b<N, TS, TC, 0, TYS>(a, ex, ey, tx, ty, etaK, seta, s_tr, s_halo, y, sy);
+            stage_phase_b<N, TS, TC, 0, TYS>(a, ex, ey, tx, ty, etaK, seta, s_tr, s_halo, y);
         else
-            stage_phase_b<N, TS, TC, 1, TYS>(a, ex, ey, tx, ty, etaK, seta, s_tr, s_halo, y, sy);
+            stage_phase_b<N, TS, TC, 1, TYS>(a, ex, ey, tx, ty, etaK, seta, s_tr, s_halo, y);
     }
     if (a.r1) return;
+    __syncthreads();   // traces read: region 0 takes the output blocks
+    if (active) {
+        TC* dst = sy + (ty * STX + tx) * L::XS + c * N * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) dst[j * N + i] = y[j][i];
+    }
     __syncthreads();
     stage_store<N, TS, TC, TYS, VEC>(a, ex0, ey0, sy);
 }
@@ -365,7 +383,8 @@ __device__ __forceinline__ void stage_body(const StageArgs<TS, TC>& a, int bx, i
 // One CTA per tile: a 2D grid over the mesh (tiles flagged in skip exit at
 // once), or (LIST) a 1D grid over the tile ids in a.tiles.
 template <int N, typename TS, typename TC, int TYS, bool VEC, bool LIST>
-__global__ void __launch_bounds__(64 * TYS) k_apply_stage(const StageArgs<TS, TC> a) {
+__global__ void __launch_bounds__(64 * TYS, (StageLayout<N, TS, TC, TYS>::MIN_BLOCKS))
+    k_apply_stage(const StageArgs<TS, TC> a) {
     grid_dep_wait();
     int bx, by;
     if constexpr (LIST) {
@@ -384,7 +403,7 @@ __global__ void __launch_bounds__(64 * TYS) k_apply_stage(const StageArgs<TS, TC
 // items[b].x (arguments args[items[b].x]) on its tile items[b].y (split
 // tile numbering); members with active[m] == 0 are skipped.
 template <int N, typename TS, typename TC, bool VEC>
-__global__ void __launch_bounds__(64 * SPLIT_TYS)
+__global__ void __launch_bounds__(64 * SPLIT_TYS, (StageLayout<N, TS, TC, SPLIT_TYS>::MIN_BLOCKS))
     k_apply_stage_batch(const StageArgs<TS, TC>* __restrict__ args, const int2* __restrict__ items,
                         const int* __restrict__ active) {
     grid_dep_wait();
@@ -464,21 +483,60 @@ void stage_plain(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const
     launch_stage<N, T, T, TYS, false>(a, grid, vec_aligned(x, y, z), s);
 }
 
+// A second stream of this host thread on the current device, with a fork
+// and a join event: the two launches of the split-precision apply write
+// disjoint tiles and run side by side (in a captured graph: two parallel
+// kernel nodes).
+struct ForkStream {
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    void release() {
+        if (s) cudaStreamDestroy(s);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        s = nullptr;
+        fork = join = nullptr;
+    }
+    ~ForkStream() { release(); }   // errors at process teardown are ignored
+};
+
+ForkStream& fork_stream() {
+    thread_local ForkStream f;
+    int dev = 0;
+    SIP_CUDA(cudaGetDevice(&dev));
+    if (f.dev != dev || !f.s) {
+        f.release();
+        SIP_CUDA(cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking));
+        SIP_CUDA(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming));
+        SIP_CUDA(cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming));
+        f.dev = dev;
+    }
+    return f;
+}
+
 // Split-precision FP32 apply: FP32 arithmetic on the tiles not flagged in
-// g.hi_flag, FP64 arithmetic on the g.n_hi tiles of g.hi_tiles.
+// g.hi_flag, FP64 arithmetic on the g.n_hi tiles of g.hi_tiles.  The FP64
+// launch has few CTAs and runs at the FP64 pipe's rate; the FP32 launch
+// fills the SMs beside it on a second stream.
 template <int N>
 void stage_split(const OpGeom& g, const float* x, float* y, const float* eta, float alpha,
                  const float* z, float beta, float* r1, cudaStream_t s) {
     const bool vec = vec_aligned(x, y, z);
+    ForkStream& f = fork_stream();
+    StageArgs<float, double> hi =
+        make_stage_args<float, double>(g, x, y, eta, alpha, z, beta, r1, N, SPLIT_TYS);
+    hi.tiles = g.hi_tiles;
+    SIP_CUDA(cudaEventRecord(f.fork, s));
+    SIP_CUDA(cudaStreamWaitEvent(f.s, f.fork, 0));
+    launch_stage<N, float, double, SPLIT_TYS, true>(hi, dim3(unsigned(g.n_hi)), vec, f.s);
+    SIP_CUDA(cudaEventRecord(f.join, f.s));
     StageArgs<float, float> lo =
         make_stage_args<float, float>(g, x, y, eta, alpha, z, beta, r1, N, SPLIT_TYS);
     lo.skip = g.hi_flag;
     const dim3 grid((g.nx + STX - 1) / STX, (g.ny + SPLIT_TYS - 1) / SPLIT_TYS);
     launch_stage<N, float, float, SPLIT_TYS, false>(lo, grid, vec, s);
-    StageArgs<float, double> hi =
-        make_stage_args<float, double>(g, x, y, eta, alpha, z, beta, r1, N, SPLIT_TYS);
-    hi.tiles = g.hi_tiles;
-    launch_stage<N, float, double, SPLIT_TYS, true>(hi, dim3(unsigned(g.n_hi)), vec, s);
+    SIP_CUDA(cudaStreamWaitEvent(s, f.join, 0));
 }
 
 template <int N, typename T>
@@ -533,6 +591,8 @@ __global__ void k_mark_hi(int nx, int ny, int ntx, int nty, const double* eta, c
 }
 
 }  // namespace
+
+void split_fork_prepare() { (void)fork_stream(); }
 
 int split_tile_count(int nx, int ny) {
     return ((nx + STX - 1) / STX) * ((ny + SPLIT_TYS - 1) / SPLIT_TYS);

@@ -206,6 +206,9 @@ bool launch_apply_sip_stage(int N, const OpGeom& g, const T* x, T* y, const T* e
 // eta >= ratio x min(eta).  scratch: 32 device bytes.  Returns the count
 // (synchronises s).
 int split_tile_count(int nx, int ny);
+// creates this host thread's side stream of the split-precision apply (its
+// first use would otherwise fall inside a graph capture)
+void split_fork_prepare();
 int mark_hi_tiles(int nx, int ny, const double* eta, double ratio, unsigned char* flag, int* list,
                   int* scratch, cudaStream_t s);
 // The apply variant in force for precision T: SIP_APPLY_KERNEL (elem2, elem1,

@@ -462,6 +462,7 @@ void Multigrid<T>::mark_split_tiles(cudaStream_t s) {
         n_hi = mark_hi_tiles(P->desc.nx, P->desc.ny, P->eta_d.as<double>(), ratio,
                              hi_flag.as<unsigned char>(), hi_list.as<int>(), hi_scr.as<int>(), s);
         if (n_hi > 0) {
+            split_fork_prepare();   // the side stream, before any graph capture
             // FP32 sums of an element block whose face neighbour is much
             // stiffer cancel the block's small components the same way
             uniq_hi.alloc(size_t(std::max(n_uniq, 1)));
