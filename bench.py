@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--apply-code", default="",
                     help="--mode kernel and --profile-only: pinned SIP apply schedule codes "
                          "'FP64[,FP32]' (1 elem2, 2 elem1, 3 tile, 4 staged 2 rows, 5 staged "
-                         "4 rows; empty leaves the tuner's choice, which timings taken "
+                         "4 rows, 6 warp-row (FP32 only); empty leaves the tuner's choice, which timings taken "
                          "under a profiler can mislead)")
     ap.add_argument("--count", type=int, default=32,
                     help="instances (batch) or requests (serve) in the bounded sample")

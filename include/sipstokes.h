@@ -147,15 +147,17 @@ sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p
  * operator: 1 component-split thread pair per element, 2 one thread per
  * element, 3 shared-memory tile, 4 / 5 component-split thread pair on
  * element blocks staged through shared memory with 2 / 4 tile rows (an FP32
- * operator with split-precision tiles, see mixed_fp64_ratio, always runs 4);
+ * operator with split-precision tiles, see mixed_fp64_ratio, always runs 4),
+ * 6 (FP32 operator only) one thread per element and one warp per tile row
+ * on element blocks staged with asynchronous 16-byte copies;
  * fused[0] / fused[1]: 1 if a p-level smoother step is one launch (apply,
  * block-Jacobi and Chebyshev update together), 0 if it is the apply and
  * block-Jacobi launches.  Either array may be NULL; the values are those of
  * the last set-up (defaults before). */
 sip_status sip_problem_schedule(const sip_problem* prob, int apply[2], int fused[2]);
 /* Pin the kernel schedule of this problem (no counterpart in the paper):
- * apply[t] in 0..5 with the codes of sip_problem_schedule (0 = autotuned;
- * 1, 2, 4, 5 need k <= 5), fused[t] in -1..1 (-1 = autotuned; 1 takes effect
+ * apply[t] in 0..6 with the codes of sip_problem_schedule (0 = autotuned;
+ * 1, 2, 4, 5, 6 need k <= 5; 6 only for apply[1]), fused[t] in -1..1 (-1 = autotuned; 1 takes effect
  * only for k <= 3).  Either array may be NULL (unchanged).  The operator
  * entry points use a pinned apply kernel at once; the multigrid set-up is
  * marked stale, so the next call that needs it rebuilds it (in the buffers

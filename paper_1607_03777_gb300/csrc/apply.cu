@@ -470,7 +470,8 @@ int apply_variant(const OpGeom& g) {
         return e == "elem2" ? int(APPLY_ELEM2)
                             : (e == "elem1" ? int(APPLY_ELEM1)
                             : (e == "tile" ? int(APPLY_TILE)
-                            : (e == "stage" ? int(APPLY_STAGE) : int(APPLY_AUTO))));
+                            : (e == "stage" ? int(APPLY_STAGE)
+                            : (e == "warp" ? int(APPLY_WARP) : int(APPLY_AUTO)))));
     }();
     return forced != APPLY_AUTO ? forced : g.variant[sizeof(T) == 4 ? 1 : 0];
 }
@@ -485,6 +486,13 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
     const int v = apply_variant<T>(g);
     // the split-precision FP32 operator exists only as the staged kernel
     const bool split = sizeof(T) == 4 && g.n_hi > 0;
+    if constexpr (sizeof(T) == 4) {
+        if (v == APPLY_WARP && !split &&
+            launch_apply_sip_warp(N, g, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
+                                  reinterpret_cast<const float*>(eta), float(alpha),
+                                  reinterpret_cast<const float*>(z), float(beta), s))
+            return;
+    }
     if ((v == APPLY_STAGE || split) &&
         launch_apply_sip_stage<T>(N, g, x, y, eta, alpha, z, beta, nullptr, s))
         return;

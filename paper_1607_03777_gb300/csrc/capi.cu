@@ -236,8 +236,10 @@ sip_status sip_problem_schedule(const sip_problem* p, int apply[2], int fused[2]
 sip_status sip_problem_set_schedule(sip_problem* p, const int apply[2], const int fused[2]) {
     if (!p) return SIP_ERR_INVALID_ARG;
     for (int t = 0; t < 2; ++t) {
-        if (apply && (apply[t] < 0 || apply[t] > 5 || (apply[t] != 0 && apply[t] != 3 && p->n > 6))) {
-            p->ctx->err = "schedule: apply code outside 0..5, or an element kernel above k = 5";
+        if (apply && (apply[t] < 0 || apply[t] > 6 || (apply[t] != 0 && apply[t] != 3 && p->n > 6) ||
+                      (apply[t] == 6 && t == 0))) {
+            p->ctx->err = "schedule: apply code outside 0..6, an element kernel above k = 5, or "
+                          "code 6 for the FP64 operator";
             return SIP_ERR_INVALID_ARG;
         }
         if (fused && (fused[t] < -1 || fused[t] > 1)) {

@@ -147,7 +147,10 @@ Tab1D<N, T> make_tab() {
 // |e|/|K| = 1/h_normal; boundary faces double it (eq. sipg_penalty).
 // Kernel schedule of one operator, per precision ([0] FP64, [1] FP32):
 // which apply kernel runs and whether the p-level smoother step is fused.
-enum ApplyVariant { APPLY_AUTO = 0, APPLY_ELEM2 = 1, APPLY_ELEM1 = 2, APPLY_TILE = 3, APPLY_STAGE = 4 };
+// APPLY_WARP exists for the FP32 operator only (one thread per element, one
+// warp per tile row, cp.async staging).
+enum ApplyVariant { APPLY_AUTO = 0, APPLY_ELEM2 = 1, APPLY_ELEM1 = 2, APPLY_TILE = 3, APPLY_STAGE = 4,
+                    APPLY_WARP = 6 };
 
 struct OpGeom {
     int nx, ny;
@@ -201,6 +204,10 @@ bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* et
 template <typename T>
 bool launch_apply_sip_stage(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                             const T* z, T beta, T* r1, cudaStream_t s);
+// Warp-row FP32 apply (N <= 6, 16-byte aligned vectors, no split-precision
+// tiles; returns false otherwise): y = alpha A x + beta z, z may equal y.
+bool launch_apply_sip_warp(int N, const OpGeom& g, const float* x, float* y, const float* eta,
+                           float alpha, const float* z, float beta, cudaStream_t s);
 // Number of split-precision tiles of an nx x ny mesh, and their flags: tile
 // t is flagged (and listed) when an element of the tile or of its halo has
 // eta >= ratio x min(eta).  scratch: 32 device bytes.  Returns the count

@@ -5,7 +5,8 @@
 // apply issues fewer loads on large ones, the shared-memory tile kernel
 // covers every degree, and the staged-tile kernel (element blocks copied
 // through shared memory with coalesced 16-byte accesses, 2 or 4 tile rows)
-// suits the memory-bound FP32 operator.  So each problem times the candidates on its own mesh
+// suits the memory-bound FP32 operator, as does the warp-row kernel (one
+// thread per element, one warp per tile row, cp.async staging; FP32 only).  So each problem times the candidates on its own mesh
 // the first time it is set up and keeps the fastest:
 //   * the apply kernel, per precision the problem runs in;
 //   * the p-level smoother step: one fused launch (apply + block-Jacobi +
@@ -106,7 +107,9 @@ void tune_apply_t(sip_problem* P, cudaStream_t s) {
         const int64_t launches = launch_counter();
         const int saved_rows = P->geom.stage_rows[t];
         for (int cand : {int(APPLY_ELEM2), int(APPLY_ELEM1), int(APPLY_TILE),
-                         int(APPLY_STAGE) + 16 * 2, int(APPLY_STAGE) + 16 * 4}) {
+                         int(APPLY_STAGE) + 16 * 2, int(APPLY_STAGE) + 16 * 4,
+                         sizeof(T) == 4 ? int(APPLY_WARP) : -1}) {
+            if (cand < 0) continue;
             P->geom.variant[t] = cand % 16;
             P->geom.stage_rows[t] = cand / 16 ? cand / 16 : saved_rows;
             const double ms = time_ms(
