@@ -146,10 +146,11 @@ sip_status sip_problem_sizes(const sip_problem* prob, int64_t* n_u, int64_t* n_p
  * the choice.  apply[0] / apply[1]: SIP apply kernel of the FP64 / FP32
  * operator: 1 component-split thread pair per element, 2 one thread per
  * element, 3 shared-memory tile, 4 / 5 component-split thread pair on
- * element blocks staged through shared memory with 2 / 4 tile rows (an FP32
- * operator with split-precision tiles, see mixed_fp64_ratio, always runs 4),
- * 6 (FP32 operator only) one thread per element and one warp per tile row
- * on element blocks staged with asynchronous 16-byte copies;
+ * element blocks staged through shared memory with 2 / 4 tile rows, 6 (FP32
+ * operator only) one thread per element and one warp per tile row on
+ * element blocks staged with asynchronous 16-byte copies.  An FP32 operator
+ * with split-precision tiles (see mixed_fp64_ratio) reports 4: its marked
+ * tiles run the staged kernel with FP64 arithmetic, the others kernel 6;
  * fused[0] / fused[1]: 1 if a p-level smoother step is one launch (apply,
  * block-Jacobi and Chebyshev update together), 0 if it is the apply and
  * block-Jacobi launches.  Either array may be NULL; the values are those of

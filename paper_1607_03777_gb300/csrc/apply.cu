@@ -490,7 +490,7 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
         if (v == APPLY_WARP && !split &&
             launch_apply_sip_warp(N, g, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                                   reinterpret_cast<const float*>(eta), float(alpha),
-                                  reinterpret_cast<const float*>(z), float(beta), s))
+                                  reinterpret_cast<const float*>(z), float(beta), nullptr, s))
             return;
     }
     if ((v == APPLY_STAGE || split) &&

@@ -36,6 +36,8 @@ namespace {
 
 constexpr int STX = 32;      // elements per tile row
 constexpr int SPLIT_TYS = 2; // tile rows of the split-precision launches
+static_assert(STX == 32 && SPLIT_TYS == 2,
+              "the warp-row kernel reads the split-precision flags of 32 x 2 tiles");
 constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory of one CTA
 
 template <int N, typename TS, typename TC, int TYS>
@@ -531,11 +533,15 @@ void stage_split(const OpGeom& g, const float* x, float* y, const float* eta, fl
     SIP_CUDA(cudaStreamWaitEvent(f.s, f.fork, 0));
     launch_stage<N, float, double, SPLIT_TYS, true>(hi, dim3(unsigned(g.n_hi)), vec, f.s);
     SIP_CUDA(cudaEventRecord(f.join, f.s));
-    StageArgs<float, float> lo =
-        make_stage_args<float, float>(g, x, y, eta, alpha, z, beta, r1, N, SPLIT_TYS);
-    lo.skip = g.hi_flag;
-    const dim3 grid((g.nx + STX - 1) / STX, (g.ny + SPLIT_TYS - 1) / SPLIT_TYS);
-    launch_stage<N, float, float, SPLIT_TYS, false>(lo, grid, vec, s);
+    // the unflagged tiles: the warp-row kernel (y = alpha A x + beta z), else
+    // (residual restricted to the Q^2_1 modes) the staged kernel
+    if (r1 || !launch_apply_sip_warp(N, g, x, y, eta, alpha, z, beta, g.hi_flag, s)) {
+        StageArgs<float, float> lo =
+            make_stage_args<float, float>(g, x, y, eta, alpha, z, beta, r1, N, SPLIT_TYS);
+        lo.skip = g.hi_flag;
+        const dim3 grid((g.nx + STX - 1) / STX, (g.ny + SPLIT_TYS - 1) / SPLIT_TYS);
+        launch_stage<N, float, float, SPLIT_TYS, false>(lo, grid, vec, s);
+    }
     SIP_CUDA(cudaStreamWaitEvent(s, f.join, 0));
 }
 

@@ -4,11 +4,13 @@
 //
 // One thread owns one element and both of its velocity components; one warp
 // owns one tile row of 32 elements; a CTA of four warps owns a 32 x 4 tile
-// and loops over tiles (persistent grid, two CTAs per SM).  Per tile:
+// and loops over tiles (persistent grid, up to three CTAs per SM).  Per tile:
 //   * the element blocks of the tile, of its left and right neighbours and
 //     of the rows below and above are copied into shared memory with 16-byte
-//     cp.async copies issued one tile ahead (double buffer), no registers
-//     and no per-value index arithmetic on the way;
+//     cp.async copies, no registers and no per-value index arithmetic on the
+//     way (one stage buffer: the next tile's copies are issued as soon as
+//     the current tile is done, and the other CTAs of the SM compute
+//     meanwhile);
 //   * each thread reads its element from shared memory (odd N: contiguous
 //     blocks of 2 N^2 words, 8-byte reads free of bank conflicts; even N:
 //     padded slots, 16-byte reads free of bank conflicts), forms the value
@@ -35,7 +37,7 @@ constexpr int WTY = 4;            // tile rows: the warps of a CTA
 constexpr int WNT = WTX * WTY;    // threads per CTA
 constexpr unsigned FULL = 0xffffffffu;
 
-template <int N>
+template <int N, int NBUF = 2>
 struct WarpLayout {
     static constexpr int NN = N * N;
     static constexpr int NB = 2 * NN;               // floats per element
@@ -51,11 +53,12 @@ struct WarpLayout {
     static constexpr int BUFB = SH * ROWB;          // one stage buffer
     static constexpr int TRS = 4 * N + 2;           // floats per trace record (TRS / 2 odd)
     static constexpr int NHALO = 2 * WTX + 2 * WTY; // halo faces of a tile
-    static constexpr int OFF_ETA = 2 * BUFB;
-    static constexpr int OFF_REC = OFF_ETA + (2 * SH * SW * 4 + 15) / 16 * 16;
+    static constexpr int OFF_ETA = NBUF * BUFB;
+    static constexpr int OFF_REC = OFF_ETA + (NBUF * SH * SW * 4 + 15) / 16 * 16;
     static constexpr int OFF_HALO = OFF_REC + 2 * WTY * WTX * TRS * 4;
     static constexpr int BYTES = OFF_HALO + NHALO * TRS * 4;
-    static constexpr int MINB = BYTES + 1024 <= 114 * 1024 ? 2 : 1;
+    static constexpr int MINB = NBUF == 1 ? (BYTES + 1024 <= 75 * 1024 ? 3 : 2)
+                                          : (BYTES + 1024 <= 114 * 1024 ? 2 : 1);
     static_assert(NHALO % WTY == 0, "halo faces split evenly over the warps");
     static_assert(NHALO / WTY <= 32, "one halo face per lane");
 };
@@ -69,6 +72,7 @@ struct WarpArgs {
     long long n_total;   // floats of x
     int ntx, ntiles;
     int bulk;            // y = A x (alpha 1, no z): aligned rows leave as bulk copies
+    const unsigned char* skip;   // split-precision tiles (32 x 2) written by another launch
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -103,6 +107,7 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Byte offset of staged element j (0 = the left neighbour column) in the row
 // buffer of mesh row ey (odd N: the row's shift of 0 or 8 bytes).
@@ -257,6 +262,9 @@ __device__ __forceinline__ void store_elem(unsigned char* p, const float (&y)[2]
 template <int N, int DIR>
 __device__ __forceinline__ void dir_traces(const float (&u)[2][N][N], float two_over_h,
                                            float (&lo)[4 * N], float (&hi)[4 * N]) {
+    float dps[N];   // l_q'(+1) times 2 / h: physical derivative
+#pragma unroll
+    for (int q = 0; q < N; ++q) dps[q] = float(kT<N>.dp[q]) * two_over_h;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -267,52 +275,61 @@ __device__ __forceinline__ void dir_traces(const float (&u)[2][N][N], float two_
                 const float uq = DIR == 0 ? u[c][m][q] : u[c][q][m];   // q along the normal
                 if (q % 2 == 0) {
                     ev = fmaf(float(kT<N>.lp[q]), uq, ev);
-                    if (q > 0) evd = fmaf(float(kT<N>.dp[q]), uq, evd);
+                    if (q > 0) evd = fmaf(dps[q], uq, evd);
                 } else {
                     od = fmaf(float(kT<N>.lp[q]), uq, od);
-                    odd = fmaf(float(kT<N>.dp[q]), uq, odd);
+                    odd = fmaf(dps[q], uq, odd);
                 }
             }
             // l_q(-1) = (-1)^q l_q(1),  l_q'(-1) = -(-1)^q l_q'(1)
             lo[c * N + m] = ev - od;
             hi[c * N + m] = ev + od;
-            lo[2 * N + c * N + m] = (odd - evd) * two_over_h;
-            hi[2 * N + c * N + m] = (evd + odd) * two_over_h;
+            lo[2 * N + c * N + m] = odd - evd;
+            hi[2 * N + c * N + m] = evd + odd;
         }
 }
 
 // Volume terms of component C times eta_K (the same 1D Kronecker form as the
-// component-split kernels: G along x and y on u_C, D x D cross terms; eta_K
-// folded into the weights).
+// component-split kernels: G along x and y on u_C, D x D cross terms), every
+// scalar factor folded into the few nonzero table entries first.
 template <int N, int C>
 __device__ __forceinline__ void volume_comp(const ElemArgs<float>& a, const float (&u)[2][N][N],
                                             float etaK, float (&y)[N][N]) {
     const float sx = etaK * (C == 0 ? a.c2hy_hx : a.chy_hx);   // weight of G along x on u_C
     const float sy = etaK * (C == 0 ? a.chx_hy : a.c2hx_hy);   // weight of G along y on u_C
+    float Gx[N][N], Gy[N][N], De[N][N];   // scaled tables (zero entries never read)
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            Gx[p][q] = kT<N>.G[p][q] != 0.0 ? sx * float(kT<N>.G[p][q]) : 0.f;
+            Gy[p][q] = kT<N>.G[p][q] != 0.0 ? sy * float(kT<N>.G[p][q]) : 0.f;
+            De[p][q] = kT<N>.D[p][q] != 0.0 ? etaK * float(kT<N>.D[p][q]) : 0.f;
+        }
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int av = 0; av < N; ++av) {
-            float gx = 0.f, gy = 0.f;
+            float acc = 0.f;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                if (kT<N>.G[av][i] != 0.0) gx = fmaf(float(kT<N>.G[av][i]), u[C][b][i], gx);
-                if (kT<N>.G[b][i] != 0.0) gy = fmaf(float(kT<N>.G[b][i]), u[C][i][av], gy);
+                if (kT<N>.G[av][i] != 0.0) acc = fmaf(Gx[av][i], u[C][b][i], acc);
+                if (kT<N>.G[b][i] != 0.0) acc = fmaf(Gy[b][i], u[C][i][av], acc);
             }
-            y[b][av] = fmaf(sx, gx, sy * gy);
+            y[b][av] = acc;
         }
     float w[N][N];
     if constexpr (C == 0) {
-        // y_x[b][a] += sum_j D[j][b] sum_i D[a][i] u_y[j][i]
+        // y_x[b][a] += eta_K sum_j D[j][b] sum_i D[a][i] u_y[j][i]
 #pragma unroll
         for (int j = 0; j < N; ++j)
 #pragma unroll
             for (int av = 0; av < N; ++av) {
-                float s = 0.f;
+                float t = 0.f;
 #pragma unroll
                 for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[av][i] != 0.0) s = fmaf(float(kT<N>.D[av][i]), u[1][j][i], s);
-                w[j][av] = etaK * s;
+                    if (kT<N>.D[av][i] != 0.0) t = fmaf(float(kT<N>.D[av][i]), u[1][j][i], t);
+                w[j][av] = t;
             }
 #pragma unroll
         for (int b = 0; b < N; ++b)
@@ -320,18 +337,18 @@ __device__ __forceinline__ void volume_comp(const ElemArgs<float>& a, const floa
             for (int av = 0; av < N; ++av)
 #pragma unroll
                 for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[j][b] != 0.0) y[b][av] = fmaf(float(kT<N>.D[j][b]), w[j][av], y[b][av]);
+                    if (kT<N>.D[j][b] != 0.0) y[b][av] = fmaf(De[j][b], w[j][av], y[b][av]);
     } else {
-        // y_y[b][a] += sum_i D[i][a] sum_j D[b][j] u_x[j][i]
+        // y_y[b][a] += eta_K sum_i D[i][a] sum_j D[b][j] u_x[j][i]
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                float s = 0.f;
+                float t = 0.f;
 #pragma unroll
                 for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[b][j] != 0.0) s = fmaf(float(kT<N>.D[b][j]), u[0][j][i], s);
-                w[b][i] = etaK * s;
+                    if (kT<N>.D[b][j] != 0.0) t = fmaf(float(kT<N>.D[b][j]), u[0][j][i], t);
+                w[b][i] = t;
             }
 #pragma unroll
         for (int b = 0; b < N; ++b)
@@ -339,7 +356,7 @@ __device__ __forceinline__ void volume_comp(const ElemArgs<float>& a, const floa
             for (int av = 0; av < N; ++av)
 #pragma unroll
                 for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[i][av] != 0.0) y[b][av] = fmaf(float(kT<N>.D[i][av]), w[b][i], y[b][av]);
+                    if (kT<N>.D[i][av] != 0.0) y[b][av] = fmaf(De[i][av], w[b][i], y[b][av]);
     }
 }
 
@@ -397,6 +414,31 @@ __device__ __forceinline__ void face_interior(const FaceGeo<float>& fg, float pe
     }
 }
 
+// Face vectors of one face of K with normal direction DIR on side `side`,
+// any kind (face_pq): the case of boundary faces and ragged tiles.
+template <int N, int DIR>
+__device__ __forceinline__ void face_general(const ElemArgs<float>& a, int side, bool nb, float etaK,
+                                          float etaN, const float* own, const float* nbr, float* P,
+                                          float* Q) {
+    const FaceGeo<float>& fg = DIR == 0 ? a.fgx : a.fgy;
+    const float pen = DIR == 0 ? a.pen_x : a.pen_y;
+    float Dm[N * N];
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+        for (int q = 0; q < N; ++q) Dm[p * N + q] = float(kT<N>.D[p][q]);
+    const int kind = nb ? 0 : 1 + a.bc[2 * DIR + side];
+    const float eN = nb ? etaN : 0.f;
+    const float sigma = pen * (nb ? fmaxf(etaK, eN) : 2.f * etaK);
+    const float s = side == 0 ? -1.f : 1.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < N; ++m)
+            face_pq<N, float>(kind, c, m, DIR, s, fg, etaK, eN, sigma, own, own + 2 * N, nbr,
+                              nbr + 2 * N, Dm, P[c * N + m], Q[c * N + m]);
+}
+
 // Face terms of the two faces with normal direction DIR, both components,
 // spread into y (test mode q along the normal, m along the face).  A side
 // whose faces are interior for the whole warp takes face_interior; otherwise
@@ -423,22 +465,15 @@ __device__ __forceinline__ void flux_dir(const ElemArgs<float>& a, bool nb_lo, b
             else
                 face_interior<N, DIR, 1>(fg, pen, etaK, etaN, own, nbr, P[1], Q[1]);
         } else {
-            float Dm[N * N];
-#pragma unroll
-            for (int p = 0; p < N; ++p)
-#pragma unroll
-                for (int q = 0; q < N; ++q) Dm[p * N + q] = float(kT<N>.D[p][q]);
-            const int F = 2 * DIR + side;
-            const int kind = nb ? 0 : 1 + a.bc[F];
-            const float eN = nb ? etaN : 0.f;
-            const float sigma = pen * (nb ? fmaxf(etaK, eN) : 2.f * etaK);
-            const float s = side == 0 ? -1.f : 1.f;
+            float tp[2 * N], tq[2 * N];
+            face_general<N, DIR>(a, side, nb, etaK, etaN, own, nbr, tp, tq);
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int m = 0; m < N; ++m)
-                    face_pq<N, float>(kind, c, m, DIR, s, fg, etaK, eN, sigma, own, own + 2 * N,
-                                      nbr, nbr + 2 * N, Dm, P[side][c][m], Q[side][c][m]);
+                for (int m = 0; m < N; ++m) {
+                    P[side][c][m] = tp[c * N + m];
+                    Q[side][c][m] = tq[c * N + m];
+                }
         }
     }
 #pragma unroll
@@ -451,12 +486,9 @@ __device__ __forceinline__ void flux_dir(const ElemArgs<float>& a, bool nb_lo, b
             const float qm = Q[1][c][m] - Q[0][c][m];
 #pragma unroll
             for (int q = 0; q < N; ++q) {
-                float add = float(kT<N>.lp[q]) * (q % 2 == 0 ? pp : pm);
-                if (q > 0) add = fmaf(float(kT<N>.dp[q]), q % 2 == 0 ? qm : qp, add);
-                if (DIR == 0)
-                    y[c][m][q] += add;
-                else
-                    y[c][q][m] += add;
+                float& yy = DIR == 0 ? y[c][m][q] : y[c][q][m];
+                yy = fmaf(float(kT<N>.lp[q]), q % 2 == 0 ? pp : pm, yy);
+                if (q > 0) yy = fmaf(float(kT<N>.dp[q]), q % 2 == 0 ? qm : qp, yy);
             }
         }
 }
@@ -566,6 +598,7 @@ __device__ __forceinline__ void warp_tile(const WarpArgs& a, int ex0, int ey0, u
     // copies (y = A x on aligned rows) or as 16-byte chunks alpha y + beta z
     if (active) store_elem<N>(mine, y);
     if (ey >= ny) return;   // uniform over the warp
+    if (a.skip && a.skip[size_t(ey >> 1) * a.ntx + (ex0 / WTX)]) return;   // the FP64 launch's row
     const int ehi = min(ex0 + WTX, nx);
     const long long row = (long long)ey * nx;
     char* yb = reinterpret_cast<char*>(a.y);
@@ -672,10 +705,10 @@ __device__ __forceinline__ void warp_tile(const WarpArgs& a, int ex0, int ey0, u
     }
 }
 
-// Persistent CTAs: tile t = blockIdx.x + i gridDim.x, staged two tiles ahead.
-template <int N>
-__global__ void __launch_bounds__(WNT, WarpLayout<N>::MINB) k_apply_warp(const WarpArgs a) {
-    using L = WarpLayout<N>;
+// Persistent CTAs: tile t = blockIdx.x + i gridDim.x, staged NBUF tiles ahead.
+template <int N, int NBUF>
+__global__ void __launch_bounds__(WNT, (WarpLayout<N, NBUF>::MINB)) k_apply_warp(const WarpArgs a) {
+    using L = WarpLayout<N, NBUF>;
     grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* seta0 = reinterpret_cast<float*>(smem_raw + L::OFF_ETA);
@@ -683,7 +716,7 @@ __global__ void __launch_bounds__(WNT, WarpLayout<N>::MINB) k_apply_warp(const W
     float* halo = reinterpret_cast<float*>(smem_raw + L::OFF_HALO);
     const int G = int(gridDim.x);
 #pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NBUF; ++s) {
         const int ts = int(blockIdx.x) + s * G;
         if (ts < a.ntiles)
             warp_stage<N>(a, (ts % a.ntx) * WTX, (ts / a.ntx) * WTY, smem_raw + s * L::BUFB,
@@ -692,14 +725,14 @@ __global__ void __launch_bounds__(WNT, WarpLayout<N>::MINB) k_apply_warp(const W
     }
 #pragma unroll 1
     for (int it = 0, t = int(blockIdx.x); t < a.ntiles; ++it, t += G) {
-        const int b = it & 1;
-        cp_wait1();        // this thread's copies of tile t are done
+        const int b = NBUF == 1 ? 0 : (it & 1);
+        if constexpr (NBUF == 1) cp_wait0(); else cp_wait1();   // this thread's copies of tile t
         __syncthreads();   // everyone's
         warp_tile<N>(a, (t % a.ntx) * WTX, (t / a.ntx) * WTY, smem_raw + b * L::BUFB,
                      seta0 + b * L::SH * L::SW, rec, halo);
         bulk_wait_read();  // this thread's bulk output copies have left buffer b
         __syncthreads();   // buffer b, records and halo faces free
-        const int tn = t + 2 * G;
+        const int tn = t + NBUF * G;
         if (tn < a.ntiles)
             warp_stage<N>(a, (tn % a.ntx) * WTX, (tn / a.ntx) * WTY, smem_raw + b * L::BUFB,
                           seta0 + b * L::SH * L::SW);
@@ -720,10 +753,10 @@ int sm_count() {
     return cached[dev];
 }
 
-template <int N>
-void warp_apply_n(const OpGeom& g, const float* x, float* y, const float* eta, float alpha,
-                  const float* z, float beta, cudaStream_t s) {
-    using L = WarpLayout<N>;
+template <int N, int NBUF>
+void warp_apply_nb(const OpGeom& g, const float* x, float* y, const float* eta, float alpha,
+                   const float* z, float beta, const unsigned char* skip, cudaStream_t s) {
+    using L = WarpLayout<N, NBUF>;
     WarpArgs a;
     a.c = make_elem_args<float>(g, nullptr, nullptr, nullptr, alpha, nullptr, beta);
     a.x = x;
@@ -734,30 +767,41 @@ void warp_apply_n(const OpGeom& g, const float* x, float* y, const float* eta, f
     a.ntx = (g.nx + WTX - 1) / WTX;
     a.ntiles = a.ntx * ((g.ny + WTY - 1) / WTY);
     a.bulk = (alpha == 1.f && z == nullptr) ? 1 : 0;
+    a.skip = skip;
     static const bool attr = [] {   // once per process, thread-safe
-        SIP_CUDA(cudaFuncSetAttribute(k_apply_warp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(L::BYTES)));
+        SIP_CUDA(cudaFuncSetAttribute(k_apply_warp<N, NBUF>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES)));
         return true;
     }();
     (void)attr;
     const int grid = std::min(a.ntiles, L::MINB * sm_count());
-    launch_k(k_apply_warp<N>, dim3(unsigned(grid)), dim3(WNT), size_t(L::BYTES), s, a);
+    launch_k(k_apply_warp<N, NBUF>, dim3(unsigned(grid)), dim3(WNT), size_t(L::BYTES), s, a);
     SIP_CHECK_LAUNCH();
+}
+
+// One stage buffer and three CTAs per SM where shared memory admits them:
+// with the loads of one CTA overlapping the arithmetic of the others this
+// measured as fast as a double buffer with two CTAs per SM, or faster (k = 3).
+template <int N>
+void warp_apply_n(const OpGeom& g, const float* x, float* y, const float* eta, float alpha,
+                  const float* z, float beta, const unsigned char* skip, cudaStream_t s) {
+    warp_apply_nb<N, 1>(g, x, y, eta, alpha, z, beta, skip, s);
 }
 
 }  // namespace
 
 bool launch_apply_sip_warp(int N, const OpGeom& g, const float* x, float* y, const float* eta,
-                           float alpha, const float* z, float beta, cudaStream_t s) {
-    if (g.n_hi > 0) return false;   // split precision: the staged kernel's two launches
+                           float alpha, const float* z, float beta, const unsigned char* skip,
+                           cudaStream_t s) {
+    if (g.n_hi > 0 && !skip) return false;   // split precision: this launch needs the flags
     if (!aligned16(x) || !aligned16(y) || (z && !aligned16(z))) return false;
     if (g.nx < 1 || g.ny < 1) return false;
     switch (N) {
-        case 2: warp_apply_n<2>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 3: warp_apply_n<3>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 4: warp_apply_n<4>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 5: warp_apply_n<5>(g, x, y, eta, alpha, z, beta, s); return true;
-        case 6: warp_apply_n<6>(g, x, y, eta, alpha, z, beta, s); return true;
+        case 2: warp_apply_n<2>(g, x, y, eta, alpha, z, beta, skip, s); return true;
+        case 3: warp_apply_n<3>(g, x, y, eta, alpha, z, beta, skip, s); return true;
+        case 4: warp_apply_n<4>(g, x, y, eta, alpha, z, beta, skip, s); return true;
+        case 5: warp_apply_n<5>(g, x, y, eta, alpha, z, beta, skip, s); return true;
+        case 6: warp_apply_n<6>(g, x, y, eta, alpha, z, beta, skip, s); return true;
         default: return false;
     }
 }

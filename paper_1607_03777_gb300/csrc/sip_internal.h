@@ -204,10 +204,13 @@ bool launch_apply_sip_elem(int N, const OpGeom& g, const T* x, T* y, const T* et
 template <typename T>
 bool launch_apply_sip_stage(int N, const OpGeom& g, const T* x, T* y, const T* eta, T alpha,
                             const T* z, T beta, T* r1, cudaStream_t s);
-// Warp-row FP32 apply (N <= 6, 16-byte aligned vectors, no split-precision
-// tiles; returns false otherwise): y = alpha A x + beta z, z may equal y.
+// Warp-row FP32 apply (N <= 6, 16-byte aligned vectors; returns false
+// otherwise): y = alpha A x + beta z, z may equal y.  skip (split-precision
+// tile flags, 32 x 2 tiles): rows of flagged tiles are left to the FP64
+// launch; without it an operator with split-precision tiles is refused.
 bool launch_apply_sip_warp(int N, const OpGeom& g, const float* x, float* y, const float* eta,
-                           float alpha, const float* z, float beta, cudaStream_t s);
+                           float alpha, const float* z, float beta, const unsigned char* skip,
+                           cudaStream_t s);
 // Number of split-precision tiles of an nx x ny mesh, and their flags: tile
 // t is flagged (and listed) when an element of the tile or of its halo has
 // eta >= ratio x min(eta).  scratch: 32 device bytes.  Returns the count
