@@ -414,7 +414,7 @@ def kernel_name(code, k, word):
     n, t = k + 1, "double" if word == 8 else "float"
     return {1: f"k_apply_elem2<{n},{t},1>", 2: f"k_apply_elem<{n},{t}>",
             3: f"k_apply_sip<{n},{t}>", 4: f"k_apply_stage<{n},{t},{t},2,1,0>",
-            5: f"k_apply_stage<{n},{t},{t},4,1,0>"}.get(code, f"code {code}")
+            5: f"k_apply_stage<{n},{t},{t},4,1,0>", 6: f"k_apply_warp<{n},{t}>"}.get(code, f"code {code}")
 
 
 def measured_alu_peaks(dev):

@@ -326,7 +326,7 @@ __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int 
         for (int q = 0; q < N; ++q) Dm[p * N + q] = T(kT<N>.D[p][q]);
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
-        T PQ[2][2][N];   // [face lo/hi][P/Q][m]
+        T P[2][N], Q[2][N];   // [face lo/hi][m]
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int F = 2 * dir + side;
@@ -356,31 +356,17 @@ __device__ __forceinline__ void elem2_phase_b(const ElemArgs<T>& a, int ex, int 
             const T sigma = pen * eta_e * (kind == 0 ? T(1) : T(2));
             const T s = side == 0 ? T(-1) : T(1);
             const FaceGeo<T>& fg = dir == 0 ? a.fgx : a.fgy;
+            if (kind == 0) {
+                face_interior_comp<N, T, C>(dir, side, fg, pen, etaK, etaN, own, nbr, P[side],
+                                            Q[side]);
+            } else {
 #pragma unroll
-            for (int m = 0; m < N; ++m) {
-                T P, Q;
-                face_pq<N, T>(kind, C, m, dir, s, fg, etaK, etaN, sigma, own, own + 2 * N, nbr,
-                              nbr + 2 * N, Dm, P, Q);
-                PQ[side][0][m] = P;
-                PQ[side][1][m] = Q;
+                for (int m = 0; m < N; ++m)
+                    face_pq<N, T>(kind, C, m, dir, s, fg, etaK, etaN, sigma, own, own + 2 * N, nbr,
+                                  nbr + 2 * N, Dm, P[side][m], Q[side][m]);
             }
         }
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const T pp = PQ[1][0][m] + PQ[0][0][m];
-            const T pm = PQ[1][0][m] - PQ[0][0][m];
-            const T qp = PQ[1][1][m] + PQ[0][1][m];
-            const T qm = PQ[1][1][m] - PQ[0][1][m];
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                T add = q % 2 == 0 ? T(kT<N>.lp[q]) * pp : T(kT<N>.lp[q]) * pm;
-                if (q > 0) add += q % 2 == 0 ? T(kT<N>.dp[q]) * qm : T(kT<N>.dp[q]) * qp;
-                if (dir == 0)
-                    y[m][q] += add;
-                else
-                    y[q][m] += add;
-            }
-        }
+        spread_faces<N, T>(dir, P, Q, y);
     }
     const T* zz = a.z ? a.z + (size_t(ey) * nx + ex) * NB + C * N * N : nullptr;
     if (a.r1) {   // residual restricted to the Q^2_1 modes (p-transfer R = P^T)

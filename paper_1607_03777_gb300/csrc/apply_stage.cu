@@ -172,7 +172,7 @@ __device__ __forceinline__ void stage_phase_b(const StageArgs<TS, TC>& a, int ex
         for (int q = 0; q < N; ++q) Dm[p * N + q] = TC(kT<N>.D[p][q]);
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
-        TC PQ[2][2][N];   // [face lo/hi][P/Q][m]
+        TC P[2][N], Q[2][N];   // [face lo/hi][m]
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int F = 2 * dir + side;
@@ -201,32 +201,17 @@ __device__ __forceinline__ void stage_phase_b(const StageArgs<TS, TC>& a, int ex
             const TC sigma = pen * eta_e * (kind == 0 ? TC(1) : TC(2));
             const TC s = side == 0 ? TC(-1) : TC(1);
             const FaceGeo<TC>& fg = dir == 0 ? a.c.fgx : a.c.fgy;
+            if (kind == 0) {
+                face_interior_comp<N, TC, C>(dir, side, fg, pen, etaK, etaN, own, nbr, P[side],
+                                             Q[side]);
+            } else {
 #pragma unroll
-            for (int m = 0; m < N; ++m) {
-                TC P, Q;
-                face_pq<N, TC>(kind, C, m, dir, s, fg, etaK, etaN, sigma, own, own + 2 * N, nbr,
-                               nbr + 2 * N, Dm, P, Q);
-                PQ[side][0][m] = P;
-                PQ[side][1][m] = Q;
+                for (int m = 0; m < N; ++m)
+                    face_pq<N, TC>(kind, C, m, dir, s, fg, etaK, etaN, sigma, own, own + 2 * N,
+                                   nbr, nbr + 2 * N, Dm, P[side][m], Q[side][m]);
             }
         }
-        // spread: test mode q along the normal, m along the face
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const TC pp = PQ[1][0][m] + PQ[0][0][m];
-            const TC pm = PQ[1][0][m] - PQ[0][0][m];
-            const TC qp = PQ[1][1][m] + PQ[0][1][m];
-            const TC qm = PQ[1][1][m] - PQ[0][1][m];
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                TC add = q % 2 == 0 ? TC(kT<N>.lp[q]) * pp : TC(kT<N>.lp[q]) * pm;
-                if (q > 0) add += q % 2 == 0 ? TC(kT<N>.dp[q]) * qm : TC(kT<N>.dp[q]) * qp;
-                if (dir == 0)
-                    y[m][q] += add;
-                else
-                    y[q][m] += add;
-            }
-        }
+        spread_faces<N, TC>(dir, P, Q, y);
     }
     if (a.r1) {   // residual restricted to the Q^2_1 modes (p-transfer R = P^T)
         const TS* zz = a.z ? a.z + (size_t(ey) * nx + ex) * NB + C * N * N : nullptr;

@@ -360,60 +360,6 @@ __device__ __forceinline__ void volume_comp(const ElemArgs<float>& a, const floa
     }
 }
 
-// Face vectors P, Q (both components, every tangential mode m) of one
-// interior face of K with normal direction DIR on side SIDE (0: minus, 1:
-// plus): the interior case of face_pq with its scalar factors gathered per
-// face, no branches.  own / nbr: trace records [val c0 | val c1 | der c0 |
-// der c1] of K and of the neighbour.
-template <int N, int DIR, int SIDE>
-__device__ __forceinline__ void face_interior(const FaceGeo<float>& fg, float pen, float etaK,
-                                              float etaN, const float (&own)[4 * N],
-                                              const float (&nbr)[4 * N], float (&P)[2][N],
-                                              float (&Q)[2][N]) {
-    constexpr int nc = DIR, tc = 1 - DIR;   // normal / tangential component
-    constexpr float s = SIDE ? 1.f : -1.f;
-    const float sigma = pen * fmaxf(etaK, etaN);
-    const float kA = -s * fg.half_ht * etaK, kB = -s * fg.half_ht * etaN;
-    const float kA2 = 0.5f * kA, kB2 = 0.5f * kB;
-    const float kC = -0.5f * s * etaK, kF = -0.5f * s * etaN;
-    const float kP = sigma * fg.half_ht;
-    const float kQn = -s * etaK * fg.ht_over_hn, kQt = -s * etaK * fg.half_ht_over_hn;
-    float w[2][N];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int m = 0; m < N; ++m) w[c][m] = own[c * N + m] - nbr[c * N + m];
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-        // normal component: flux of the normal derivative, symmetry term
-        // through the tangential derivative of the jump, penalty
-        float dtw = 0.f;
-#pragma unroll
-        for (int mm = 0; mm < N; ++mm)
-            if (kT<N>.D[mm][m] != 0.0) dtw = fmaf(float(kT<N>.D[mm][m]), w[tc][mm], dtw);
-        float p = kA * own[2 * N + nc * N + m];
-        p = fmaf(kB, nbr[2 * N + nc * N + m], p);
-        p = fmaf(kC, dtw, p);
-        P[nc][m] = fmaf(kP, w[nc][m], p);
-        Q[nc][m] = kQn * w[nc][m];
-        // tangential component: shear flux with the tangential derivative of
-        // the normal component on both sides, penalty
-        float svo = 0.f, svn = 0.f;
-#pragma unroll
-        for (int mm = 0; mm < N; ++mm)
-            if (kT<N>.D[m][mm] != 0.0) {
-                svo = fmaf(float(kT<N>.D[m][mm]), own[nc * N + mm], svo);
-                svn = fmaf(float(kT<N>.D[m][mm]), nbr[nc * N + mm], svn);
-            }
-        float t = kA2 * own[2 * N + tc * N + m];
-        t = fmaf(kB2, nbr[2 * N + tc * N + m], t);
-        t = fmaf(kC, svo, t);
-        t = fmaf(kF, svn, t);
-        P[tc][m] = fmaf(kP, w[tc][m], t);
-        Q[tc][m] = kQt * w[tc][m];
-    }
-}
-
 // Face vectors of one face of K with normal direction DIR on side `side`,
 // any kind (face_pq): the case of boundary faces and ragged tiles.
 template <int N, int DIR>
@@ -452,18 +398,18 @@ __device__ __forceinline__ void flux_dir(const ElemArgs<float>& a, bool nb_lo, b
                                          float (&y)[2][N][N]) {
     const FaceGeo<float>& fg = DIR == 0 ? a.fgx : a.fgy;
     const float pen = DIR == 0 ? a.pen_x : a.pen_y;
-    float P[2][2][N], Q[2][2][N];   // [side][comp][m]
+    float P[2][2][N], Q[2][2][N];   // [comp][side][m]
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         const bool nb = side == 0 ? nb_lo : nb_hi;
         const float etaN = side == 0 ? eta_lo : eta_hi;
         const float(&own)[4 * N] = side == 0 ? own_lo : own_hi;
         const float(&nbr)[4 * N] = side == 0 ? nbr_lo : nbr_hi;
-        if (__all_sync(FULL, nb)) {
-            if (side == 0)
-                face_interior<N, DIR, 0>(fg, pen, etaK, etaN, own, nbr, P[0], Q[0]);
-            else
-                face_interior<N, DIR, 1>(fg, pen, etaK, etaN, own, nbr, P[1], Q[1]);
+        if (__all_sync(FULL, nb)) {   // every lane of the warp is active here
+            face_interior_comp<N, float, 0>(DIR, side, fg, pen, etaK, etaN, own, nbr, P[0][side],
+                                            Q[0][side]);
+            face_interior_comp<N, float, 1>(DIR, side, fg, pen, etaK, etaN, own, nbr, P[1][side],
+                                            Q[1][side]);
         } else {
             float tp[2 * N], tq[2 * N];
             face_general<N, DIR>(a, side, nb, etaK, etaN, own, nbr, tp, tq);
@@ -471,26 +417,13 @@ __device__ __forceinline__ void flux_dir(const ElemArgs<float>& a, bool nb_lo, b
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int m = 0; m < N; ++m) {
-                    P[side][c][m] = tp[c * N + m];
-                    Q[side][c][m] = tq[c * N + m];
+                    P[c][side][m] = tp[c * N + m];
+                    Q[c][side][m] = tq[c * N + m];
                 }
         }
     }
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const float pp = P[1][c][m] + P[0][c][m];
-            const float pm = P[1][c][m] - P[0][c][m];
-            const float qp = Q[1][c][m] + Q[0][c][m];
-            const float qm = Q[1][c][m] - Q[0][c][m];
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                float& yy = DIR == 0 ? y[c][m][q] : y[c][q][m];
-                yy = fmaf(float(kT<N>.lp[q]), q % 2 == 0 ? pp : pm, yy);
-                if (q > 0) yy = fmaf(float(kT<N>.dp[q]), q % 2 == 0 ? qm : qp, yy);
-            }
-        }
+    spread_faces<N, float>(DIR, P[0], Q[0], y[0]);
+    spread_faces<N, float>(DIR, P[1], Q[1], y[1]);
 }
 
 template <int N>

@@ -119,6 +119,92 @@ constexpr CTabs<N> build_ctabs() {
 template <int N>
 __device__ constexpr CTabs<N> kT = build_ctabs<N>();
 
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
+// Face vectors P, Q of test component C (every tangential mode m) for one
+// interior face of K with normal direction dir on side `side` (0: minus, 1:
+// plus): the interior case of face_pq with its scalar factors gathered per
+// face, no branches on the face kind.  own / nbr: trace records [val c0 |
+// val c1 | der c0 | der c1] (N each) of K and of the neighbour.
+template <int N, typename T, int C>
+__device__ __forceinline__ void face_interior_comp(int dir, int side, const FaceGeo<T>& fg, T pen,
+                                                   T etaK, T etaN, const T* own, const T* nbr,
+                                                   T* P, T* Q) {
+    const int nc = dir, tc = 1 - dir;   // normal / tangential component
+    const T s = side ? T(1) : T(-1);
+    const T kP = pen * (etaK > etaN ? etaK : etaN) * fg.half_ht;
+    if (C == nc) {
+        // flux of the normal derivative, symmetry term through the tangential
+        // derivative of the jump, penalty
+        const T kA = -s * fg.half_ht * etaK, kB = -s * fg.half_ht * etaN;
+        const T kC = T(-0.5) * s * etaK, kQ = -s * etaK * fg.ht_over_hn;
+        T wt[N];
+#pragma unroll
+        for (int mm = 0; mm < N; ++mm) wt[mm] = own[tc * N + mm] - nbr[tc * N + mm];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            T dtw = T(0);
+#pragma unroll
+            for (int mm = 0; mm < N; ++mm)
+                if (kT<N>.D[mm][m] != 0.0) dtw = fmat(T(kT<N>.D[mm][m]), wt[mm], dtw);
+            const T wn = own[nc * N + m] - nbr[nc * N + m];
+            T p = kA * own[2 * N + nc * N + m];
+            p = fmat(kB, nbr[2 * N + nc * N + m], p);
+            p = fmat(kC, dtw, p);
+            P[m] = fmat(kP, wn, p);
+            Q[m] = kQ * wn;
+        }
+    } else {
+        // shear flux with the tangential derivative of the normal component
+        // on both sides, penalty
+        const T kA2 = T(-0.5) * s * fg.half_ht * etaK, kB2 = T(-0.5) * s * fg.half_ht * etaN;
+        const T kC = T(-0.5) * s * etaK, kF = T(-0.5) * s * etaN;
+        const T kQ = -s * etaK * fg.half_ht_over_hn;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            T svo = T(0), svn = T(0);
+#pragma unroll
+            for (int mm = 0; mm < N; ++mm)
+                if (kT<N>.D[m][mm] != 0.0) {
+                    svo = fmat(T(kT<N>.D[m][mm]), own[nc * N + mm], svo);
+                    svn = fmat(T(kT<N>.D[m][mm]), nbr[nc * N + mm], svn);
+                }
+            const T wt = own[tc * N + m] - nbr[tc * N + m];
+            T t = kA2 * own[2 * N + tc * N + m];
+            t = fmat(kB2, nbr[2 * N + tc * N + m], t);
+            t = fmat(kC, svo, t);
+            t = fmat(kF, svn, t);
+            P[m] = fmat(kP, wt, t);
+            Q[m] = kQ * wt;
+        }
+    }
+}
+
+// Spread the face vectors of the two faces with normal direction dir into
+// one component's result: test mode q along the normal, m along the face;
+// the even / odd parts of l_q(+-1) and l_q'(+-1) combine the two faces.
+template <int N, typename T>
+__device__ __forceinline__ void spread_faces(int dir, const T (&P)[2][N], const T (&Q)[2][N],
+                                             T (&y)[N][N]) {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        const T pp = P[1][m] + P[0][m], pm = P[1][m] - P[0][m];
+        const T qp = Q[1][m] + Q[0][m], qm = Q[1][m] - Q[0][m];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const T a = q % 2 == 0 ? pp : pm, b = q % 2 == 0 ? qm : qp;
+            if (dir == 0) {
+                y[m][q] = fmat(T(kT<N>.lp[q]), a, y[m][q]);
+                if (q > 0) y[m][q] = fmat(T(kT<N>.dp[q]), b, y[m][q]);
+            } else {
+                y[q][m] = fmat(T(kT<N>.lp[q]), a, y[q][m]);
+                if (q > 0) y[q][m] = fmat(T(kT<N>.dp[q]), b, y[q][m]);
+            }
+        }
+    }
+}
+
 constexpr int TX = 32, TY = 2, TXY = TX * TY;
 constexpr int NHALO = 2 * TX + 2 * TY;
 
@@ -129,6 +215,9 @@ template <int N, typename T>
 __device__ __forceinline__ void face_traces(const T (&u)[2][N][N], int F, T two_over_h,
                                             T* out /* [2][2][N] */) {
     const bool plus = (F & 1) != 0;
+    T dps[N];   // l_q'(+1) times 2 / h: physical derivative
+#pragma unroll
+    for (int q = 0; q < N; ++q) dps[q] = T(kT<N>.dp[q]) * two_over_h;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -138,16 +227,16 @@ __device__ __forceinline__ void face_traces(const T (&u)[2][N][N], int F, T two_
             for (int q = 0; q < N; ++q) {
                 const T uq = F < 2 ? u[c][m][q] : u[c][q][m];   // q along the normal
                 if (q % 2 == 0) {
-                    ev += T(kT<N>.lp[q]) * uq;
-                    if (q > 0) evd += T(kT<N>.dp[q]) * uq;
+                    ev = fmat(T(kT<N>.lp[q]), uq, ev);
+                    if (q > 0) evd = fmat(dps[q], uq, evd);
                 } else {
-                    od += T(kT<N>.lp[q]) * uq;
-                    odd += T(kT<N>.dp[q]) * uq;
+                    od = fmat(T(kT<N>.lp[q]), uq, od);
+                    odd = fmat(dps[q], uq, odd);
                 }
             }
             // l_q(-1) = (-1)^q l_q(1),  l_q'(-1) = -(-1)^q l_q'(1)
             out[0 * 2 * N + c * N + m] = plus ? ev + od : ev - od;
-            out[1 * 2 * N + c * N + m] = (plus ? evd + odd : odd - evd) * two_over_h;
+            out[1 * 2 * N + c * N + m] = plus ? evd + odd : odd - evd;
         }
 }
 
@@ -156,6 +245,9 @@ template <int N, typename T>
 __device__ __forceinline__ void face_traces_comp(const T (&u)[2][N][N], int F, int c,
                                                  T two_over_h, T* out /* [2][2][N] */) {
     const bool plus = (F & 1) != 0;
+    T dps[N];   // l_q'(+1) times 2 / h: physical derivative
+#pragma unroll
+    for (int q = 0; q < N; ++q) dps[q] = T(kT<N>.dp[q]) * two_over_h;
 #pragma unroll
     for (int m = 0; m < N; ++m) {
         T ev = T(0), od = T(0), evd = T(0), odd = T(0);
@@ -163,15 +255,15 @@ __device__ __forceinline__ void face_traces_comp(const T (&u)[2][N][N], int F, i
         for (int q = 0; q < N; ++q) {
             const T uq = F < 2 ? u[c][m][q] : u[c][q][m];
             if (q % 2 == 0) {
-                ev += T(kT<N>.lp[q]) * uq;
-                if (q > 0) evd += T(kT<N>.dp[q]) * uq;
+                ev = fmat(T(kT<N>.lp[q]), uq, ev);
+                if (q > 0) evd = fmat(dps[q], uq, evd);
             } else {
-                od += T(kT<N>.lp[q]) * uq;
-                odd += T(kT<N>.dp[q]) * uq;
+                od = fmat(T(kT<N>.lp[q]), uq, od);
+                odd = fmat(dps[q], uq, odd);
             }
         }
         out[0 * 2 * N + c * N + m] = plus ? ev + od : ev - od;
-        out[1 * 2 * N + c * N + m] = (plus ? evd + odd : odd - evd) * two_over_h;
+        out[1 * 2 * N + c * N + m] = plus ? evd + odd : odd - evd;
     }
 }
 
@@ -209,32 +301,41 @@ __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)
 #pragma unroll
     for (int F = 0; F < 4; ++F)
         face_traces_comp<N, T>(u, F, C, F < 2 ? a.two_over_hx : a.two_over_hy, tr + F * 4 * N);
-    const T sx = C == 0 ? a.c2hy_hx : a.chy_hx;   // weight of G along x on u_C
-    const T sy = C == 0 ? a.chx_hy : a.c2hx_hy;   // weight of G along y on u_C
+    const T sx = etaK * (C == 0 ? a.c2hy_hx : a.chy_hx);   // weight of G along x on u_C
+    const T sy = etaK * (C == 0 ? a.chx_hy : a.c2hx_hy);   // weight of G along y on u_C
+    T Gx[N][N], Gy[N][N], De[N][N];   // scaled tables (zero entries never read)
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            Gx[p][q] = kT<N>.G[p][q] != 0.0 ? sx * T(kT<N>.G[p][q]) : T(0);
+            Gy[p][q] = kT<N>.G[p][q] != 0.0 ? sy * T(kT<N>.G[p][q]) : T(0);
+            De[p][q] = kT<N>.D[p][q] != 0.0 ? etaK * T(kT<N>.D[p][q]) : T(0);
+        }
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int av = 0; av < N; ++av) {
-            T gx = T(0), gy = T(0);
+            T acc = T(0);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                if (kT<N>.G[av][i] != 0.0) gx += T(kT<N>.G[av][i]) * u[C][b][i];
-                if (kT<N>.G[b][i] != 0.0) gy += T(kT<N>.G[b][i]) * u[C][i][av];
+                if (kT<N>.G[av][i] != 0.0) acc = fmat(Gx[av][i], u[C][b][i], acc);
+                if (kT<N>.G[b][i] != 0.0) acc = fmat(Gy[b][i], u[C][i][av], acc);
             }
-            y[b][av] = sx * gx + sy * gy;
+            y[b][av] = acc;
         }
     T w[N][N];
     if (C == 0) {
-        // y_x[b][a] += sum_j D[j][b] sum_i D[a][i] u_y[j][i]
+        // y_x[b][a] += eta_K sum_j D[j][b] sum_i D[a][i] u_y[j][i]
 #pragma unroll
         for (int j = 0; j < N; ++j)
 #pragma unroll
             for (int av = 0; av < N; ++av) {
-                T s = T(0);
+                T t = T(0);
 #pragma unroll
                 for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[av][i] != 0.0) s += T(kT<N>.D[av][i]) * u[1][j][i];
-                w[j][av] = s;
+                    if (kT<N>.D[av][i] != 0.0) t = fmat(T(kT<N>.D[av][i]), u[1][j][i], t);
+                w[j][av] = t;
             }
 #pragma unroll
         for (int b = 0; b < N; ++b)
@@ -242,18 +343,18 @@ __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)
             for (int av = 0; av < N; ++av)
 #pragma unroll
                 for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[j][b] != 0.0) y[b][av] += T(kT<N>.D[j][b]) * w[j][av];
+                    if (kT<N>.D[j][b] != 0.0) y[b][av] = fmat(De[j][b], w[j][av], y[b][av]);
     } else {
-        // y_y[b][a] += sum_i D[i][a] sum_j D[b][j] u_x[j][i]
+        // y_y[b][a] += eta_K sum_i D[i][a] sum_j D[b][j] u_x[j][i]
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                T s = T(0);
+                T t = T(0);
 #pragma unroll
                 for (int j = 0; j < N; ++j)
-                    if (kT<N>.D[b][j] != 0.0) s += T(kT<N>.D[b][j]) * u[0][j][i];
-                w[b][i] = s;
+                    if (kT<N>.D[b][j] != 0.0) t = fmat(T(kT<N>.D[b][j]), u[0][j][i], t);
+                w[b][i] = t;
             }
 #pragma unroll
         for (int b = 0; b < N; ++b)
@@ -261,12 +362,8 @@ __device__ __forceinline__ void elem2_phase_a(const ElemArgs<T>& a, const T (&u)
             for (int av = 0; av < N; ++av)
 #pragma unroll
                 for (int i = 0; i < N; ++i)
-                    if (kT<N>.D[i][av] != 0.0) y[b][av] += T(kT<N>.D[i][av]) * w[b][i];
+                    if (kT<N>.D[i][av] != 0.0) y[b][av] = fmat(De[i][av], w[b][i], y[b][av]);
     }
-#pragma unroll
-    for (int b = 0; b < N; ++b)
-#pragma unroll
-        for (int av = 0; av < N; ++av) y[b][av] *= etaK;
 }
 
 
