@@ -110,49 +110,47 @@ __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Byte offset of staged element j (0 = the left neighbour column) in the row
-// buffer of mesh row ey (odd N: the row's shift of 0 or 8 bytes).
+// buffer of mesh row ey (odd N: the row's shift of 0 or 8 bytes, from the
+// parity of the row's first staged element ey nx + ex0 - 1).
 template <int N>
-__device__ __forceinline__ int elem_off(long long ey, int nx, int ex0, int j) {
+__device__ __forceinline__ int elem_off(int ey, int nx, int ex0, int j) {
     using L = WarpLayout<N>;
     if constexpr (L::PAD) {
         return j * L::SLOT;
     } else {
-        const long long anchor = ey * nx + ex0 - 1;   // element index, may be -1
-        return int(anchor & 1) * 8 + j * L::EB;        // EB = 8 mod 16
+        return (((ey & nx) ^ (ex0 - 1)) & 1) * 8 + j * L::EB;   // EB = 8 mod 16
     }
 }
 
 // Issue the copies of tile (ex0, ey0) into one stage buffer.  Stage row r is
-// mesh row ey0 - 1 + r; the first and last rows hold only the 32 elements
-// below / above the tile; corners and elements outside the mesh are not
-// copied (and never read).  Each half of a stage row goes to one warp (three
-// halves per warp): the row's set-up once per warp, the chunk loop unrolled
-// with immediate offsets.
+// mesh row ey0 - 1 + r and holds its elements ex0 - 1 .. ex0 + 32 that lie in
+// the mesh (the corners of the first and last rows are copied but never
+// read; rows outside the mesh are not copied and never read).  Each half of
+// a stage row, with its viscosities, goes to one warp (three halves per
+// warp); the chunk loops are unrolled with immediate offsets.
 template <int N>
 __device__ __forceinline__ void warp_stage(const WarpArgs& a, int ex0, int ey0,
                                            unsigned char* buf, float* seta) {
     using L = WarpLayout<N>;
     static_assert((2 * L::SH) % WTY == 0, "stage half-rows split evenly over the warps");
+    static_assert(L::SW % 2 == 0 && L::SW / 2 <= 32, "one viscosity per lane and half-row");
     const int nx = a.c.nx, ny = a.c.ny;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int q = threadIdx.x; q < L::SH * L::SW; q += WNT) {
-        const int r = q / L::SW, c = q - r * L::SW;
-        const int ey = ey0 - 1 + r, ex = ex0 - 1 + c;
-        const bool in = ey >= 0 && ey < ny && ex >= 0 && ex < nx;
-        cp_async4z(smem_u32(seta + q), in ? a.eta + (size_t(ey) * nx + ex) : a.eta, in ? 4 : 0);
-    }
+    const int elo = max(ex0 - 1, 0), ehi = min(ex0 + WTX + 1, nx);   // every stage row
     const unsigned sbuf = smem_u32(buf);
     const char* xb = reinterpret_cast<const char*>(a.x);
 #pragma unroll 1
     for (int hr = warp; hr < 2 * L::SH; hr += WTY) {
         const int r = hr >> 1, half = hr & 1;
         const int ey = ey0 - 1 + r;
-        if (ey < 0 || ey >= ny) continue;   // uniform over the warp
-        const bool edge = r == 0 || r == L::SH - 1;
-        const int elo = edge ? ex0 : max(ex0 - 1, 0);
-        const int ehi = edge ? min(ex0 + WTX, nx) : min(ex0 + WTX + 1, nx);
-        if (elo >= ehi) continue;
+        const bool row_in = ey >= 0 && ey < ny;   // uniform over the warp
         const long long row = (long long)ey * nx;
+        if (lane < L::SW / 2) {   // viscosities of stage columns half * SW / 2 + lane
+            const int c = half * (L::SW / 2) + lane, ex = ex0 - 1 + c;
+            const bool in = row_in && ex >= 0 && ex < nx;
+            cp_async4z(smem_u32(seta + r * L::SW + c), in ? a.eta + (row + ex) : a.eta, in ? 4 : 0);
+        }
+        if (!row_in) continue;
         const unsigned srow = sbuf + r * L::ROWB;
         if constexpr (L::PAD) {
             // whole element slots, the row's elements split into two halves
