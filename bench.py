@@ -414,7 +414,7 @@ def kernel_name(code, k, word):
     n, t = k + 1, "double" if word == 8 else "float"
     return {1: f"k_apply_elem2<{n},{t},1>", 2: f"k_apply_elem<{n},{t}>",
             3: f"k_apply_sip<{n},{t}>", 4: f"k_apply_stage<{n},{t},{t},2,1,0>",
-            5: f"k_apply_stage<{n},{t},{t},4,1,0>", 6: f"k_apply_warp<{n},{t}>"}.get(code, f"code {code}")
+            5: f"k_apply_stage<{n},{t},{t},4,1,0>", 6: f"k_apply_warp<{n},1>"}.get(code, f"code {code}")
 
 
 def measured_alu_peaks(dev):
@@ -496,7 +496,9 @@ def apply_f32_rooflines(ctx, dev, flush, stream, peaks):
         ms = time_launches(lambda: pr.apply_A_f32(x, y, stream=stream), flush, stream)
         ab, af = algorithmic_apply(k, n * n, 4)
         code = pr.schedule()["apply"][1]
-        out.append({"elements": f"{n}x{n}", "k": k, "kernel": kernel_name(code, k, 4),
+        kernel = kernel_name(code, k, 4)
+        out.append({"elements": f"{n}x{n}", "k": k, "kernel": kernel,
+                    "traffic": captured_traffic(kernel),
                     "ms": ms, "GB_per_s": ab / ms / 1e6, "hbm_frac": ab / ms / 1e6 / hbm,
                     "TFLOP_per_s": af / ms / 1e9, "fp32_frac": af / ms / 1e9 / peaks["fp32"],
                     "algorithmic_bytes": ab, "algorithmic_flops": af,
@@ -507,11 +509,15 @@ def apply_f32_rooflines(ctx, dev, flush, stream, peaks):
     return out
 
 
-# committed ncu summaries of the FP64 apply kernels on the 128^2, k = 3 workload
+# committed ncu summaries: the FP64 apply kernels on the 128^2, k = 3 workload and the
+# FP32 warp-row apply on 512^2
 TRAFFIC_PROFILES = {
     "k_apply_elem2<4,double,1>": os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md"),
     "k_apply_stage<4,double,double,4,1,0>": os.path.join(
         ROOT, "profiles", "k_apply_stage4_fp64_128x128_k3.md"),
+    # the warp-row FP32 apply on the 512^2 meshes of sip_apply_f32
+    "k_apply_warp<4,1>": os.path.join(ROOT, "profiles", "k_apply_warp_fp32_512x512_k3.md"),
+    "k_apply_warp<5,1>": os.path.join(ROOT, "profiles", "k_apply_warp_fp32_512x512_k4.md"),
 }
 
 
