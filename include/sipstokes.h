@@ -284,7 +284,10 @@ typedef struct {
                          *    double-double) or when a step fails to halve ||r||. *
                          *    Reaches residuals below FP64's attainable accuracy   *
                          *    for high viscosity contrasts, in place of the        *
-                         *    paper's quadruple precision (Sec. 7.4).             */
+                         *    paper's quadruple precision (Sec. 7.4).  sip_solve   *
+                         *    returns the iterate rounded to FP64, whose residual  *
+                         *    can lie above rtol at such contrasts; sip_solve_dd   *
+                         *    returns the double-double iterate itself.            */
     double time_limit_ms;  /* 0 (default): none.  > 0: wall-clock limit of the  *
                             *    solve (sip_solve, sip_solve_batch: from the    *
                             *    call; served requests: from submission).  It   *
@@ -343,6 +346,21 @@ sip_status sip_solve(sip_problem* prob, const double* f_u, const double* g_p, do
 sip_status sip_residual_dd(sip_problem* prob, const double* f_u, const double* g_p,
                            const double* x_u, const double* x_p, double* r_u, double* r_p,
                            void* stream);
+
+/* The refined solve of sip_solve (opts->refine > 0, required) returning its
+ * double-double iterate (Sec. 7.4 solves high-contrast problems in quadruple
+ * precision; the iterate of the refinement carries about 106 bits): u_dd, p_dd
+ * are 2 n_u / 2 n_p doubles of interleaved (hi, lo) pairs, value = hi + lo,
+ * caller-owned device buffers, the layout sip_residual_dd reads.  The
+ * relative residual the report gives (and that rtol bounds) is that of this
+ * iterate; rounded to FP64 (what sip_solve returns) it can lie above rtol
+ * when ||K|| eps_64 ||x|| > rtol ||b|| (viscosity contrasts of 1e6 and more).
+ * Without a Neumann face the pressure is fixed only up to a constant (the
+ * FP64 outputs of sip_solve have zero mean).  Errors as sip_solve, and
+ * INVALID_ARG without refinement. */
+sip_status sip_solve_dd(sip_problem* prob, const double* f_u, const double* g_p, double* u_dd,
+                        double* p_dd, const sip_solve_opts* opts, sip_solve_report* report,
+                        void* stream);
 
 /* ---- batches and serving ----------------------------------------------------
  * Not in the paper (it solves one problem at a time on one CPU core): many

@@ -116,6 +116,8 @@ SIGNATURES = {
     "sip_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "sip_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveReport), _VP]),
+    "sip_solve_dd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(SolveOpts),
+                                    ctypes.POINTER(SolveReport), _VP]),
     "sip_solve_batch": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                        ctypes.POINTER(SolveOpts), _VP, ctypes.c_int]),
     "sip_solve_batch_grouped": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,

@@ -272,6 +272,30 @@ class Problem:
         out["status"] = st
         return out
 
+    def solve_dd(self, f, u_dd, p_dd, g=None, rtol=1e-8, max_outer=500, restart=100,
+                 inner_rtol=1e-3, max_inner=200, inner_loop="device", inner_krylov="auto",
+                 inner_norm="true", inner_restart=30, outer_krylov="fgmres", refine=4,
+                 time_limit_ms=0.0, stream=None, check=True):
+        """sip_solve_dd: the refined solve (``refine`` > 0) returning its
+        double-double iterate in ``u_dd``, ``p_dd`` (float64 tensors of
+        2 n_u / 2 n_p entries, (hi, lo) pairs); options and report as
+        ``solve``."""
+        for t, m in ((u_dd, self.n_u), (p_dd, self.n_p)):
+            if t.numel() != 2 * m:
+                raise ValueError("double-double vectors hold 2 doubles per entry")
+        o = _opts(self.ctx.lib, rtol, max_outer, restart, inner_rtol, max_inner, inner_loop,
+                  inner_krylov, inner_norm, inner_restart, outer_krylov, refine, time_limit_ms)
+        rep = SolveReport()
+        st = self.ctx.lib.sip_solve_dd(self.handle, _ptr(f, torch.float64),
+                                       _ptr(g, torch.float64) if g is not None else None,
+                                       _ptr(u_dd, torch.float64), _ptr(p_dd, torch.float64),
+                                       ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        out = {name: getattr(rep, name) for name, _ in SolveReport._fields_}
+        if check:
+            self.ctx.check(st)
+        out["status"] = st
+        return out
+
 
 # ---------------------------------------------------------------- batches, serving
 def make_desc(ctx, nx, ny, k, eta, bc=("navier",) * 4, lx=1.0, ly=1.0, penalty_scale=1.0,

@@ -568,6 +568,27 @@ sip_status sip_residual_dd(sip_problem* p, const double* f, const double* g, con
     });
 }
 
+sip_status sip_solve_dd(sip_problem* p, const double* f, const double* g, double* u_dd,
+                        double* p_dd, const sip_solve_opts* opts, sip_solve_report* rep,
+                        void* stream) {
+    if (!p) return SIP_ERR_INVALID_ARG;
+    sip_status st = SIP_OK;
+    const sip_status gst = guarded(p->ctx, [&] {
+        sip::require(f && u_dd && p_dd, "null vector");
+        sip::require(opts && opts->refine > 0, "sip_solve_dd needs opts->refine > 0");
+        const sip_solve_opts o = *opts;
+        sip::require_valid_opts(o, p->desc.precision);
+        SIP_CUDA(cudaSetDevice(p->ctx->device));
+        const sip::StopScope stop(o.time_limit_ms > 0.0 ? sip::steady_ms() + o.time_limit_ms : 0.0,
+                                  nullptr);
+        st = sip::run_solve_refined(p, f, g, nullptr, nullptr, o, rep, as_stream(stream), u_dd,
+                                    p_dd);
+        if (st != SIP_OK) throw Error(st, sip::status_message(st));
+    });
+    if (gst != SIP_OK && rep) rep->status = gst;
+    return gst;
+}
+
 sip_status sip_solve(sip_problem* p, const double* f, const double* g, double* u, double* pp,
                      const sip_solve_opts* opts, sip_solve_report* rep, void* stream) {
     if (!p) return SIP_ERR_INVALID_ARG;

@@ -258,9 +258,11 @@ void residual_dd(sip_problem* P, const double* f_u, const double* g_p, const dou
 // Iterative refinement (o.refine > 0): FP64 / mixed solves of K d = r for
 // the residual r = b - K x evaluated in double-double, x accumulated in
 // double-double, until the residual meets o.rtol or stops halving.
+// u, p (FP64, the iterate rounded) may be null; u_dd, p_dd (may be null)
+// receive the double-double iterate as interleaved (hi, lo) pairs.
 sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_p, double* u,
                              double* p, const sip_solve_opts& o, sip_solve_report* rep,
-                             cudaStream_t s);
+                             cudaStream_t s, double* u_dd = nullptr, double* p_dd = nullptr);
 
 // Throws Error(SIP_ERR_INVALID_ARG) unless the options are valid for a
 // problem of this precision (every solve entry point checks them).

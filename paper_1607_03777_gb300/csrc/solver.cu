@@ -1402,7 +1402,7 @@ void residual_dd(sip_problem* P, const double* f_u, const double* g_p, const dou
 
 sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_p, double* u_out,
                              double* p_out, const sip_solve_opts& o, sip_solve_report* rep,
-                             cudaStream_t s) {
+                             cudaStream_t s, double* u_dd, double* p_dd) {
     const double t_start = now_ms();
     const int64_t launches0 = launch_counter();
     const size_t n_u = size_t(P->n_u), n_p = size_t(P->n_p), n = n_u + n_p;
@@ -1476,8 +1476,16 @@ sip_status run_solve_refined(sip_problem* P, const double* f_u, const double* g_
     const bool singular = P->desc.bc[0] != SIP_BC_NEUMANN && P->desc.bc[1] != SIP_BC_NEUMANN &&
                           P->desc.bc[2] != SIP_BC_NEUMANN && P->desc.bc[3] != SIP_BC_NEUMANN;
     if (singular) launch_zero_mean_pressure(size_t(P->ne), P->mp, d64 + n_u, part, s);
-    SIP_CUDA(cudaMemcpyAsync(u_out, d64, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    SIP_CUDA(cudaMemcpyAsync(p_out, d64 + n_u, n_p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (u_out)
+        SIP_CUDA(cudaMemcpyAsync(u_out, d64, n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (p_out)
+        SIP_CUDA(cudaMemcpyAsync(p_out, d64 + n_u, n_p * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 s));
+    // the double-double iterate itself: its residual is the one tested above
+    static_assert(sizeof(dd) == 2 * sizeof(double), "(hi, lo) pairs");
+    if (u_dd) SIP_CUDA(cudaMemcpyAsync(u_dd, x, n_u * sizeof(dd), cudaMemcpyDeviceToDevice, s));
+    if (p_dd)
+        SIP_CUDA(cudaMemcpyAsync(p_dd, x + n_u, n_p * sizeof(dd), cudaMemcpyDeviceToDevice, s));
     SIP_CUDA(cudaStreamSynchronize(s));
     if (rep) {
         rep->status = st;
