@@ -410,7 +410,10 @@ sip_status sip_solve_batch_grouped(sip_ctx* ctx, int n, sip_problem* const* prob
 int64_t sip_problem_footprint(const sip_problem_desc* desc, int restart);
 /* A request server on ctx's device: at most max_slots solves in flight and
  * at most budget_bytes of estimated device footprint admitted at once.
- * Requests are admitted first in, first out as slots and memory free up. */
+ * Requests are admitted in arrival order as slots and memory free up; while
+ * the oldest queued request does not fit the free budget, later requests
+ * that fit may run ahead of it, at most 4 x max_slots of them, after which
+ * it waits alone for memory (bounded backfilling, no starvation). */
 sip_status sip_server_create(sip_ctx* ctx, int64_t budget_bytes, int max_slots, sip_server** out);
 /* Queue one request: the problem desc (eta_host copied), the element
  * densities rho_host (copied; body force (0, -g rho_K)), host outputs u_host

@@ -3,10 +3,13 @@
 //
 // Each in-flight solve owns a CUDA stream, its device-resident multigrid and
 // Krylov state and a captured V-cycle graph; solves in flight at the same
-// time overlap on the device.  The server admits queued requests first-in
-// first-out whenever a slot is free and the request's device footprint fits
-// in the remaining budget, so requests that arrive while others run join as
-// capacity frees up (continuous batching).
+// time overlap on the device.  The server admits queued requests in arrival
+// order whenever a slot is free and the request's device footprint fits in
+// the remaining budget, so requests that arrive while others run join as
+// capacity frees up (continuous batching).  A head request that does not fit
+// yet does not hold up smaller ones behind it: the first queued request that
+// fits runs ahead of it (backfilling), at most 4 x slots times per head
+// request, after which the head is reserved and runs as soon as memory frees.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -224,6 +227,7 @@ struct ServerRequest {
     sip_solve_opts opts{};
     int64_t bytes = 0;
     double t_submit = 0.0;
+    int bypassed = 0;   // requests admitted ahead of this one while it was the head
     std::shared_ptr<volatile bool> cancel = std::make_shared<volatile bool>(false);
 };
 
@@ -249,6 +253,15 @@ struct sip_server {
 
     void worker_loop();
     sip_status solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep);
+    // index of the queued request to admit now, or -1 (called with mu held)
+    int pick() const {
+        if (queue.empty()) return -1;
+        if (in_use + queue.front().bytes <= budget) return 0;
+        if (queue.front().bypassed >= 4 * slots) return -1;   // reserved: wait for memory
+        for (size_t i = 1; i < queue.size(); ++i)
+            if (in_use + queue[i].bytes <= budget) return int(i);
+        return -1;
+    }
 };
 
 sip_status sip_server::solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep) {
@@ -296,14 +309,18 @@ void sip_server::worker_loop() {
         ServerRequest r;
         {
             std::unique_lock<std::mutex> lk(mu);
-            // FIFO admission: the head request runs when its footprint fits
+            // admission in arrival order with bounded backfilling (pick)
+            int i = -1;
             cv_work.wait(lk, [&] {
-                return stop || (!queue.empty() && in_use + queue.front().bytes <= budget);
+                i = pick();
+                return stop || i >= 0;
             });
             if (stop && queue.empty()) break;
             if (queue.empty()) continue;
-            r = std::move(queue.front());
-            queue.pop_front();
+            if (i < 0) i = 0;   // stopping: drain in order
+            if (i > 0) ++queue.front().bypassed;
+            r = std::move(queue[size_t(i)]);
+            queue.erase(queue.begin() + i);
             in_use += r.bytes;
             ++busy;
             running[r.id] = r.cancel;

@@ -161,6 +161,36 @@ def test_server_queues_beyond_slots(ctx):
     srv.close()
 
 
+def test_server_backfills_past_a_large_head(ctx):
+    """A large request that does not fit the free budget does not hold up the
+    small requests queued behind it: with one large solve running and a
+    second large one at the head of the queue, the small ones run in the
+    spare memory and finish first; the second large one still runs."""
+    nb, ns = 128, 16
+    eta_b = synth.random_eta(nb * nb, 5, (0.0, 2.0))
+    eta_s = synth.random_eta(ns * ns, 6, (0.0, 2.0))
+    big = api.footprint(ctx, nx=nb, ny=nb, k=3, eta=eta_b, n_hlevels=3)
+    small = api.footprint(ctx, nx=ns, ny=ns, k=2, eta=eta_s, n_hlevels=1)
+    assert small < big // 2
+    srv = api.Server(ctx, budget_bytes=big + 3 * small // 2, max_slots=2)
+    order = [("big", 0), ("big", 1), ("small", 2), ("small", 3)]
+    for kind, rid in order:
+        if kind == "big":
+            st, _, _ = srv.submit(rid, nb, nb, 3, eta_b, np.ones(nb * nb), n_hlevels=3,
+                                  bc=synth.SINKER_BC)
+        else:
+            st, _, _ = srv.submit(rid, ns, ns, 2, eta_s, np.ones(ns * ns), n_hlevels=1,
+                                  bc=synth.SINKER_BC)
+        assert st == _lib.SIP_OK
+    srv.drain()
+    done = srv.poll()
+    ids = [i for i, _ in done]
+    assert sorted(ids) == [0, 1, 2, 3]
+    assert all(r["status"] == 0 and r["rel_residual"] <= 1e-8 for _, r in done)
+    assert ids.index(2) < ids.index(1) and ids.index(3) < ids.index(1), ids
+    srv.close()
+
+
 @pytest.mark.parametrize("k,precision", [(2, "fp64"), (3, "mixed"), (5, "fp64"), (6, "fp64")])
 def test_autotuned_schedule(ctx, k, precision):
     """The first set-up of a shape picks its kernels by timing; a second
