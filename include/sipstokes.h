@@ -104,7 +104,8 @@ typedef struct {
      * rounding noise of size eps_32 eta_K |u|, which swamps the residual of
      * the soft medium: at contrast 1e6 the FP32 V-cycle stops reducing the
      * residual altogether.  Default 1e3; 0 = FP32 arithmetic everywhere.
-     * Needs k <= 5 (k = 6 keeps FP32 arithmetic). */
+     * At k = 6, which has no staged kernel, the whole FP32 operator takes
+     * FP64 arithmetic as soon as one tile is marked. */
     double mixed_fp64_ratio;
 } sip_problem_desc;
 

@@ -26,12 +26,15 @@ struct TileCfg {
     static constexpr int EX = (N <= 3) ? 32 : (N <= 5 ? 16 : 8);
 };
 
-template <int N, typename T>
+// TS: storage precision of x, y, z and eta; T: arithmetic precision (the
+// values are converted to T on their way into shared memory and rounded to
+// TS once, at the output).
+template <int N, typename TS, typename T>
 struct ApplyArgs {
-    const T* x;
-    T* y;
-    const T* eta;
-    const T* z;
+    const TS* x;
+    TS* y;
+    const TS* eta;
+    const TS* z;
     T alpha, beta;
     int nx, ny;
     T hx, hy;
@@ -60,8 +63,8 @@ constexpr size_t apply_smem_elems() {
 // the volume cross-term intermediates; stage 2 the face vectors P, Q; stage 3
 // writes each output mode once (no atomics; every face is evaluated from
 // both sides).
-template <int N, typename T>
-__global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
+template <int N, typename TS, typename T>
+__global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, TS, T> a) {
     grid_dep_wait();
     constexpr int NN = N * N, NB = 2 * NN, EX = TileCfg<N>::EX, EXH = EX + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -87,12 +90,12 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
         for (int r = 0; r < 3; ++r) {
             const int eyr = ey + r - 1;
             if (eyr < 0 || eyr >= ny) continue;
-            const T* src = a.x + (size_t(eyr) * nx + exa) * NB;
+            const TS* src = a.x + (size_t(eyr) * nx + exa) * NB;
             T* dst = su + (size_t(r) * EXH + (exa - (ex0 - 1))) * NB;
             const int cnt = ncol * NB;
-            for (int q = tid; q < cnt; q += nt) dst[q] = src[q];
+            for (int q = tid; q < cnt; q += nt) dst[q] = T(src[q]);
             for (int q = tid; q < ncol; q += nt)
-                seta[r * EXH + (exa - (ex0 - 1)) + q] = a.eta[size_t(eyr) * nx + exa + q];
+                seta[r * EXH + (exa - (ex0 - 1)) + q] = T(a.eta[size_t(eyr) * nx + exa + q]);
         }
     }
     __syncthreads();
@@ -243,15 +246,15 @@ __global__ void __launch_bounds__(256) k_apply_sip(const ApplyArgs<N, T> a) {
         acc += a.tab.lp[b] * pT[av] + a.tab.dp[b] * pT[2 * N + av];
         const size_t o = (size_t(ey) * nx + ex) * NB + (q - t * NB);
         T out = a.alpha * acc;
-        if (a.z) out += a.beta * a.z[o];
-        a.y[o] = out;
+        if (a.z) out += a.beta * T(a.z[o]);
+        a.y[o] = TS(out);
     }
 }
 
-template <int N, typename T>
-void apply_sip_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const T* z, T beta,
+template <int N, typename TS, typename T>
+void apply_sip_n(const OpGeom& g, const TS* x, TS* y, const TS* eta, T alpha, const TS* z, T beta,
                  cudaStream_t s) {
-    ApplyArgs<N, T> a;
+    ApplyArgs<N, TS, T> a;
     a.x = x;
     a.y = y;
     a.eta = eta;
@@ -277,13 +280,13 @@ void apply_sip_n(const OpGeom& g, const T* x, T* y, const T* eta, T alpha, const
     constexpr int EX = TileCfg<N>::EX;
     const size_t smem = apply_smem_elems<N, T>() * sizeof(T);
     static const bool attr_set = [smem] {   // once per process, thread-safe
-        SIP_CUDA(cudaFuncSetAttribute(k_apply_sip<N, T>,
+        SIP_CUDA(cudaFuncSetAttribute(k_apply_sip<N, TS, T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         return true;
     }();
     (void)attr_set;
     dim3 grid((g.nx + EX - 1) / EX, g.ny);
-    launch_k(k_apply_sip<N, T>, grid, 256, smem, s, a);
+    launch_k(k_apply_sip<N, TS, T>, grid, 256, smem, s, a);
     SIP_CHECK_LAUNCH();
 }
 
@@ -484,7 +487,8 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
     // low degrees: thread-per-element kernels with compile-time tables,
     // unless the schedule picks the shared-memory tile kernel
     const int v = apply_variant<T>(g);
-    // the split-precision FP32 operator exists only as the staged kernel
+    // the split-precision FP32 operator: the staged kernel's two launches
+    // (k <= 5), else the tile kernel with FP64 arithmetic throughout
     const bool split = sizeof(T) == 4 && g.n_hi > 0;
     if constexpr (sizeof(T) == 4) {
         if (v == APPLY_WARP && !split &&
@@ -496,6 +500,23 @@ void launch_apply_sip(int N, const OpGeom& g, const T* x, T* y, const T* eta, T 
     if ((v == APPLY_STAGE || split) &&
         launch_apply_sip_stage<T>(N, g, x, y, eta, alpha, z, beta, nullptr, s))
         return;
+    if constexpr (sizeof(T) == 4) {
+        if (split) {
+            // no staged kernel at this degree (k = 6): FP64 arithmetic on the
+            // FP32 data of the whole mesh rather than FP32 arithmetic on the
+            // marked tiles, whose cancellation it cannot afford
+            const double a64 = double(alpha), b64 = double(beta);
+            switch (N) {
+                case 2: apply_sip_n<2, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                case 3: apply_sip_n<3, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                case 4: apply_sip_n<4, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                case 5: apply_sip_n<5, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                case 6: apply_sip_n<6, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                case 7: apply_sip_n<7, float, double>(g, x, y, eta, a64, z, b64, s); return;
+                default: throw Error(SIP_ERR_INVALID_ARG, "unsupported polynomial degree");
+            }
+        }
+    }
     if (v != APPLY_TILE &&
         launch_apply_sip_elem<T>(N, g, x, y, eta, alpha, z, beta, v != APPLY_ELEM1, s))
         return;

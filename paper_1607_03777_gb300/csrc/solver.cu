@@ -448,13 +448,14 @@ void Multigrid<T>::build_coarse_from_band(const std::vector<double>& band_in, in
 }
 
 // Mixed form: the FP32 operator evaluates the tiles near elements with
-// eta >= ratio x min(eta) in FP64 arithmetic (apply_stage.cu); the FP64
+// eta >= ratio x min(eta) in FP64 arithmetic (apply_stage.cu; for k = 6,
+// which has no staged kernel, the whole operator: apply.cu); the FP64
 // operator has no such tiles.
 template <typename T>
 void Multigrid<T>::mark_split_tiles(cudaStream_t s) {
     n_hi = 0;
     const double ratio = P->desc.mixed_fp64_ratio;
-    if (sizeof(T) == 4 && ratio > 0.0 && N <= 6) {
+    if (sizeof(T) == 4 && ratio > 0.0) {
         const int nt = split_tile_count(P->desc.nx, P->desc.ny);
         hi_flag.alloc(size_t(nt));
         hi_list.alloc(size_t(nt) * sizeof(int));
