@@ -406,7 +406,6 @@ def run_ours(args, rank, world):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # the same count for FP32: 128 FMA per SM per clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md")
 
 
 def kernel_name(code, k, word):
@@ -509,10 +508,10 @@ def apply_f32_rooflines(ctx, dev, flush, stream, peaks):
     return out
 
 
-# committed ncu summaries: the FP64 apply kernels on the 128^2, k = 3 workload and the
-# FP32 warp-row apply on 512^2
+# committed ncu summaries of kernels in their current form: the FP64 staged apply on the
+# 128^2, k = 3 workload and the FP32 warp-row apply on 512^2 (a kernel without one
+# reports traffic null)
 TRAFFIC_PROFILES = {
-    "k_apply_elem2<4,double,1>": os.path.join(ROOT, "profiles", "k_apply_elem2_fp64_128x128_k3.md"),
     "k_apply_stage<4,double,double,4,1,0>": os.path.join(
         ROOT, "profiles", "k_apply_stage4_fp64_128x128_k3.md"),
     # the warp-row FP32 apply on the 512^2 meshes of sip_apply_f32
