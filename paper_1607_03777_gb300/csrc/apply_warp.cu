@@ -37,7 +37,9 @@ constexpr int WTY = 4;            // tile rows: the warps of a CTA
 constexpr int WNT = WTX * WTY;    // threads per CTA
 constexpr unsigned FULL = 0xffffffffu;
 
-template <int N, int NBUF = 2>
+// NBUF stage buffers (the launched kernel uses one; the helpers below read
+// only the members that do not depend on NBUF)
+template <int N, int NBUF = 1>
 struct WarpLayout {
     static constexpr int NN = N * N;
     static constexpr int NB = 2 * NN;               // floats per element
