@@ -23,6 +23,7 @@
 #include <mutex>
 #include <thread>
 
+#include "admission.h"
 #include "sip_solver.h"
 
 using sip::Error;
@@ -254,14 +255,7 @@ struct sip_server {
     void worker_loop();
     sip_status solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep);
     // index of the queued request to admit now, or -1 (called with mu held)
-    int pick() const {
-        if (queue.empty()) return -1;
-        if (in_use + queue.front().bytes <= budget) return 0;
-        if (queue.front().bypassed >= 4 * slots) return -1;   // reserved: wait for memory
-        for (size_t i = 1; i < queue.size(); ++i)
-            if (in_use + queue[i].bytes <= budget) return int(i);
-        return -1;
-    }
+    int pick() const { return sip::admission_pick(queue, in_use, budget, 4 * slots); }
 };
 
 sip_status sip_server::solve_one(ServerRequest& r, cudaStream_t s, sip_solve_report& rep) {
