@@ -556,7 +556,7 @@ def roofline(ab, af, apply_ms, kernel, traffic, peaks):
 
 
 # ------------------------------------------------------------------ oracle
-ORACLE_SIZES = (16, 24)   # meshes of the timed oracle samples (3 h-coarsenings each)
+ORACLE_SIZES = (16, 24, 32)   # meshes of the timed oracle samples (3 h-coarsenings each)
 
 
 def oracle_sample(n):
@@ -581,31 +581,56 @@ def oracle_sample(n):
     return time.perf_counter() - t0, its
 
 
-def _oracle_worker(n, q):
-    q.put((n,) + oracle_sample(n))
+# BLAS thread counts of the oracle's processes: one each, so that a process
+# uses one host core (numpy is first imported in the spawned child)
+_BLAS_THREADS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                 "BLIS_NUM_THREADS")
 
 
-def oracle_scaling():
-    """The oracle timed on two mesh sizes at once (one process each, spawned:
-    two host cores), and the growth exponent of its time in the element
-    count fitted to them; the 128^2 time is the 24^2 time scaled by that
-    exponent (an extrapolation, labelled as such)."""
-    import math
+def _oracle_worker(n, reps, q):
+    q.put((n, [oracle_sample(n) for _ in range(reps)]))
+
+
+def run_oracle_processes(jobs):
+    """Oracle samples in spawned processes, one per (n, reps) job, each with
+    single-threaded BLAS; returns {n: [(seconds, outer iterations), ...]}."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(n, q)) for n in ORACLE_SIZES]
-    for p in procs:
-        p.start()
+    saved = {k: os.environ.get(k) for k in _BLAS_THREADS}
+    os.environ.update({k: "1" for k in _BLAS_THREADS})
+    try:
+        procs = [ctx.Process(target=_oracle_worker, args=(n, reps, q)) for n, reps in jobs]
+        for p in procs:
+            p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     got = {}
     for _ in procs:
-        n, dt, its = q.get()
-        got[n] = (dt, its)
+        n, res = q.get()
+        got[n] = res
     for p in procs:
         p.join()
-    (n0, n1) = ORACLE_SIZES
-    alpha = math.log(got[n1][0] / got[n0][0]) / math.log((n1 * n1) / (n0 * n0))
-    t128 = got[n1][0] * ((128 * 128) / (n1 * n1)) ** alpha
+    return got
+
+
+def oracle_scaling():
+    """The oracle timed on several mesh sizes at once (one spawned process
+    each, one host core each), and the growth of its time in the element
+    count fitted to them by least squares in log-log; the 128^2 time is that
+    fit evaluated at 128^2 (an extrapolation, labelled as such)."""
+    import math
+    res = run_oracle_processes([(n, 1) for n in ORACLE_SIZES])
+    got = {n: res[n][0] for n in ORACLE_SIZES}
+    xs = [math.log(n * n) for n in ORACLE_SIZES]
+    ys = [math.log(got[n][0]) for n in ORACLE_SIZES]
+    mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+    alpha = sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    t128 = math.exp(my + alpha * (math.log(128 * 128) - mx))
     return {"samples": {f"{n}x{n}": {"s": got[n][0], "outer_its": got[n][1]} for n in ORACLE_SIZES},
             "exponent": alpha, "extrapolated_s_128x128": t128,
             "cores": len(ORACLE_SIZES), "host_cpus": os.cpu_count()}
@@ -617,12 +642,10 @@ def run_reference(args):
     (the full 128 x 128 solve takes the oracle minutes): the line's value
     and ms_per_step are what was timed; the 128 x 128 estimate is beside
     them."""
-    per, its = [], 0
     n0 = ORACLE_SIZES[0]
-    for i in range(args.warmup + args.steps):
-        dt, its = oracle_sample(n0)
-        if i >= args.warmup:
-            per.append(dt)
+    runs = run_oracle_processes([(n0, args.warmup + args.steps)])[n0]   # one core
+    per = [dt for dt, _ in runs[args.warmup:]]
+    its = runs[-1][1]
     value = len(per) / sum(per)
     cfg = dict(headline_config(args),
                workload=f"single_box_inclusion_{n0}x{n0}_k3_eta1e4_Q1+3h (oracle sample of the "
@@ -638,7 +661,8 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cpus": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{n0}x{n0} mesh of the headline physics per step, "
-                                       f"{its} outer iterations; SciPy sparse, single-threaded"},
+                                       f"{its} outer iterations; one spawned process, "
+                                       "single-threaded BLAS"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -646,13 +670,13 @@ def run_reference(args):
 def cpu_baseline():
     sc = oracle_scaling()
     t = sc["extrapolated_s_128x128"]
-    n0, n1 = ORACLE_SIZES
+    meshes = ", ".join(f"{n}x{n}" for n in ORACLE_SIZES)
     return {"value": 1.0 / t, "unit": UNIT, "cores": sc["cores"], "host_cpus": sc["host_cpus"],
             "kind": "oracle",
-            "sample": f"oracle solves of the headline physics on {n0}x{n0} and {n1}x{n1} meshes "
-                      "(3 h-coarsenings each), one spawned process per mesh, SciPy sparse "
-                      f"single-threaded; value = 1 / (the {n1}x{n1} time scaled to 128x128 by the "
-                      "fitted exponent of time in the element count): an extrapolation",
+            "sample": f"oracle solves of the headline physics on {meshes} meshes (3 "
+                      "h-coarsenings each), one spawned process per mesh with single-threaded "
+                      "BLAS; value = 1 / (the 128x128 time of the least-squares fit "
+                      "of log time against log element count): an extrapolation",
             "measured": sc["samples"], "exponent": sc["exponent"],
             "extrapolated_s_128x128": t}
 
